@@ -1,0 +1,147 @@
+"""CPU FP64 oracle for the spinor polarizability (TEST INFRASTRUCTURE ONLY).
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  The product path (the CUDA library and
+its binding) never does.  The arithmetic lives in `bgw_oracle.c` (plain C,
+FP64, direct G-space convolution, no FFT); this module compiles it with gcc,
+loads it with ctypes and walks k in a fixed order.
+
+What the functions follow (arXiv:2206.00808, Sec. II):
+  * `mtxel`      -- M_vc(k,q,G), Eq. (matrix_el) as a cyclic convolution;
+  * `weight`     -- the P-formula bracket at omega -> i omega, eta -> 0;
+  * `chi0`       -- the P formula: (1/N_k) sum_k sum_v sum_c w conj(M) M,
+                    no spin-degeneracy factor;
+  * `umklapp`    -- k + q = k' + G0 with k' on the grid (Bloch periodicity;
+                    the paper is silent on it).
+All are pinned by tests/test_oracle_pins.py; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bgw_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile bgw_oracle.c into oracle/_build/liboracle.so with gcc."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            lib.oracle_mtxel.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P,
+                                         ctypes.c_int, P, ctypes.c_int, P, P,
+                                         ctypes.c_int, P, P]
+            lib.oracle_mtxel.restype = ctypes.c_int
+            lib.oracle_weight.argtypes = [ctypes.c_double] * 3
+            lib.oracle_weight.restype = ctypes.c_double
+            lib.oracle_chi0_accumulate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                                   P, P, ctypes.c_int, P, P]
+            lib.oracle_chi0_accumulate.restype = None
+            lib.oracle_scale.argtypes = [ctypes.c_long, ctypes.c_double, P]
+            lib.oracle_scale.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def mtxel(box, gv, cv, gc, cc, G0, geps) -> np.ndarray:
+    """M[v][c][g] (complex128) for valence coefficients cv [nv][2][ngw_v] on
+    sphere gv at k and conduction coefficients cc [nc][2][ngw_c] on sphere gc
+    at k' = k + q - G0; geps is the dielectric sphere (ng, 3)."""
+    lib = _load()
+    box, gv, gc, G0, geps = _i32(box), _i32(gv), _i32(gc), _i32(G0), _i32(geps)
+    cv, cc = _c128(cv), _c128(cc)
+    nv, nc, ng = cv.shape[0], cc.shape[0], geps.shape[0]
+    M = np.zeros((nv, nc, ng), dtype=np.complex128)
+    rc = lib.oracle_mtxel(_ptr(box), gv.shape[0], _ptr(gv), nv, _ptr(cv),
+                          gc.shape[0], _ptr(gc), nc, _ptr(cc), _ptr(G0), ng, _ptr(geps), _ptr(M))
+    if rc != 0:
+        raise MemoryError("oracle_mtxel: scratch allocation failed")
+    return M
+
+
+def weight(e_v: float, e_c: float, w: float) -> float:
+    """2 D / (D^2 + w^2), D = e_v - e_c (eV^-1)."""
+    return _load().oracle_weight(float(e_v), float(e_c), float(w))
+
+
+def chi0_accumulate(M, e_v, e_c, freq, chi) -> None:
+    """chi[j] += sum_{v,c} w_vc(i w_j) conj(M[v,c,:])^T M[v,c,:] (in place)."""
+    lib = _load()
+    M, e_v, e_c, freq = _c128(M), _f64(e_v), _f64(e_c), _f64(freq)
+    assert chi.dtype == np.complex128 and chi.flags.c_contiguous
+    nv, nc, ng = M.shape
+    assert chi.shape == (len(freq), ng, ng)
+    lib.oracle_chi0_accumulate(nv, nc, ng, _ptr(M), _ptr(e_v), _ptr(e_c), len(freq),
+                               _ptr(freq), _ptr(chi))
+
+
+def umklapp(kcrys: np.ndarray, ik: int, q) -> tuple[int, np.ndarray]:
+    """(k', G0) with kcrys[ik] + q = kcrys[k'] + G0, G0 integer."""
+    target = np.asarray(kcrys[ik], float) + np.asarray(q, float)
+    for kp in range(len(kcrys)):
+        d = target - kcrys[kp]
+        if np.all(np.abs(d - np.round(d)) < 1e-8):
+            return kp, np.round(d).astype(np.int32)
+    raise ValueError(f"k + q is not on the k-grid (k index {ik}, q = {q})")
+
+
+def chi0(problem, iq: int = 0, k_indices=None, nc=None) -> np.ndarray:
+    """chi0[j][G][G'] (complex128, eV^-1) of a synthetic Problem for q-point iq.
+
+    Sums k over `k_indices` (default: every k, in index order) and always
+    divides by the full N_k, so a subset gives that subset's share of the sum.
+    """
+    lib = _load()
+    q, geps, ncq = problem.qs[iq]
+    if nc is not None:
+        ncq = nc
+    nv = problem.nv
+    ng = len(geps)
+    freq = _f64(problem.freq)
+    chi = np.zeros((len(freq), ng, ng), dtype=np.complex128)
+    ks = range(problem.nk) if k_indices is None else k_indices
+    for ik in ks:
+        kp, G0 = umklapp(problem.kcrys, ik, q)
+        M = mtxel(problem.box, problem.gvec[ik], problem.coeff[ik][:nv],
+                  problem.gvec[kp], problem.coeff[kp][nv:nv + ncq], G0, geps)
+        chi0_accumulate(M, problem.energy[ik][:nv], problem.energy[kp][nv:nv + ncq], freq, chi)
+    flat = chi.reshape(-1).view(np.float64)
+    lib.oracle_scale(flat.size, 1.0 / problem.nk, _ptr(flat))
+    return chi

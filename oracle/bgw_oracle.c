@@ -1,0 +1,168 @@
+/*
+ * CPU FP64 oracle for the spinor RPA polarizability chi0_GG'(q, i omega).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the package smoke check and
+ * the benchmark's CPU-baseline leg load this file's library.  It shares no
+ * code, header, table or helper with the CUDA path; it is plain C99 with
+ * OpenMP, no FFT and no BLAS, written to be checked against the paper by eye.
+ *
+ * What it computes (arXiv:2206.00808, Sec. II):
+ *
+ *  Matrix element, Eq. (matrix_el) and the M_nn' definition above it.  With
+ *  the band at k written as v and the band at k+q as c, and plane-wave
+ *  coefficients u_{n,k,alpha}(r) = sum_h c_{n,k,alpha}(h) e^{2 pi i h.r/N}
+ *  (Sec. III.A, the plane-wave form of a Bloch function), the FFT route
+ *      M_vc(k,q,G) = N^-3 sum_r sum_alpha u*_{v,k,alpha}(r) u_{c,k+q,alpha}(r) e^{-2 pi i G.r/N}
+ *  is identical, for every box, to the cyclic convolution in G-space
+ *      M_vc(k,q,G) = sum_alpha sum_{h1 in sphere(k)} conj(c_{v,k,alpha}(h1)) C_{c,k+q,alpha}[(h1+G) mod N]
+ *  where C is the coefficient array of the band at k+q scattered (additively)
+ *  onto the N1 x N2 x N3 box.  This oracle evaluates the second form directly.
+ *  The band at k+q is stored at the grid point k' = k + q - G0 (Bloch
+ *  periodicity, c_{k+q}(h) = c_{k'}(h + G0)), so a coefficient of k' at Miller
+ *  index m lands at box index (m - G0) mod N.
+ *
+ *  Polarizability, the unnumbered P_GG'(q, omega) formula of Sec. II,
+ *  evaluated on the imaginary axis (omega -> i omega, eta -> 0):
+ *      chi0_GG'(q, i w) = (1/N_k) sum_k sum_v sum_c w_vc(i w) conj(M_vc(G)) M_vc(G')
+ *      w_vc(i w) = 1/(D - i w) + 1/(D + i w) = 2 D / (D^2 + w^2),  D = e_{v,k} - e_{c,k+q}
+ *  in eV^-1, with no spin-degeneracy factor: spinor bands carry both spin
+ *  components, and the sum over alpha inside M is the only spin sum
+ *  (Sec. II, the paragraph after Eq. matrix_el).
+ *
+ * Summation order is fixed (k outer in the caller, then v, c), and the
+ * parallel loops split only independent output entries, so the result does
+ * not depend on the thread count.
+ *
+ * Parity status: every function here is pinned by the CPU tests (brute-force
+ * real-space sums, numpy.fft, closed forms and invariants); none is unpinned.
+ */
+#include <stdlib.h>
+#include <string.h>
+
+static long wrap_index(long h, long n)
+{
+    long r = h % n;
+    return r < 0 ? r + n : r;
+}
+
+static long box_index(const int *box, long h0, long h1, long h2)
+{
+    return (wrap_index(h0, box[0]) * box[1] + wrap_index(h1, box[1])) * box[2]
+           + wrap_index(h2, box[2]);
+}
+
+/*
+ * Matrix elements for one k: M[v][c][g] (interleaved complex128).
+ *   box      : N1, N2, N3
+ *   gv, cv   : sphere at k (ngw_v Miller triples) and valence coefficients
+ *              [nv][2][ngw_v] interleaved complex128
+ *   gc, cc   : sphere at k' and conduction coefficients [nc][2][ngw_c]
+ *   G0       : umklapp vector, k + q = k' + G0
+ *   geps     : dielectric sphere, ng Miller triples
+ * Returns 0, or -1 if a scratch allocation failed.
+ */
+int oracle_mtxel(const int *box,
+                 int ngw_v, const int *gv, int nv, const double *cv,
+                 int ngw_c, const int *gc, int nc, const double *cc,
+                 const int *G0, int ng, const int *geps, double *M)
+{
+    const long nbox = (long)box[0] * box[1] * box[2];
+    int failed = 0;
+
+#pragma omp parallel
+    {
+        double *cbox = (double *)malloc(sizeof(double) * 2 * 2 * nbox);
+        if (!cbox) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int c = 0; c < nc; ++c) {
+            if (!cbox) continue;
+            /* C_{c,k+q,alpha} on the box: coefficient of k' at m sits at m - G0. */
+            memset(cbox, 0, sizeof(double) * 2 * 2 * nbox);
+            for (int a = 0; a < 2; ++a) {
+                const double *src = cc + 2 * ((long)(c * 2 + a) * ngw_c);
+                double *dst = cbox + 2 * (long)a * nbox;
+                for (int i = 0; i < ngw_c; ++i) {
+                    long idx = box_index(box, (long)gc[3 * i] - G0[0],
+                                         (long)gc[3 * i + 1] - G0[1],
+                                         (long)gc[3 * i + 2] - G0[2]);
+                    dst[2 * idx] += src[2 * i];
+                    dst[2 * idx + 1] += src[2 * i + 1];
+                }
+            }
+            for (int v = 0; v < nv; ++v) {
+                for (int g = 0; g < ng; ++g) {
+                    double re = 0.0, im = 0.0;
+                    for (int a = 0; a < 2; ++a) {
+                        const double *vv = cv + 2 * ((long)(v * 2 + a) * ngw_v);
+                        const double *cb = cbox + 2 * (long)a * nbox;
+                        for (int i = 0; i < ngw_v; ++i) {
+                            long idx = box_index(box, (long)gv[3 * i] + geps[3 * g],
+                                                 (long)gv[3 * i + 1] + geps[3 * g + 1],
+                                                 (long)gv[3 * i + 2] + geps[3 * g + 2]);
+                            /* conj(a) * b */
+                            double ar = vv[2 * i], ai = vv[2 * i + 1];
+                            double br = cb[2 * idx], bi = cb[2 * idx + 1];
+                            re += ar * br + ai * bi;
+                            im += ar * bi - ai * br;
+                        }
+                    }
+                    double *out = M + 2 * (((long)v * nc + c) * ng + g);
+                    out[0] = re;
+                    out[1] = im;
+                }
+            }
+        }
+        free(cbox);
+    }
+    return failed ? -1 : 0;
+}
+
+/*
+ * Weight of one pair on the imaginary axis: the bracket of the P formula with
+ * omega -> i w and eta -> 0, 1/(D - i w) + 1/(D + i w) = 2 D / (D^2 + w^2).
+ */
+double oracle_weight(double e_v, double e_c, double w)
+{
+    double d = e_v - e_c;
+    return 2.0 * d / (d * d + w * w);
+}
+
+/*
+ * chi[j][G][G'] += sum_{v,c} w_vc(i w_j) conj(M[v][c][G]) M[v][c][G'] for one k,
+ * all G, G' (the full matrix, no symmetry used).  e_v: [nv] energies at k,
+ * e_c: [nc] energies at k+q, freq: [nfreq] eV.  The 1/N_k factor is applied by
+ * oracle_scale once all k are in.
+ */
+void oracle_chi0_accumulate(int nv, int nc, int ng, const double *M,
+                            const double *e_v, const double *e_c,
+                            int nfreq, const double *freq, double *chi)
+{
+    for (int j = 0; j < nfreq; ++j) {
+        double *cj = chi + 2 * (long)j * ng * ng;
+#pragma omp parallel for schedule(static)
+        for (int g = 0; g < ng; ++g) {
+            for (int v = 0; v < nv; ++v) {
+                for (int c = 0; c < nc; ++c) {
+                    double w = oracle_weight(e_v[v], e_c[c], freq[j]);
+                    const double *mp = M + 2 * (((long)v * nc + c) * ng);
+                    double ar = mp[2 * g], ai = mp[2 * g + 1];
+                    double *row = cj + 2 * (long)g * ng;
+                    for (int h = 0; h < ng; ++h) {
+                        double br = mp[2 * h], bi = mp[2 * h + 1];
+                        row[2 * h] += w * (ar * br + ai * bi);
+                        row[2 * h + 1] += w * (ar * bi - ai * br);
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* x[i] *= s for n doubles (applies the 1/N_k of the P formula). */
+void oracle_scale(long n, double s, double *x)
+{
+    for (long i = 0; i < n; ++i) x[i] *= s;
+}
