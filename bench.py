@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark of the spinor polarizability chi0_GG'(q, i w) on GB300.
+
+One step = the whole hot path for one q-point of the Si-like workload
+(FCC a = 10.26 bohr, 24^3 FFT box, ~2000 plane waves per spinor component,
+N_G = 350, 4x4x4 k-grid (N_k = 64), N_v = 8, N_c = 200, omega = 0 plus 4
+imaginary frequencies up to 40 eV, q = (1/4, 0, 0)): every k-point's spinor
+coefficients go to the real-space grid, every (v, c, k) pair's matrix
+elements are formed and contracted into chi0, and chi0 is finalised.
+Inputs are seeded synthetic states of that shape (no DFT data).
+
+Prints one JSON line (metric q-points/s); see --help.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "si24"
+WORKLOAD_DESC = ("Si-like FCC a=10.26 bohr, 24^3 box, N_w~2000 per spinor component, N_G=350, "
+                 "N_k=64 (4x4x4), N_v=8, N_c=200, 5 imaginary freqs (0..40 eV), q=(1/4,0,0)")
+METRIC = "spinor chi0 q-points/s and TFLOP/s, FP64 vs mixed at ≤2e-5 rel. Frobenius error"
+
+# FP64 issue rate of GB300 derived from its nominal 1.25 TFLOP/s over 152 SMs
+# at the 2070 MHz maximum clock: 1.25e12 / (152 * 2.07e9) ~ 4 flop/clk/SM,
+# i.e. 2 DFMA per clock per SM.  Peak = 152 * 2 * 2 * 2.07e9.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# DRAM bytes per launch of the FP64 contraction kernel from one ncu capture
+# (profiles/k4_herk_f64_si24.txt); valid for the kernel source it was taken on.
+TRAFFIC = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------- distributed --
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    def __init__(self, world, rank, backend):
+        self.world, self.rank = world, rank
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.rows, self.proc = [], None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------ flop model --
+
+def flop_model(p, iq=0):
+    """Algorithmic FLOPs of one q-point: pruned radix FFTs (5 L log2 L per
+    line of length L), the pair density (8 flops per point and spin
+    component) and the Hermitian contraction (8 flops per complex MAC over
+    N_G(N_G+1)/2 entries per pair and frequency)."""
+    q, geps, nc = p.qs[iq]
+    n = np.array(p.box, float)
+    L = float(np.log2(n[0]))
+    w = geps.max(0) - geps.min(0) + 1
+    per_pair_fft = 5 * n[0] * L * (n[0] * n[1] + n[0] * w[1] + w[1] * w[2])
+    per_pair_rho = 8 * 2 * np.prod(n)
+    pairs = p.nk * p.nv * nc
+    band_fft = 0.0
+    for ik in range(p.nk):
+        ws = p.gvec[ik].max(0) - p.gvec[ik].min(0) + 1
+        band_fft += 2 * p.nbands * 5 * n[0] * L * (ws[1] * ws[2] + n[0] * ws[2] + n[0] * n[1])
+    ng = len(geps)
+    herk = 8.0 * pairs * len(p.freq) * ng * (ng + 1) / 2
+    return {"wfn_to_grid": band_fft, "mtxel": pairs * (per_pair_fft + per_pair_rho),
+            "contraction": herk, "total": band_fft + pairs * (per_pair_fft + per_pair_rho) + herk}
+
+
+# ---------------------------------------------------------------- oracle --
+
+def oracle_sample(p, k_indices):
+    """Time the CPU oracle on the given k-points of one q (all bands, all G,
+    all frequencies); returns (seconds, threads)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.chi0(p, k_indices=k_indices)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dt, threads
+
+
+def cpu_baseline(p):
+    ks = [0]
+    dt, cores = oracle_sample(p, ks)
+    qps = 1.0 / (dt * p.nk / len(ks))
+    return {"value": qps, "unit": "q-points/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(ks)} of {p.nk} k-points of one q (all {p.nv}x{p.qs[0][2]} pairs, "
+                      f"N_G={len(p.qs[0][1])}, {len(p.freq)} freqs) in {dt:.1f} s, scaled x{p.nk}"}
+
+
+# ------------------------------------------------------------------ arms --
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from paper_2206_00808_gb300 import synthetic as syn
+    p = syn.make_problem(WORKLOAD)
+    for _ in range(args.warmup and 1):
+        oracle_sample(p, [0])
+    times = []
+    cores = 1
+    for _ in range(args.steps):
+        dt, cores = oracle_sample(p, [0])
+        times.append(dt * p.nk)
+    ms = 1e3 * statistics.mean(times)
+    value = 1e3 / ms
+    line = {"metric": METRIC, "value": value, "unit": "q-points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "q-points/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: 1 of {p.nk} k-points, scaled x{p.nk}"},
+            "e2e": {"value": value, "unit": "q-points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = Dist(world, rank, "nccl")
+    from paper_2206_00808_gb300 import build
+    build.build()
+    from paper_2206_00808_gb300 import binding as B
+    from paper_2206_00808_gb300 import synthetic as syn
+
+    p = syn.make_problem(WORKLOAD)
+    q, geps, nc = p.qs[0]
+    ng, nf = len(geps), len(p.freq)
+    stream = torch.cuda.current_stream()
+    dev_in = [(torch.from_numpy(np.ascontiguousarray(p.coeff[ik])).cuda(),
+               torch.from_numpy(np.ascontiguousarray(p.energy[ik])).cuda()) for ik in range(p.nk)]
+    out = torch.empty((nf, ng, ng), dtype=torch.complex128, device="cuda")
+    ctx = B.Chi0Context(p, args.precision, stream)
+
+    def step():
+        ctx.reset()
+        ctx.upload(device_inputs=dev_in)
+        ctx.accumulate()
+        B.bgw_chi0_finalize(ctx.ctx, 0, out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    B.bgw_profile(ctx.ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ms_total = dist.max(ev0.elapsed_time(ev1))
+    prof = B.bgw_profile_read(ctx.ctx)
+    B.bgw_profile(ctx.ctx, False)
+    ms = ms_total / args.steps
+    value = world * 1e3 / ms
+
+    fl = flop_model(p)
+    stages = {}
+    for s, (sms, calls, kern) in prof.items():
+        stages[s] = {"ms_per_step": sms / args.steps, "share": sms / max(1e-9, ms_total),
+                     "launch_groups": calls, "kernels": kern}
+    con_ms, con_calls, _ = prof["contraction"]
+    per_launch_flop = fl["contraction"] / p.nk
+    achieved = per_launch_flop / (con_ms / con_calls * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS
+    roofline = {"bound": "alu", "kernel": "k4_herk_f64", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRAFFIC.get("k4_herk_f64"),
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal FP64 1.25 TFLOP/s)"}
+    gpu_launches = sum(v["kernels"] for v in stages.values())
+
+    e2e = None
+    if not args.no_e2e:
+        pin = [(torch.from_numpy(np.ascontiguousarray(p.coeff[ik])).pin_memory(),
+                torch.from_numpy(np.ascontiguousarray(p.energy[ik])).pin_memory()) for ik in range(p.nk)]
+        host_out = torch.empty((nf, ng, ng), dtype=torch.complex128).pin_memory()
+        h2d = sum(c.numel() * c.element_size() + e.numel() * e.element_size() for c, e in pin)
+        d2h = host_out.numel() * host_out.element_size()
+
+        def e2e_step():
+            ctx.reset()
+            ctx.upload(device_inputs=pin)
+            ctx.accumulate()
+            B.bgw_chi0_finalize(ctx.ctx, 0, host_out.numpy())
+
+        e2e_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        ev0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ems = dist.max(ev0.elapsed_time(ev1)) / args.e2e_steps
+        e2e = {"value": world * 1e3 / ems, "unit": "q-points/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "q-points/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32+bf16x3",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD_DESC, "precision": args.precision,
+                           "pairs_per_q": p.pairs(), "l2": "inputs larger than L2 (coefficients "
+                           f"{sum(c.nbytes for c in p.coeff) / 1e9:.2f} GB, grids resident per step)"},
+                "tflops": fl["total"] / (ms * 1e-3) / 1e12,
+                "pairs_per_s": value * p.pairs(),
+                "stages": stages,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * bgw_chi.h -- C ABI of libbgwchi.so: the spinor RPA polarizability
+ * chi0_GG'(q, i w) on one GB300 (sm_103a).
+ *
+ * Method (arXiv:2206.00808, Sec. II):
+ *   Spinor states psi_nk = sum_alpha phi_nk,alpha |alpha>, normalised over
+ *   both components together; plane-wave coefficients c_nk,alpha(G) on a
+ *   wavefunction G-sphere at each k (Sec. II; plane-wave form, Sec. III.A).
+ *   Matrix element, Eq. (matrix_el): multiply the real-space wavefunctions of a
+ *   common spin component, Fourier transform the product, sum over alpha:
+ *       M_vc(k,q,G) = N^-3 sum_r sum_alpha u*_{v,k,alpha}(r) u_{c,k+q,alpha}(r) e^{-iG.r}.
+ *   Polarizability (the P_GG'(q,w) formula of Sec. II) on the imaginary axis,
+ *   w -> i w, eta -> 0, no spin-degeneracy factor:
+ *       chi0_GG'(q,iw) = (1/N_k) sum_k sum_v sum_c w_vc(iw) conj(M_vc(G)) M_vc(G'),
+ *       w_vc(iw) = 2 D / (D^2 + w^2),  D = e_{v,k} - e_{c,k+q}   (eV, chi0 in 1/eV).
+ *   Occupied bands sit at k, empty bands at k+q; the paper's own arrangement
+ *   (occupied at k+q, e^{+i(q+G)r}) is the same matrix at -q with G -> -G.
+ *   k + q is reduced to a grid point k' with k + q = k' + G0 (G0 integer);
+ *   c_{k+q}(G) = c_{k'}(G + G0).
+ *
+ * Conventions
+ *   - Complex numbers are interleaved (re, im) pairs: complex128 = 2 doubles,
+ *     complex64 = 2 floats.  Arrays are C row-major, last index fastest.
+ *   - G-vectors are Miller triples (int32[3]) in the reciprocal basis; k and q
+ *     are in crystal coordinates.  Only the FFT box, the Miller spheres and
+ *     the k list enter: the cell itself is not needed.
+ *   - Supported FFT lengths per axis: 16, 18, 20, 24, 27, 30, 32, 36, 40, 48, 64
+ *     (products of 2, 3 and 5 up to 64).
+ *
+ * Ownership and streams
+ *   - The caller owns every pointer it passes.  The context owns its device
+ *     buffers (real-space grids, scratch, accumulators) and frees them in
+ *     bgw_destroy.
+ *   - All device work is queued on the stream given to bgw_create (NULL = the
+ *     legacy default stream) and is asynchronous unless a function says
+ *     otherwise.  Host input buffers are read by copies queued on that stream:
+ *     keep them alive and unchanged until the stream has passed this work (a
+ *     blocking bgw_chi0_finalize, or a stream synchronize).
+ *   - A context is not thread-safe: use one context per host thread.
+ *
+ * Errors
+ *   - Negative status: the call was rejected or failed; no accumulated state
+ *     changed, except BGW_E_CUDA (the device state is then unknown; destroy
+ *     the context).
+ *   - Positive status: a warning; the result is defined.
+ *   - bgw_last_error(ctx) returns a message for the last call on ctx;
+ *     bgw_last_error(NULL) for a failed bgw_create.
+ */
+#ifndef BGW_CHI_H
+#define BGW_CHI_H
+
+#if defined(__GNUC__)
+#define BGW_API __attribute__((visibility("default")))
+#else
+#define BGW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bgw_ctx_s *bgw_ctx;
+
+typedef enum {
+    BGW_OK = 0,
+    BGW_E_ARG = -1,      /* invalid argument (null pointer, range, shape) */
+    BGW_E_STATE = -2,    /* call out of order (e.g. k not uploaded, q-set mismatch) */
+    BGW_E_CUDA = -3,     /* a CUDA call failed; see bgw_last_error */
+    BGW_E_NOMEM = -4,    /* a device allocation failed; context unchanged */
+    BGW_E_GRID = -5,     /* a wavefunction sphere does not fit the FFT box */
+    BGW_E_TIMEOUT = -6,  /* a device-side wait gave up (bounded spin) */
+    BGW_W_ALIAS = 1      /* the box is smaller than the alias-free size for this
+                            (q, k): the result is the cyclic (box) M, exactly
+                            what the FFT route computes */
+} bgw_status;
+
+typedef enum {
+    BGW_FP64 = 0,          /* FP64 throughout: grids, FFTs, M, contraction */
+    BGW_MIXED_BF16X3 = 1   /* FP32 grids/FFTs, complex64 M, contraction as
+                              split-BF16 (3 products) on tensor cores with FP32
+                              accumulation per k, FP64 weights and FP64
+                              reduction across k */
+} bgw_precision;
+
+/* One momentum transfer with its dielectric G-sphere (the G, G' of chi0). */
+typedef struct {
+    double q[3];        /* crystal coordinates; k + q must land on the k list */
+    int ng;             /* number of G-vectors, >= 1 */
+    const int *gvec;    /* host, [ng][3] Miller indices, no duplicates */
+    int nc;             /* conduction bands used for this q, 1..nc_max */
+} bgw_q;
+
+/* Library version string (static storage). */
+BGW_API const char *bgw_version(void);
+
+/*
+ * Create a context for one k list and band layout.
+ *   fft[3]  : FFT box N1, N2, N3 (each a supported length)
+ *   nk      : number of k-points (the N_k of the 1/N_k factor)
+ *   kcrys   : host, [nk][3] crystal coordinates
+ *   nv      : occupied bands per k (bands 0..nv-1 of each upload)
+ *   nc_max  : empty bands held per k (bands nv..nv+nc_max-1)
+ *   prec    : BGW_FP64 or BGW_MIXED_BF16X3
+ *   stream  : cudaStream_t to queue all work on (NULL = default stream)
+ * Allocates the real-space grids, nk * (nv+nc_max) * 2 * N1*N2*N3 complex
+ * values (complex128 for FP64, complex64 for mixed), on the current device.
+ * Errors: BGW_E_ARG, BGW_E_NOMEM, BGW_E_CUDA.
+ */
+BGW_API bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const double *kcrys,
+                      int nv, int nc_max, bgw_precision prec, void *stream);
+
+/*
+ * Load the spinor wavefunctions of k-point ik and transform them to the
+ * real-space grid (scatter of the G-sphere into the box, inverse 3-D FFT per
+ * band and spin component; Sec. II Eq. matrix_el needs u_nk,alpha(r)).
+ *   ngw       : sphere size N_w(ik) >= 1
+ *   gvec      : HOST, [ngw][3] Miller indices of the sphere, no duplicates
+ *   coeff     : [nv+nc_max][2][ngw] complex128, band-major then spin
+ *   energy_eV : [nv+nc_max] band energies (float64)
+ *   on_device : 0 = coeff and energy_eV are host pointers (copied on the
+ *               stream); 1 = they are device pointers on this device
+ * Errors: BGW_E_ARG (range, duplicate G), BGW_E_GRID (sphere wider than the
+ * box on some axis), BGW_E_NOMEM, BGW_E_CUDA.
+ */
+BGW_API bgw_status bgw_wfn_upload(bgw_ctx ctx, int ik, int ngw, const int *gvec,
+                          const double *coeff, const double *energy_eV, int on_device);
+
+/*
+ * Matrix elements M_vc(k,q,G) (Eq. matrix_el) for valence bands v0..v0+nv-1
+ * at k = kcrys[ik] and conduction bands c0..c0+nc-1 at k+q, on q->gvec.
+ *   M_dev : caller-owned DEVICE buffer [nv][nc][q->ng], complex128 for a
+ *           BGW_FP64 context, complex64 for a mixed one
+ * The k-point ik and its partner k' must have been uploaded.
+ * Returns BGW_W_ALIAS (and the cyclic result) when the box is too small to be
+ * alias-free for this pair of spheres.  Asynchronous.
+ */
+BGW_API bgw_status bgw_mtxel_spinor(bgw_ctx ctx, const bgw_q *q, int ik, int v0, int nv,
+                            int c0, int nc, void *M_dev);
+
+/* Discard all chi0 accumulators (the next accumulate starts a new sum). */
+BGW_API bgw_status bgw_chi0_reset(bgw_ctx ctx);
+
+/*
+ * Add the contribution of k-points k_begin..k_end-1 to chi0 for each of the
+ * nq q-points at the nfreq imaginary frequencies freq_eV[j] >= 0 (the P
+ * formula, Sec. II).  Repeated calls with the same q-set and frequencies
+ * accumulate (k-chunking); a different q-set or frequency list after a call
+ * is BGW_E_STATE until bgw_chi0_reset.  The sum over k runs in index order
+ * and the result does not depend on how k is chunked.  Every k in the range
+ * and its k+q partner must have been uploaded.  Asynchronous.
+ */
+BGW_API bgw_status bgw_chi0_accumulate(bgw_ctx ctx, int nq, const bgw_q *qs, int nfreq,
+                               const double *freq_eV, int k_begin, int k_end);
+
+/*
+ * Write chi0 for q-point iq (an index into the q-set of the accumulate calls)
+ * to chi0: complex128 [nfreq][ng][ng], row G, column G' fastest, scaled by
+ * 1/N_k and Hermitian by construction.
+ *   on_device : 1 = chi0 is a device pointer (asynchronous);
+ *               0 = chi0 is a host pointer (blocks until written).
+ * The accumulators are kept (call bgw_chi0_reset to start over).
+ */
+BGW_API bgw_status bgw_chi0_finalize(bgw_ctx ctx, int iq, void *chi0, int on_device);
+
+/*
+ * Stage timing with CUDA events recorded on the context stream around each
+ * launch group.  Stages: 0 sphere->grid (bgw_wfn_upload), 1 matrix elements,
+ * 2 pair weights, 3 contraction, 4 finalize.
+ *   bgw_profile(ctx, 1) clears the totals and starts recording; 0 stops.
+ *   bgw_profile_read(ctx, ms, calls, kernels, n) fills the first n stages:
+ *   device milliseconds, launch groups and kernels launched since the last
+ *   bgw_profile(ctx, 1).  It blocks until the stream is idle.
+ */
+BGW_API bgw_status bgw_profile(bgw_ctx ctx, int enable);
+BGW_API bgw_status bgw_profile_read(bgw_ctx ctx, double *ms, long *calls, long *kernels, int n);
+
+/* Release every device buffer of the context (synchronizes its stream). */
+BGW_API void bgw_destroy(bgw_ctx ctx);
+
+/* Message of the last failing call on ctx (NULL ctx: last failed create). */
+BGW_API const char *bgw_last_error(bgw_ctx ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BGW_CHI_H */

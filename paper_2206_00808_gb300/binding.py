@@ -1,0 +1,227 @@
+"""Thin ctypes binding of libbgwchi.so (include/bgw_chi.h), same names.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch CUDA tensors (their data_ptr is passed);
+host buffers are numpy arrays or CPU tensors.  Importing this module fails
+loudly when the library has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2206_00808_gb300.build.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+BGW_OK, BGW_E_ARG, BGW_E_STATE, BGW_E_CUDA, BGW_E_NOMEM, BGW_E_GRID, BGW_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+BGW_W_ALIAS = 1
+BGW_FP64, BGW_MIXED_BF16X3 = 0, 1
+PRECISIONS = {"fp64": BGW_FP64, "mixed": BGW_MIXED_BF16X3}
+
+EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
+            "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
+            "bgw_destroy", "bgw_last_error"]
+STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize"]
+
+
+class bgw_q(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_double * 3), ("ng", ctypes.c_int), ("gvec", ctypes.c_void_p),
+                ("nc", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_lib.bgw_version.argtypes, _lib.bgw_version.restype = [], ctypes.c_char_p
+_lib.bgw_create.argtypes = [ctypes.POINTER(_P), _P, _I, _P, _I, _I, _I, _P]
+_lib.bgw_wfn_upload.argtypes = [_P, _I, _I, _P, _P, _P, _I]
+_lib.bgw_mtxel_spinor.argtypes = [_P, ctypes.POINTER(bgw_q), _I, _I, _I, _I, _I, _P]
+_lib.bgw_chi0_reset.argtypes = [_P]
+_lib.bgw_chi0_accumulate.argtypes = [_P, _I, ctypes.POINTER(bgw_q), _I, _P, _I, _I]
+_lib.bgw_chi0_finalize.argtypes = [_P, _I, _P, _I]
+_lib.bgw_profile.argtypes = [_P, _I]
+_lib.bgw_profile_read.argtypes = [_P, _P, _P, _P, _I]
+_lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
+_lib.bgw_last_error.argtypes, _lib.bgw_last_error.restype = [_P], ctypes.c_char_p
+for _f in ["bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
+           "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read"]:
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+class BgwError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"bgw status {status}: {message}")
+        self.status = status
+
+
+def _check(status: int, ctx) -> int:
+    if status < 0:
+        raise BgwError(status, bgw_last_error(ctx))
+    return status
+
+
+def _host_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _ptr_and_device(x):
+    """(pointer, on_device) for a numpy array or a torch tensor."""
+    if isinstance(x, np.ndarray):
+        return _host_ptr(x), 0
+    import torch
+    if isinstance(x, torch.Tensor):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream_handle(stream):
+    """cudaStream_t of a torch stream (None: torch's current stream when CUDA
+    is up, else the default stream)."""
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return ctypes.c_void_p(0)
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def make_q(q, gvec: np.ndarray, nc: int):
+    """A bgw_q struct plus the array that must outlive the call using it."""
+    g = np.ascontiguousarray(gvec, dtype=np.int32)
+    s = bgw_q((ctypes.c_double * 3)(*[float(x) for x in q]), len(g), _host_ptr(g), int(nc))
+    return s, g
+
+
+def bgw_version() -> str:
+    return _lib.bgw_version().decode()
+
+
+def bgw_last_error(ctx) -> str:
+    m = _lib.bgw_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def bgw_create(fft, kcrys, nv: int, nc_max: int, precision="fp64", stream=None):
+    fft = np.ascontiguousarray(fft, dtype=np.int32)
+    kc = np.ascontiguousarray(kcrys, dtype=np.float64)
+    prec = PRECISIONS.get(precision, precision)
+    ctx = ctypes.c_void_p()
+    _check(_lib.bgw_create(ctypes.byref(ctx), _host_ptr(fft), len(kc), _host_ptr(kc), nv, nc_max,
+                           prec, _stream_handle(stream)), None)
+    return ctx
+
+
+def bgw_wfn_upload(ctx, ik: int, gvec, coeff, energy) -> int:
+    """coeff complex128 [nb][2][ngw] and energy float64 [nb], both host or both device."""
+    g = np.ascontiguousarray(gvec, dtype=np.int32)
+    pc, dc = _ptr_and_device(coeff)
+    pe, de = _ptr_and_device(energy)
+    if dc != de:
+        raise ValueError("coeff and energy must both be host or both be device buffers")
+    return _check(_lib.bgw_wfn_upload(ctx, ik, len(g), _host_ptr(g), pc, pe, dc), ctx)
+
+
+def bgw_mtxel_spinor(ctx, q, gvec, ik: int, v0: int, nv: int, c0: int, nc: int, M_dev) -> int:
+    s, keep = make_q(q, gvec, nc if nc > 0 else 1)
+    pm, dm = _ptr_and_device(M_dev)
+    if not dm:
+        raise ValueError("M_dev must be a device tensor")
+    st = _lib.bgw_mtxel_spinor(ctx, ctypes.byref(s), ik, v0, nv, c0, nc, pm)
+    del keep
+    return _check(st, ctx)
+
+
+def bgw_chi0_reset(ctx) -> int:
+    return _check(_lib.bgw_chi0_reset(ctx), ctx)
+
+
+def bgw_chi0_accumulate(ctx, qs, freq, k_begin: int, k_end: int) -> int:
+    """qs: list of (q, gvec, nc)."""
+    structs, keep = [], []
+    for q, g, nc in qs:
+        s, a = make_q(q, g, nc)
+        structs.append(s)
+        keep.append(a)
+    arr = (bgw_q * len(structs))(*structs)
+    f = np.ascontiguousarray(freq, dtype=np.float64)
+    return _check(_lib.bgw_chi0_accumulate(ctx, len(structs), arr, len(f), _host_ptr(f),
+                                           k_begin, k_end), ctx)
+
+
+def bgw_chi0_finalize(ctx, iq: int, out) -> int:
+    """out: complex128 [nfreq][ng][ng], a device tensor (async) or host array (blocking)."""
+    p, d = _ptr_and_device(out)
+    return _check(_lib.bgw_chi0_finalize(ctx, iq, p, d), ctx)
+
+
+def bgw_profile(ctx, enable: bool) -> int:
+    return _check(_lib.bgw_profile(ctx, int(bool(enable))), ctx)
+
+
+def bgw_profile_read(ctx) -> dict:
+    """{stage: (device ms, launch groups, kernels)} since bgw_profile(ctx, True)."""
+    n = len(STAGES)
+    ms = np.zeros(n, dtype=np.float64)
+    calls = np.zeros(n, dtype=np.int64)
+    kern = np.zeros(n, dtype=np.int64)
+    _check(_lib.bgw_profile_read(ctx, _host_ptr(ms), _host_ptr(calls), _host_ptr(kern), n), ctx)
+    return {s: (float(ms[i]), int(calls[i]), int(kern[i])) for i, s in enumerate(STAGES)}
+
+
+def bgw_destroy(ctx) -> None:
+    _lib.bgw_destroy(ctx)
+
+
+class Chi0Context:
+    """Owns one bgw context for a synthetic Problem (marshalling helper)."""
+
+    def __init__(self, problem, precision=None, stream=None):
+        self.p = problem
+        self.precision = precision or problem.precision
+        self.ctx = bgw_create(problem.box, problem.kcrys, problem.nv, problem.nc, self.precision,
+                              stream)
+
+    def upload(self, device_inputs=None, ks=None):
+        """Upload every k (host numpy inputs, or device tensors given as a
+        list of (coeff, energy) pairs)."""
+        for ik in (range(self.p.nk) if ks is None else ks):
+            if device_inputs is None:
+                c = np.ascontiguousarray(self.p.coeff[ik])
+                e = np.ascontiguousarray(self.p.energy[ik])
+            else:
+                c, e = device_inputs[ik]
+            bgw_wfn_upload(self.ctx, ik, self.p.gvec[ik], c, e)
+
+    def qlist(self):
+        return [(q, g, nc) for q, g, nc in self.p.qs]
+
+    def accumulate(self, k_begin=0, k_end=None, freq=None):
+        return bgw_chi0_accumulate(self.ctx, self.qlist(), self.p.freq if freq is None else freq,
+                                   k_begin, self.p.nk if k_end is None else k_end)
+
+    def finalize(self, iq=0, out=None):
+        ng = len(self.p.qs[iq][1])
+        if out is None:
+            out = np.zeros((len(self.p.freq), ng, ng), dtype=np.complex128)
+        bgw_chi0_finalize(self.ctx, iq, out)
+        return out
+
+    def reset(self):
+        bgw_chi0_reset(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            bgw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

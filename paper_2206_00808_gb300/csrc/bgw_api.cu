@@ -1,0 +1,744 @@
+// C-ABI of libbgwchi.so (declared in include/bgw_chi.h): validation,
+// geometry bookkeeping and the order of kernel launches for the spinor
+// polarizability chi0_GG'(q, i omega) of arXiv:2206.00808, Sec. II.
+//
+// Data kept on the device by a context:
+//   grids  [nk][nb][2][N1*N2*N3]  real-space spinor components u_nk,alpha(r)
+//                                 (complex128 for FP64, complex64 for mixed)
+//   energy [nk][nb]               band energies, eV
+//   per q of the current q-set: gmap[ng] (position of each G in the kept
+//   cube of the pruned forward FFT) and the FP64 accumulator
+//   acc[nfreq][ng][ng] (lower block triangle filled; finalize mirrors it).
+// Scratch buffers grow on demand and are reused.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bgw_chi.h"
+#include "bgw_internal.h"
+#include "bgw_mixed.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    // Grow to at least `bytes`; old contents are not kept.  Waits for the
+    // stream first so no queued kernel still reads the old allocation.
+    cudaError_t ensure(size_t bytes, cudaStream_t st) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+            cudaFree(p);
+            p = nullptr;
+            cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        cap = bytes;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct KPoint {
+    bool uploaded = false;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // sphere extents (Miller)
+    std::vector<int> cube_map;                  // host copy of the device map
+    DevBuf map_dev;
+};
+
+struct QState {
+    double q[3];
+    int ng = 0, nc = 0;
+    std::vector<int> gvec;   // [ng][3]
+    int emin[3], emax[3];
+    int w[3];                // kept widths, min(emax - emin + 1, N)
+    std::vector<int> gmap;   // [ng]
+    DevBuf gmap_dev;
+    DevBuf acc;              // complex128 [nfreq][ng][ng]
+};
+
+bool is_supported_len(int n) {
+    static const int lens[] = {16, 18, 20, 24, 27, 30, 32, 36, 40, 48, 64};
+    for (int l : lens)
+        if (l == n) return true;
+    return false;
+}
+
+int pmod(long a, int n) {
+    long r = a % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+// Device tables (FFT twiddles) are uploaded once per device per process.
+std::mutex g_tables_mu;
+bool g_tables_done[128];
+
+cudaError_t ensure_tables(int dev) {
+    std::lock_guard<std::mutex> lk(g_tables_mu);
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    if (g_tables_done[dev]) return cudaSuccess;
+    cudaError_t e = bgw::grid_tables_init_f64();
+    if (e == cudaSuccess) e = bgw::grid_tables_init_f32();
+    if (e == cudaSuccess) g_tables_done[dev] = true;
+    return e;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct bgw_ctx_s {
+    int box[3];
+    long nbox;
+    int nk, nv, nc_max, nb;
+    std::vector<double> kcrys;
+    bgw_precision prec;
+    cudaStream_t st;
+    int device;
+    size_t csize;        // bytes per complex grid / M element
+    DevBuf grids, energy;
+    std::vector<KPoint> k;
+    DevBuf stage;        // host-uploaded coefficients
+    DevBuf S, R;         // sphere -> grid scratch
+    DevBuf A, Bs, M, W;  // mtxel scratch, M block, weights
+    DevBuf mixed_ws;     // mixed contraction workspace
+    DevBuf freq_dev;
+    DevBuf out_stage;    // finalize to host
+    DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
+    // stage timing (bgw_profile)
+    static constexpr int kStages = 5;
+    bool prof = false;
+    struct Rec { int stage; long kernels; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[kStages] = {0};
+    long prof_calls[kStages] = {0}, prof_kernels[kStages] = {0};
+    cudaEvent_t take_event() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    // Bracket a launch group; returns the index to close, or -1.
+    int stage_begin(int stage) {
+        if (!prof) return -1;
+        Rec r{stage, 0, take_event(), take_event()};
+        if (!r.a || !r.b) return -1;
+        cudaEventRecord(r.a, st);
+        recs.push_back(r);
+        return (int)recs.size() - 1;
+    }
+    void stage_end(int idx, long kernels) {
+        if (idx < 0) return;
+        recs[idx].kernels = kernels;
+        cudaEventRecord(recs[idx].b, st);
+    }
+    // Fold finished records into the totals (blocks on the stream).
+    cudaError_t drain() {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        for (auto &r : recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) prof_ms[r.stage] += ms;
+            prof_calls[r.stage] += 1;
+            prof_kernels[r.stage] += r.kernels;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+        return cudaSuccess;
+    }
+    // current q-set of the accumulators
+    bool have_qset = false;
+    int nfreq = 0;
+    std::vector<double> freq;
+    std::vector<QState> qs;
+    std::string err;
+
+    bgw_status fail(bgw_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+    bgw_status cuda_fail(cudaError_t e, const char *what) {
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? BGW_E_NOMEM : BGW_E_CUDA;
+    }
+    long grid_elems_per_k() const { return (long)nb * 2 * nbox; }
+    char *grid_of(int ik, int band) {
+        return static_cast<char *>(grids.p) + ((long)ik * grid_elems_per_k() + (long)band * 2 * nbox) * csize;
+    }
+};
+
+#include <cstdarg>
+bgw_status bgw_ctx_s::fail(bgw_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return s;
+}
+
+namespace {
+
+// k + q = k' + G0 with k' on the list (tolerance 1e-6 in crystal units).
+bool find_umklapp(const bgw_ctx_s *c, int ik, const double q[3], int &kp, int G0[3]) {
+    for (int j = 0; j < c->nk; ++j) {
+        bool ok = true;
+        int g[3];
+        for (int a = 0; a < 3; ++a) {
+            const double d = c->kcrys[3 * ik + a] + q[a] - c->kcrys[3 * j + a];
+            const double r = std::nearbyint(d);
+            if (std::fabs(d - r) > 1e-6) {
+                ok = false;
+                break;
+            }
+            g[a] = (int)r;
+        }
+        if (ok) {
+            kp = j;
+            for (int a = 0; a < 3; ++a) G0[a] = g[a];
+            return true;
+        }
+    }
+    return false;
+}
+
+// Geometry of one dielectric sphere: extents, kept widths, cube positions.
+bgw_status prepare_q(bgw_ctx_s *c, const bgw_q *q, QState &s) {
+    if (!q) return c->fail(BGW_E_ARG, "null q");
+    if (q->ng < 1 || !q->gvec) return c->fail(BGW_E_ARG, "q: ng must be >= 1 with a gvec list");
+    if (q->nc < 1 || q->nc > c->nc_max)
+        return c->fail(BGW_E_ARG, "q: nc=%d outside 1..nc_max=%d", q->nc, c->nc_max);
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(q->q[a])) return c->fail(BGW_E_ARG, "q: non-finite component");
+        s.q[a] = q->q[a];
+    }
+    s.ng = q->ng;
+    s.nc = q->nc;
+    s.gvec.assign(q->gvec, q->gvec + 3 * (long)q->ng);
+    for (int a = 0; a < 3; ++a) {
+        s.emin[a] = s.emax[a] = s.gvec[a];
+    }
+    for (int g = 0; g < s.ng; ++g)
+        for (int a = 0; a < 3; ++a) {
+            s.emin[a] = std::min(s.emin[a], s.gvec[3 * g + a]);
+            s.emax[a] = std::max(s.emax[a], s.gvec[3 * g + a]);
+        }
+    for (int a = 0; a < 3; ++a) s.w[a] = std::min(s.emax[a] - s.emin[a] + 1, c->box[a]);
+    const long cube = (long)s.w[0] * s.w[1] * s.w[2];
+    if (cube * (long)c->csize > 200 * 1024)
+        return c->fail(BGW_E_ARG, "dielectric sphere spans a %dx%dx%d cube, too wide for one block",
+                       s.w[0], s.w[1], s.w[2]);
+    s.gmap.resize(s.ng);
+    // Two G that agree mod N (an aliased sphere) share a cube cell and both
+    // read the same cyclic value, which is what the FFT route gives.
+    for (int g = 0; g < s.ng; ++g) {
+        int j[3];
+        for (int a = 0; a < 3; ++a) j[a] = pmod((long)s.gvec[3 * g + a] - s.emin[a], c->box[a]);
+        s.gmap[g] = (j[0] * s.w[1] + j[1]) * s.w[2] + j[2];
+    }
+    return BGW_OK;
+}
+
+bool same_q(const QState &s, const bgw_q *q) {
+    if (s.ng != q->ng || s.nc != q->nc) return false;
+    for (int a = 0; a < 3; ++a)
+        if (s.q[a] != q->q[a]) return false;
+    return std::equal(s.gvec.begin(), s.gvec.end(), q->gvec);
+}
+
+// Alias-free test for one (k, k+q) pair of spheres and one dielectric sphere:
+// the product density has Fourier components h2 - h1 in [dmin, dmax]; no
+// other component folds onto a G in [emin, emax] iff N > dmax - emin and
+// N > emax - dmin on every axis.
+bool alias_free(const bgw_ctx_s *c, int ik, int kp, const int G0[3], const QState &s) {
+    for (int a = 0; a < 3; ++a) {
+        const int dmin = (c->k[kp].lo[a] - G0[a]) - c->k[ik].hi[a];
+        const int dmax = (c->k[kp].hi[a] - G0[a]) - c->k[ik].lo[a];
+        if (!(c->box[a] > dmax - s.emin[a] && c->box[a] > s.emax[a] - dmin)) return false;
+    }
+    return true;
+}
+
+bgw::Axes mtxel_axes(const bgw_ctx_s *c, const QState &s, const int G0[3]) {
+    bgw::Axes ax;
+    for (int a = 0; a < 3; ++a) {
+        ax.n[a] = c->box[a];
+        ax.w[a] = s.w[a];
+        ax.s[a] = pmod((long)s.emin[a] + G0[a], c->box[a]);
+    }
+    return ax;
+}
+
+// Scratch for P pairs of one k on sphere s; M block too if want_m.
+cudaError_t ensure_mtxel_scratch(bgw_ctx_s *c, const QState &s, long P) {
+    const long n01 = (long)c->box[0] * c->box[1];
+    cudaError_t e = c->A.ensure((size_t)(P * n01 * s.w[2]) * c->csize, c->st);
+    if (e == cudaSuccess) e = c->Bs.ensure((size_t)(P * c->box[0] * s.w[1] * s.w[2]) * c->csize, c->st);
+    return e;
+}
+
+cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const int G0[3], int v0,
+                         int nv, int c0, int nc, void *M, long ldm) {
+    const bgw::Axes ax = mtxel_axes(c, s, G0);
+    const void *Uv = c->grid_of(ik, v0);
+    const void *Uc = c->grid_of(kp, c->nv + c0);
+    const int *gmap = static_cast<const int *>(s.gmap_dev.p);
+    const int rec = c->stage_begin(1);
+    cudaError_t e = (c->prec == BGW_FP64)
+        ? bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st)
+        : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st);
+    c->stage_end(rec, 3);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bgw_version(void) { return "bgwchi 0.1 (sm_103a)"; }
+
+const char *bgw_last_error(bgw_ctx ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const double *kcrys, int nv,
+                      int nc_max, bgw_precision prec, void *stream) {
+    g_create_error.clear();
+    if (!out || !fft || !kcrys) {
+        g_create_error = "bgw_create: null pointer argument";
+        return BGW_E_ARG;
+    }
+    *out = nullptr;
+    for (int a = 0; a < 3; ++a)
+        if (!is_supported_len(fft[a])) {
+            g_create_error = "bgw_create: FFT length " + std::to_string(fft[a]) +
+                             " not supported (16,18,20,24,27,30,32,36,40,48,64)";
+            return BGW_E_ARG;
+        }
+    if (nk < 1 || nv < 1 || nc_max < 1) {
+        g_create_error = "bgw_create: nk, nv and nc_max must be >= 1";
+        return BGW_E_ARG;
+    }
+    if (prec != BGW_FP64 && prec != BGW_MIXED_BF16X3) {
+        g_create_error = "bgw_create: unknown precision";
+        return BGW_E_ARG;
+    }
+    for (long i = 0; i < 3L * nk; ++i)
+        if (!std::isfinite(kcrys[i])) {
+            g_create_error = "bgw_create: non-finite k coordinate";
+            return BGW_E_ARG;
+        }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = ensure_tables(dev);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("bgw_create: ") + cudaGetErrorString(e);
+        return BGW_E_CUDA;
+    }
+    bgw_ctx_s *c = new bgw_ctx_s();
+    for (int a = 0; a < 3; ++a) c->box[a] = fft[a];
+    c->nbox = (long)fft[0] * fft[1] * fft[2];
+    c->nk = nk;
+    c->nv = nv;
+    c->nc_max = nc_max;
+    c->nb = nv + nc_max;
+    c->kcrys.assign(kcrys, kcrys + 3L * nk);
+    c->prec = prec;
+    c->st = static_cast<cudaStream_t>(stream);
+    c->device = dev;
+    c->csize = (prec == BGW_FP64) ? 16 : 8;
+    c->k.resize(nk);
+    e = c->grids.ensure((size_t)nk * c->grid_elems_per_k() * c->csize, c->st);
+    if (e == cudaSuccess) e = c->energy.ensure(sizeof(double) * (size_t)nk * c->nb, c->st);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("bgw_create: allocating grids: ") + cudaGetErrorString(e);
+        const bgw_status s = (e == cudaErrorMemoryAllocation) ? BGW_E_NOMEM : BGW_E_CUDA;
+        cudaGetLastError();
+        c->grids.release();
+        c->energy.release();
+        delete c;
+        return s;
+    }
+    *out = c;
+    return BGW_OK;
+}
+
+bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const double *coeff,
+                          const double *energy_eV, int on_device) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (ik < 0 || ik >= c->nk) return c->fail(BGW_E_ARG, "wfn_upload: ik=%d outside 0..%d", ik, c->nk - 1);
+    if (ngw < 1 || !gvec || !coeff || !energy_eV)
+        return c->fail(BGW_E_ARG, "wfn_upload: ngw >= 1 and non-null gvec, coeff, energy required");
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = gvec[a];
+    for (long i = 0; i < ngw; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], gvec[3 * i + a]);
+            hi[a] = std::max(hi[a], gvec[3 * i + a]);
+        }
+    int w[3];
+    for (int a = 0; a < 3; ++a) {
+        w[a] = hi[a] - lo[a] + 1;
+        if (w[a] > c->box[a])
+            return c->fail(BGW_E_GRID,
+                           "wfn_upload: sphere of k %d spans %d points on axis %d, box has %d",
+                           ik, w[a], a, c->box[a]);
+    }
+    std::vector<int> map((size_t)w[0] * w[1] * w[2], -1);
+    for (long i = 0; i < ngw; ++i) {
+        const long idx = ((long)(gvec[3 * i] - lo[0]) * w[1] + (gvec[3 * i + 1] - lo[1])) * w[2] +
+                         (gvec[3 * i + 2] - lo[2]);
+        if (map[idx] >= 0)
+            return c->fail(BGW_E_ARG, "wfn_upload: duplicate G (%d,%d,%d) in the sphere of k %d",
+                           gvec[3 * i], gvec[3 * i + 1], gvec[3 * i + 2], ik);
+        map[idx] = (int)i;
+    }
+    const long B = 2L * c->nb;
+    cudaError_t e;
+    KPoint &kp = c->k[ik];
+    // device copy of the cube map (only when it changed)
+    const bool map_changed = kp.cube_map != map;
+    if (map_changed) {
+        e = kp.map_dev.ensure(sizeof(int) * map.size(), c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: map buffer");
+        kp.cube_map.swap(map);
+        e = cudaMemcpyAsync(kp.map_dev.p, kp.cube_map.data(), sizeof(int) * kp.cube_map.size(),
+                            cudaMemcpyHostToDevice, c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: map copy");
+    }
+    const double *src = coeff;
+    const size_t cbytes = sizeof(double) * 2 * (size_t)B * ngw;
+    if (!on_device) {
+        e = c->stage.ensure(cbytes, c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: staging buffer");
+        e = cudaMemcpyAsync(c->stage.p, coeff, cbytes, cudaMemcpyHostToDevice, c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: coefficient copy");
+        src = static_cast<const double *>(c->stage.p);
+    }
+    e = cudaMemcpyAsync(static_cast<double *>(c->energy.p) + (long)ik * c->nb, energy_eV,
+                        sizeof(double) * c->nb,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: energy copy");
+    const size_t sbytes = (size_t)B * c->box[0] * w[1] * w[2] * c->csize;
+    const size_t rbytes = (size_t)B * c->box[0] * c->box[1] * w[2] * c->csize;
+    e = c->S.ensure(sbytes, c->st);
+    if (e == cudaSuccess) e = c->R.ensure(rbytes, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: transform scratch");
+    bgw::Axes ax;
+    for (int a = 0; a < 3; ++a) {
+        ax.n[a] = c->box[a];
+        ax.w[a] = w[a];
+        ax.s[a] = pmod(lo[a], c->box[a]);
+    }
+    void *U = c->grid_of(ik, 0);
+    const int *mp = static_cast<const int *>(kp.map_dev.p);
+    const int rec = c->stage_begin(0);
+    e = (c->prec == BGW_FP64)
+            ? bgw::wfn_to_grid_f64(src, ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st)
+            : bgw::wfn_to_grid_f32(src, ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st);
+    c->stage_end(rec, 3);
+    if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: sphere-to-grid kernels");
+    for (int a = 0; a < 3; ++a) {
+        kp.lo[a] = lo[a];
+        kp.hi[a] = hi[a];
+    }
+    kp.uploaded = true;
+    return BGW_OK;
+}
+
+bgw_status bgw_mtxel_spinor(bgw_ctx c, const bgw_q *q, int ik, int v0, int nv, int c0, int nc,
+                            void *M_dev) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (!M_dev) return c->fail(BGW_E_ARG, "mtxel: null output");
+    if (ik < 0 || ik >= c->nk) return c->fail(BGW_E_ARG, "mtxel: ik=%d out of range", ik);
+    if (nv < 0 || v0 < 0 || v0 + nv > c->nv) return c->fail(BGW_E_ARG, "mtxel: valence range");
+    if (nc < 0 || c0 < 0 || c0 + nc > c->nc_max) return c->fail(BGW_E_ARG, "mtxel: conduction range");
+    QState s;
+    bgw_status st = prepare_q(c, q, s);
+    if (st != BGW_OK) return st;
+    int kp, G0[3];
+    if (!find_umklapp(c, ik, s.q, kp, G0))
+        return c->fail(BGW_E_ARG, "mtxel: k + q is not on the k list (k %d)", ik);
+    if (!c->k[ik].uploaded || !c->k[kp].uploaded)
+        return c->fail(BGW_E_STATE, "mtxel: k %d or its partner %d not uploaded", ik, kp);
+    if (nv == 0 || nc == 0) return BGW_OK;
+    const bool clean = alias_free(c, ik, kp, G0, s);
+    const long P = (long)nv * nc;
+    cudaError_t e = ensure_mtxel_scratch(c, s, P);
+    if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: scratch");
+    // The per-call map goes to a context buffer; reuse is stream-ordered and
+    // a pageable-memory copy has read the host vector when the call returns.
+    e = c->gmap_tmp.ensure(sizeof(int) * (size_t)s.ng, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: map buffer");
+    e = cudaMemcpyAsync(c->gmap_tmp.p, s.gmap.data(), sizeof(int) * s.ng, cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: map copy");
+    s.gmap_dev.p = c->gmap_tmp.p;   // borrowed, not owned
+    e = launch_mtxel(c, s, ik, kp, G0, v0, nv, c0, nc, M_dev, s.ng);
+    s.gmap_dev.p = nullptr;
+    if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: kernels");
+    return clean ? BGW_OK : BGW_W_ALIAS;
+}
+
+bgw_status bgw_chi0_reset(bgw_ctx c) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    // The buffers stay allocated for reuse by the next q-set of the same
+    // shapes; the next accumulate zeroes them on the stream.  No host sync.
+    c->have_qset = false;
+    return BGW_OK;
+}
+
+bgw_status bgw_chi0_accumulate(bgw_ctx c, int nq, const bgw_q *qs, int nfreq,
+                               const double *freq_eV, int k_begin, int k_end) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (nq < 1 || !qs) return c->fail(BGW_E_ARG, "accumulate: nq >= 1 and a q list required");
+    if (nfreq < 1 || !freq_eV) return c->fail(BGW_E_ARG, "accumulate: nfreq >= 1 and freq required");
+    for (int j = 0; j < nfreq; ++j)
+        if (!std::isfinite(freq_eV[j]) || freq_eV[j] < 0)
+            return c->fail(BGW_E_ARG, "accumulate: frequency %d must be finite and >= 0", j);
+    if (k_begin < 0 || k_end > c->nk || k_begin > k_end)
+        return c->fail(BGW_E_ARG, "accumulate: k range [%d,%d) outside [0,%d)", k_begin, k_end, c->nk);
+    // validate every q and every (k, k+q) before touching any state
+    std::vector<QState> fresh(nq);
+    for (int iq = 0; iq < nq; ++iq) {
+        bgw_status st = prepare_q(c, &qs[iq], fresh[iq]);
+        if (st != BGW_OK) return st;
+        for (int ik = k_begin; ik < k_end; ++ik) {
+            int kp, G0[3];
+            if (!find_umklapp(c, ik, fresh[iq].q, kp, G0))
+                return c->fail(BGW_E_ARG, "accumulate: k + q not on the k list (q %d, k %d)", iq, ik);
+            if (!c->k[ik].uploaded || !c->k[kp].uploaded)
+                return c->fail(BGW_E_STATE, "accumulate: k %d or its partner %d not uploaded", ik, kp);
+        }
+    }
+    if (c->have_qset) {
+        bool same = (int)c->qs.size() == nq && c->nfreq == nfreq &&
+                    std::equal(c->freq.begin(), c->freq.end(), freq_eV);
+        for (int iq = 0; same && iq < nq; ++iq) same = same_q(c->qs[iq], &qs[iq]);
+        if (!same)
+            return c->fail(BGW_E_STATE,
+                           "accumulate: q-set or frequencies differ from the running sum; call bgw_chi0_reset");
+    }
+    // scratch sizes over the set
+    long Pmax = 0, PMbytes = 0;
+    for (auto &s : fresh) {
+        const long P = (long)c->nv * s.nc;
+        Pmax = std::max(Pmax, P);
+        PMbytes = std::max(PMbytes, P * s.ng * (long)c->csize);
+    }
+    cudaError_t e;
+    for (auto &s : fresh) {
+        e = ensure_mtxel_scratch(c, s, (long)c->nv * s.nc);
+        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: scratch");
+    }
+    e = c->M.ensure((size_t)PMbytes, c->st);
+    if (e == cudaSuccess) e = c->W.ensure(sizeof(double) * (size_t)Pmax * nfreq, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: M/weight buffers");
+    if (c->prec != BGW_FP64) {
+        size_t ws = 0;
+        for (auto &s : fresh)
+            ws = std::max(ws, bgw::mixed_workspace_bytes((long)c->nv * s.nc, s.ng, nfreq));
+        e = c->mixed_ws.ensure(ws, c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: mixed workspace");
+    }
+    if (!c->have_qset) {
+        // Reuse the previous set's buffers when every q keeps its size.
+        bool reuse = c->qs.size() == fresh.size() && c->nfreq == nfreq;
+        for (size_t i = 0; reuse && i < fresh.size(); ++i)
+            reuse = c->qs[i].ng == fresh[i].ng && c->qs[i].acc.p != nullptr;
+        if (reuse) {
+            for (size_t i = 0; i < fresh.size(); ++i) {
+                std::swap(fresh[i].gmap_dev, c->qs[i].gmap_dev);
+                std::swap(fresh[i].acc, c->qs[i].acc);
+            }
+        } else if (!c->qs.empty()) {
+            e = cudaStreamSynchronize(c->st);
+            if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: stream");
+            for (auto &s : c->qs) {
+                s.gmap_dev.release();
+                s.acc.release();
+            }
+        }
+        for (auto &s : fresh) {
+            e = s.gmap_dev.ensure(sizeof(int) * (size_t)s.ng, c->st);
+            if (e == cudaSuccess) e = s.acc.ensure(16 * (size_t)nfreq * s.ng * s.ng, c->st);
+            if (e != cudaSuccess) {
+                for (auto &t : fresh) {
+                    t.gmap_dev.release();
+                    t.acc.release();
+                }
+                c->qs.clear();
+                return c->cuda_fail(e, "accumulate: accumulators");
+            }
+        }
+        e = c->freq_dev.ensure(sizeof(double) * nfreq, c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: frequency buffer");
+        c->qs.swap(fresh);
+        c->freq.assign(freq_eV, freq_eV + nfreq);
+        c->nfreq = nfreq;
+        c->have_qset = true;
+        e = cudaMemcpyAsync(c->freq_dev.p, c->freq.data(), sizeof(double) * nfreq,
+                            cudaMemcpyHostToDevice, c->st);
+        for (auto &s : c->qs) {
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s.gmap_dev.p, s.gmap.data(), sizeof(int) * s.ng,
+                                    cudaMemcpyHostToDevice, c->st);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(s.acc.p, 0, 16 * (size_t)nfreq * s.ng * s.ng, c->st);
+        }
+        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: initialising accumulators");
+    }
+    bool clean = true;
+    const double *energy = static_cast<const double *>(c->energy.p);
+    for (int iq = 0; iq < nq; ++iq) {
+        QState &s = c->qs[iq];
+        const int P = c->nv * s.nc;
+        for (int ik = k_begin; ik < k_end; ++ik) {
+            int kp, G0[3];
+            find_umklapp(c, ik, s.q, kp, G0);
+            clean = clean && alias_free(c, ik, kp, G0, s);
+            e = launch_mtxel(c, s, ik, kp, G0, 0, c->nv, 0, s.nc, c->M.p, s.ng);
+            if (e == cudaSuccess) {
+                const int rec = c->stage_begin(2);
+                e = bgw::pair_weights(energy + (long)ik * c->nb, energy + (long)kp * c->nb + c->nv,
+                                      c->nv, s.nc, static_cast<const double *>(c->freq_dev.p),
+                                      nfreq, static_cast<double *>(c->W.p), c->st);
+                c->stage_end(rec, 1);
+            }
+            if (e == cudaSuccess) {
+                const int rec = c->stage_begin(3);
+                int nkern = 1;
+                if (c->prec == BGW_FP64)
+                    e = bgw::herk_f64(c->M.p, P, s.ng, static_cast<const double *>(c->W.p), nfreq,
+                                      s.acc.p, c->st);
+                else
+                    e = bgw::herk_mixed(c->M.p, P, s.ng, static_cast<const double *>(c->W.p), nfreq,
+                                        c->mixed_ws.p, s.acc.p, c->st, &nkern);
+                c->stage_end(rec, nkern);
+            }
+            if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: kernels");
+        }
+    }
+    return clean ? BGW_OK : BGW_W_ALIAS;
+}
+
+bgw_status bgw_chi0_finalize(bgw_ctx c, int iq, void *chi0, int on_device) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (!chi0) return c->fail(BGW_E_ARG, "finalize: null output");
+    if (!c->have_qset) return c->fail(BGW_E_STATE, "finalize: nothing accumulated");
+    if (iq < 0 || iq >= (int)c->qs.size()) return c->fail(BGW_E_ARG, "finalize: iq=%d out of range", iq);
+    QState &s = c->qs[iq];
+    const size_t bytes = 16 * (size_t)c->nfreq * s.ng * s.ng;
+    const double scale = 1.0 / c->nk;
+    cudaError_t e;
+    if (on_device) {
+        const int rec = c->stage_begin(4);
+        e = bgw::chi0_finalize(s.acc.p, s.ng, c->nfreq, scale, chi0, c->st);
+        c->stage_end(rec, 1);
+        if (e != cudaSuccess) return c->cuda_fail(e, "finalize: kernel");
+        return BGW_OK;
+    }
+    e = c->out_stage.ensure(bytes, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "finalize: staging");
+    const int rec = c->stage_begin(4);
+    e = bgw::chi0_finalize(s.acc.p, s.ng, c->nfreq, scale, c->out_stage.p, c->st);
+    c->stage_end(rec, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(chi0, c->out_stage.p, bytes, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "finalize: copy to host");
+    return BGW_OK;
+}
+
+bgw_status bgw_profile(bgw_ctx c, int enable) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    cudaError_t e = c->drain();
+    if (e != cudaSuccess) return c->cuda_fail(e, "profile: stream");
+    if (enable) {
+        for (int i = 0; i < bgw_ctx_s::kStages; ++i) {
+            c->prof_ms[i] = 0;
+            c->prof_calls[i] = c->prof_kernels[i] = 0;
+        }
+    }
+    c->prof = enable != 0;
+    return BGW_OK;
+}
+
+bgw_status bgw_profile_read(bgw_ctx c, double *ms, long *calls, long *kernels, int n) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (n < 0 || n > bgw_ctx_s::kStages) return c->fail(BGW_E_ARG, "profile_read: n outside 0..5");
+    cudaError_t e = c->drain();
+    if (e != cudaSuccess) return c->cuda_fail(e, "profile_read: stream");
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = c->prof_ms[i];
+        if (calls) calls[i] = c->prof_calls[i];
+        if (kernels) kernels[i] = c->prof_kernels[i];
+    }
+    return BGW_OK;
+}
+
+void bgw_destroy(bgw_ctx c) {
+    if (!c) return;
+    {
+        DeviceGuard dg(c->device);
+        cudaStreamSynchronize(c->st);
+        for (auto &r : c->recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto ev : c->pool) cudaEventDestroy(ev);
+        for (auto &k : c->k) k.map_dev.release();
+        for (auto &s : c->qs) {
+            s.gmap_dev.release();
+            s.acc.release();
+        }
+        DevBuf *bufs[] = {&c->grids, &c->energy, &c->stage, &c->S,  &c->R,        &c->A,
+                          &c->Bs,    &c->M,      &c->W,     &c->mixed_ws, &c->freq_dev, &c->out_stage, &c->gmap_tmp};
+        for (DevBuf *b : bufs) b->release();
+    }
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+// In-register mixed-radix FFT of one line per thread, for the short box
+// lengths of plane-wave codes (products of 2, 3 and 5 up to 64).
+//
+// The transform of Eq. (matrix_el) of arXiv:2206.00808 is a 3-D DFT; it is
+// done here one axis at a time, each line held in the registers of one
+// thread.  Lengths are compile-time, so every index below is a constant and
+// the arrays stay in registers.
+//
+// Decomposition (Cooley-Tukey, decimation in time): N = R * M with
+// n = R*n2 + n1 and k = k1 + M*k2,
+//   X[k1 + M k2] = sum_{n1} w_R^{n1 k2} [ w_N^{n1 k1} (sum_{n2} x[R n2 + n1] w_M^{n2 k1}) ],
+// i.e. R sub-transforms of length M, a twiddle, then M transforms of length R.
+// w_N = exp(S * 2 pi i / N): S = -1 forward (e^{-iG.r}), S = +1 inverse.
+//
+// Twiddles are exp(-2 pi i j / N) for every supported N, computed on the
+// host in double precision (std::cos / std::sin) and kept in constant memory
+// (one table per translation unit; bgw_fft_upload_tables fills it).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bgw {
+
+template <typename T> struct cpx { T x, y; };
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) { return {a.x * s, a.y * s}; }
+// conj(a) * b
+template <typename T>
+__device__ __forceinline__ cpx<T> cconjmul(cpx<T> a, cpx<T> b) {
+    return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+}
+
+// ----------------------------------------------------------- twiddle tables --
+constexpr int kFftLens[] = {16, 18, 20, 24, 27, 30, 32, 36, 40, 48, 64};
+constexpr int kNumFftLens = sizeof(kFftLens) / sizeof(int);
+
+__host__ __device__ constexpr int tw_offset(int n) {
+    // running sum of the lengths listed in kFftLens before n
+    return n == 16 ? 0 : n == 18 ? 16 : n == 20 ? 34 : n == 24 ? 54 : n == 27 ? 78
+         : n == 30 ? 105 : n == 32 ? 135 : n == 36 ? 167 : n == 40 ? 203 : n == 48 ? 243
+         : n == 64 ? 291 : -1;
+}
+constexpr int kTwTotal = tw_offset(64) + 64;
+
+__host__ __device__ constexpr bool fft_len_supported(int n) { return tw_offset(n) >= 0; }
+
+// Forward roots w^j = exp(-2 pi i j / N); j-th entry of length N at tw_offset(N).
+static __constant__ double2 c_tw64[kTwTotal];
+static __constant__ float2 c_tw32[kTwTotal];
+
+template <typename T> struct Tw;
+template <> struct Tw<double> {
+    static __device__ __forceinline__ cpx<double> at(int i) {
+        double2 v = c_tw64[i];
+        return {v.x, v.y};
+    }
+};
+template <> struct Tw<float> {
+    static __device__ __forceinline__ cpx<float> at(int i) {
+        float2 v = c_tw32[i];
+        return {v.x, v.y};
+    }
+};
+
+// exp(-2 pi i j / NTOP) with runtime j in [0, NTOP) (warp-uniform j is cheap).
+template <typename T, int NTOP>
+__device__ __forceinline__ cpx<T> root_fwd(int j) {
+    return Tw<T>::at(tw_offset(NTOP) + j);
+}
+// exp(+2 pi i j / NTOP)
+template <typename T, int NTOP>
+__device__ __forceinline__ cpx<T> root_inv(int j) {
+    cpx<T> w = Tw<T>::at(tw_offset(NTOP) + j);
+    return {w.x, -w.y};
+}
+
+// Multiply by w_N^E (w_N = exp(S 2 pi i / N)) with E a compile-time exponent;
+// the table of the top-level length NTOP serves every sub-length N | NTOP.
+template <typename T, int S, int N, int NTOP, int E>
+__device__ __forceinline__ cpx<T> twiddle(cpx<T> a) {
+    constexpr int e = E % N;
+    if constexpr (e == 0) {
+        return a;
+    } else if constexpr (2 * e == N) {
+        return {-a.x, -a.y};
+    } else if constexpr (4 * e == N) {        // w = S i
+        return {-(T)S * a.y, (T)S * a.x};
+    } else if constexpr (4 * e == 3 * N) {    // w = -S i
+        return {(T)S * a.y, -(T)S * a.x};
+    } else {
+        cpx<T> w = Tw<T>::at(tw_offset(NTOP) + e * (NTOP / N));
+        if constexpr (S > 0) w.y = -w.y;
+        return cmul(a, w);
+    }
+}
+
+__host__ __device__ constexpr int first_radix(int n) {
+    return (n % 4 == 0) ? 4 : (n % 2 == 0) ? 2 : (n % 3 == 0) ? 3 : (n % 5 == 0) ? 5 : n;
+}
+
+// Length-R DFT in place, R in {2, 3, 4, 5}.
+template <typename T, int S, int R, int NTOP>
+__device__ __forceinline__ void dft_small(cpx<T> (&a)[R]) {
+    if constexpr (R == 2) {
+        cpx<T> t = a[0];
+        a[0] = cadd(t, a[1]);
+        a[1] = csub(t, a[1]);
+    } else if constexpr (R == 4) {
+        cpx<T> t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+        cpx<T> t2 = cadd(a[1], a[3]), d = csub(a[1], a[3]);
+        cpx<T> t3 = {-(T)S * d.y, (T)S * d.x};   // (a1 - a3) * (S i)
+        a[0] = cadd(t0, t2);
+        a[2] = csub(t0, t2);
+        a[1] = cadd(t1, t3);
+        a[3] = csub(t1, t3);
+    } else if constexpr (R == 3) {
+        // w_3 = -1/2 + S i sqrt(3)/2
+        constexpr T h = (T)0.86602540378443864676372317075293618;
+        cpx<T> t1 = cadd(a[1], a[2]), t2 = csub(a[1], a[2]);
+        cpx<T> m = {a[0].x - (T)0.5 * t1.x, a[0].y - (T)0.5 * t1.y};
+        cpx<T> r = {-(T)S * h * t2.y, (T)S * h * t2.x};   // S i (sqrt3/2) t2
+        a[0] = cadd(a[0], t1);
+        a[1] = cadd(m, r);
+        a[2] = csub(m, r);
+    } else {
+        static_assert(R == 5, "radix");
+        cpx<T> x[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) x[k] = a[k];
+        // direct 5-point sum with table roots (w_5^j = w_NTOP^{j NTOP/5})
+        a[0] = cadd(cadd(cadd(x[0], x[1]), cadd(x[2], x[3])), x[4]);
+#pragma unroll
+        for (int k = 1; k < 5; ++k) {
+            cpx<T> s = x[0];
+#pragma unroll
+            for (int n = 1; n < 5; ++n) {
+                const int e = (n * k) % 5;
+                cpx<T> w = Tw<T>::at(tw_offset(NTOP) + e * (NTOP / 5));
+                if (S > 0) w.y = -w.y;
+                s = cadd(s, cmul(x[n], w));
+            }
+            a[k] = s;
+        }
+    }
+}
+
+template <typename T, int S, int N, int NTOP>
+struct Fft {
+    static constexpr int R = first_radix(N);
+    static constexpr int M = N / R;
+
+    // sub[n1][k1] *= w_N^{n1 k1}, unrolled at compile time over (n1, k1).
+    template <int N1, int K1>
+    __device__ __forceinline__ static void stage_twiddle(cpx<T> (&sub)[R][M]) {
+        if constexpr (N1 < R) {
+            if constexpr (K1 < M) {
+                sub[N1][K1] = twiddle<T, S, N, NTOP, N1 * K1>(sub[N1][K1]);
+                stage_twiddle<N1, K1 + 1>(sub);
+            } else {
+                stage_twiddle<N1 + 1, 0>(sub);
+            }
+        }
+    }
+
+    __device__ __forceinline__ static void run(cpx<T> (&a)[N]) {
+        if constexpr (M == 1) {
+            dft_small<T, S, R, NTOP>(a);
+        } else {
+            cpx<T> sub[R][M];
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1)
+#pragma unroll
+                for (int n2 = 0; n2 < M; ++n2) sub[n1][n2] = a[R * n2 + n1];
+#pragma unroll
+            for (int n1 = 0; n1 < R; ++n1) Fft<T, S, M, NTOP>::run(sub[n1]);
+            stage_twiddle<1, 0>(sub);
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1) {
+                cpx<T> t[R];
+#pragma unroll
+                for (int n1 = 0; n1 < R; ++n1) t[n1] = sub[n1][k1];
+                dft_small<T, S, R, NTOP>(t);
+#pragma unroll
+                for (int k2 = 0; k2 < R; ++k2) a[k1 + M * k2] = t[k2];
+            }
+        }
+    }
+};
+
+// Forward (S = -1) or inverse (S = +1) unnormalised DFT of length N.
+template <typename T, int S, int N>
+__device__ __forceinline__ void fft_line(cpx<T> (&a)[N]) {
+    static_assert(fft_len_supported(N), "unsupported FFT length");
+    Fft<T, S, N, N>::run(a);
+}
+
+}  // namespace bgw

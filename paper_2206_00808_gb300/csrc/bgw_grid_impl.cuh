@@ -1,0 +1,269 @@
+// Real-space grids and matrix elements (the FFT route of Eq. matrix_el,
+// arXiv:2206.00808 Sec. II), one template for FP64 and FP32.
+//
+// Included once per precision by bgw_grid_f64.cu / bgw_grid_f32.cu with
+// BGW_REAL and BGW_SUFFIX defined.
+//
+// Both 3-D transforms are done one axis at a time, one line per thread, with
+// pruning on the side where most of the box is empty:
+//   sphere -> grid (inverse, u(r) = sum_h c(h) e^{+2 pi i h.r/N}): only the
+//     lines that meet the sphere's bounding cube are transformed along x,
+//     then along y, then along z (cube w0*w1*w2 -> n0*w1*w2 -> n0*n1*w2 -> n0*n1*n2);
+//   pair density -> M (forward, e^{-2 pi i f.r/N}): z first on all n0*n1
+//     lines, keeping the w2 needed outputs, then y keeping w1, then x keeping
+//     w0, then a gather of the dielectric sphere from the kept cube.
+// A cube that starts at index s (not 0) is handled by a phase: an input
+// placed at s + j picks up e^{+2 pi i s x/N} after the inverse transform; the
+// outputs s + j of a forward transform are the outputs j of the input
+// multiplied by e^{-2 pi i s z/N}.  The phases come from the twiddle table
+// with a warp-uniform index, so no register array is indexed at run time.
+#pragma once
+#include <cmath>
+#include <vector>
+
+#include "bgw_fft.cuh"
+#include "bgw_internal.h"
+
+namespace bgw {
+
+namespace BGW_SUFFIX {
+
+using T = BGW_REAL;
+using C = cpx<T>;
+
+constexpr int kLineThreads = 128;
+
+// ---------------------------------------------------------------- tables --
+static cudaError_t upload_tables() {
+    std::vector<double2> t64(kTwTotal);
+    std::vector<float2> t32(kTwTotal);
+    for (int i = 0; i < kNumFftLens; ++i) {
+        const int n = kFftLens[i];
+        const int off = tw_offset(n);
+        for (int j = 0; j < n; ++j) {
+            // exp(-2 pi i j / n); exact values where the angle is a multiple of pi/4
+            const double ang = -2.0 * 3.14159265358979323846264338327950288 * (double)j / (double)n;
+            double c = std::cos(ang), s = std::sin(ang);
+            if ((8 * j) % n == 0) {
+                const int o = (8 * j) / n;   // multiple of pi/4
+                const double r = 0.70710678118654752440084436210484904;
+                const double cs[8] = {1, r, 0, -r, -1, -r, 0, r};
+                const double sn[8] = {0, -r, -1, -r, 0, r, 1, r};
+                c = cs[o];
+                s = sn[o];
+            }
+            t64[off + j] = make_double2(c, s);
+            t32[off + j] = make_float2((float)c, (float)s);
+        }
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_tw64, t64.data(), sizeof(double2) * kTwTotal);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_tw32, t32.data(), sizeof(float2) * kTwTotal);
+}
+
+// ------------------------------------------------------ sphere -> grid --
+// Pass x: one thread per (band component b, y', z') line of the cube.
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k1_xpass(const double2 *__restrict__ coeff, int ngw, long B, const int *__restrict__ cube_map,
+         int w0, int w1, int w2, int s0, C *__restrict__ S) {
+    const long yzs = (long)w1 * w2;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * yzs) return;
+    const long yz = t % yzs;
+    const long b = t / yzs;
+    C a[N];
+#pragma unroll
+    for (int x = 0; x < N; ++x) {
+        C v = {T(0), T(0)};
+        if (x < w0) {
+            const int idx = __ldg(cube_map + x * yzs + yz);
+            if (idx >= 0) {
+                const double2 c = __ldg(coeff + b * ngw + idx);
+                v = {(T)c.x, (T)c.y};
+            }
+        }
+        a[x] = v;
+    }
+    fft_line<T, +1, N>(a);
+    C *out = S + b * N * yzs + yz;
+#pragma unroll
+    for (int x = 0; x < N; ++x) out[x * yzs] = cmul(a[x], root_inv<T, N>((s0 * x) % N));
+}
+
+// Pass y: one thread per (b, x, z') line; input rows y' < w1 of S.
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k1_ypass(const C *__restrict__ S, long nbx, int w1, int w2, int s1, C *__restrict__ R) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nbx * w2) return;
+    const long z = t % w2;
+    const long bx = t / w2;
+    C a[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) a[y] = (y < w1) ? S[(bx * w1 + y) * w2 + z] : C{T(0), T(0)};
+    fft_line<T, +1, N>(a);
+#pragma unroll
+    for (int y = 0; y < N; ++y) R[(bx * N + y) * w2 + z] = cmul(a[y], root_inv<T, N>((s1 * y) % N));
+}
+
+// Pass z: one thread per (b, x, y) line; writes full grid lines.
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k1_zpass(const C *__restrict__ R, long nbxy, int w2, int s2, C *__restrict__ U) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nbxy) return;
+    C a[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) a[z] = (z < w2) ? R[t * w2 + z] : C{T(0), T(0)};
+    fft_line<T, +1, N>(a);
+#pragma unroll
+    for (int z = 0; z < N; ++z) U[t * N + z] = cmul(a[z], root_inv<T, N>((s2 * z) % N));
+}
+
+// ------------------------------------------------ pair density -> M --
+// Pass z: one thread per (pair p, x, y): rho(z) = sum_alpha conj(u_v) u_c,
+// forward transform along z, keep outputs s2 .. s2+w2-1.
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k2_zpass(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, long plane, int w2,
+         int s2, C *__restrict__ A) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P * plane) return;
+    const long xy = t % plane;
+    const long p = t / plane;
+    const long v = p / nc, c = p % nc;
+    const long vol = plane * N;
+    const C *v0 = Uv + (2 * v) * vol + xy * N;
+    const C *c0 = Uc + (2 * c) * vol + xy * N;
+    C a[N];
+#pragma unroll
+    for (int z = 0; z < N; ++z) {
+        const C r0 = cconjmul(v0[z], c0[z]);
+        const C r1 = cconjmul(v0[vol + z], c0[vol + z]);
+        a[z] = cmul(cadd(r0, r1), root_fwd<T, N>((s2 * z) % N));
+    }
+    fft_line<T, -1, N>(a);
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (j < w2) A[t * w2 + j] = a[j];
+}
+
+// Pass y: one thread per (p, x, j2); keep outputs s1 .. s1+w1-1.
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k2_ypass(const C *__restrict__ A, long npx, int w1, int w2, int s1, C *__restrict__ Bs) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npx * w2) return;
+    const long jz = t % w2;
+    const long px = t / w2;
+    C a[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) a[y] = cmul(A[(px * N + y) * w2 + jz], root_fwd<T, N>((s1 * y) % N));
+    fft_line<T, -1, N>(a);
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (j < w1) Bs[(px * w1 + j) * w2 + jz] = a[j];
+}
+
+// Pass x + gather: one block per pair; the kept w0*w1*w2 cube goes to shared
+// memory, then M[p][g] = cube[gmap[g]] / N^3.
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k2_xpass_gather(const C *__restrict__ Bs, int w0, int w1, int w2, int s0,
+                const int *__restrict__ gmap, int ng, T scale, C *__restrict__ M, long ldm) {
+    extern __shared__ unsigned char smem_raw[];
+    C *cube = reinterpret_cast<C *>(smem_raw);
+    const long p = blockIdx.x;
+    const int lines = w1 * w2;
+    for (int l = threadIdx.x; l < lines; l += blockDim.x) {
+        C a[N];
+#pragma unroll
+        for (int x = 0; x < N; ++x)
+            a[x] = cmul(Bs[(p * N + x) * lines + l], root_fwd<T, N>((s0 * x) % N));
+        fft_line<T, -1, N>(a);
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < w0) cube[j * lines + l] = a[j];
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        const C v = cube[__ldg(gmap + g)];
+        M[p * ldm + g] = C{v.x * scale, v.y * scale};
+    }
+}
+
+// -------------------------------------------------------------- launch --
+static inline unsigned blocks_for(long n) { return (unsigned)((n + kLineThreads - 1) / kLineThreads); }
+
+#define BGW_FOR_EACH_LEN(n, ...)                                                        \
+    switch (n) {                                                                         \
+        case 16: { constexpr int N = 16; __VA_ARGS__; } break;                                  \
+        case 18: { constexpr int N = 18; __VA_ARGS__; } break;                                  \
+        case 20: { constexpr int N = 20; __VA_ARGS__; } break;                                  \
+        case 24: { constexpr int N = 24; __VA_ARGS__; } break;                                  \
+        case 27: { constexpr int N = 27; __VA_ARGS__; } break;                                  \
+        case 30: { constexpr int N = 30; __VA_ARGS__; } break;                                  \
+        case 32: { constexpr int N = 32; __VA_ARGS__; } break;                                  \
+        case 36: { constexpr int N = 36; __VA_ARGS__; } break;                                  \
+        case 40: { constexpr int N = 40; __VA_ARGS__; } break;                                  \
+        case 48: { constexpr int N = 48; __VA_ARGS__; } break;                                  \
+        case 64: { constexpr int N = 64; __VA_ARGS__; } break;                                  \
+        default: return cudaErrorInvalidValue;                                           \
+    }
+
+static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *cube_map,
+                               const Axes &a, void *S, void *R, void *U, cudaStream_t st) {
+    const long nb = B;
+    C *Sp = static_cast<C *>(S), *Rp = static_cast<C *>(R), *Up = static_cast<C *>(U);
+    const double2 *cf = reinterpret_cast<const double2 *>(coeff);
+    {
+        const long lines = nb * a.w[1] * a.w[2];
+        BGW_FOR_EACH_LEN(a.n[0], (k1_xpass<N><<<blocks_for(lines), kLineThreads, 0, st>>>(
+                                     cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
+    }
+    {
+        const long nbx = nb * a.n[0];
+        BGW_FOR_EACH_LEN(a.n[1], (k1_ypass<N><<<blocks_for(nbx * a.w[2]), kLineThreads, 0, st>>>(
+                                     Sp, nbx, a.w[1], a.w[2], a.s[1], Rp)));
+    }
+    {
+        const long nbxy = nb * a.n[0] * a.n[1];
+        BGW_FOR_EACH_LEN(a.n[2], (k1_zpass<N><<<blocks_for(nbxy), kLineThreads, 0, st>>>(
+                                     Rp, nbxy, a.w[2], a.s[2], Up)));
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
+                         const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
+                         cudaStream_t st) {
+    const long P = (long)nv * nc;
+    if (P == 0) return cudaSuccess;
+    const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
+    C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
+    const long plane = (long)a.n[0] * a.n[1];
+    BGW_FOR_EACH_LEN(a.n[2], (k2_zpass<N><<<blocks_for(P * plane), kLineThreads, 0, st>>>(
+                                 uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
+    const long npx = P * a.n[0];
+    BGW_FOR_EACH_LEN(a.n[1], (k2_ypass<N><<<blocks_for(npx * a.w[2]), kLineThreads, 0, st>>>(
+                                 Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
+    const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
+    const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
+    cudaError_t e = cudaSuccess;
+    BGW_FOR_EACH_LEN(a.n[0], {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k2_xpass_gather<N><<<(unsigned)P, kLineThreads, smem, st>>>(
+            Bp, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
+    });
+    return cudaGetLastError();
+}
+
+#undef BGW_FOR_EACH_LEN
+
+}  // namespace BGW_SUFFIX
+}  // namespace bgw

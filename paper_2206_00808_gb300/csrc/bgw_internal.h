@@ -1,0 +1,58 @@
+// Internal launchers shared by the C-ABI layer (bgw_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bgw {
+
+// Extents of a pruned transform along the three box axes.
+struct Axes {
+    int n[3];   // FFT box N1, N2, N3
+    int w[3];   // kept (or occupied) width along each axis, 1 <= w <= n
+    int s[3];   // start index along each axis (mod n), 0 <= s < n
+};
+
+// ---- bgw_grid_f64.cu / bgw_grid_f32.cu (T = double / float) -------------
+// Twiddle tables into this translation unit's constant memory (per device).
+cudaError_t grid_tables_init_f64();
+cudaError_t grid_tables_init_f32();
+
+// Sphere -> real space for B = 2*nb band components of one k:
+//   u_b(r) = sum_{h in sphere} c_b(h) e^{+2 pi i h.r / N}
+// coeff: complex128 [B][ngw]; cube_map: [w0][w1][w2] -> coefficient index or
+// -1 (cube origin at Miller index s, i.e. a.s = sphere minimum); S: [B][n0][w1][w2],
+// R: [B][n0][n1][w2] scratch of T-complex; U: [B][n0][n1][n2] T-complex.
+cudaError_t wfn_to_grid_f64(const double *coeff, int ngw, int B, const int *cube_map,
+                            const Axes &a, void *S, void *R, void *U, cudaStream_t st);
+cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube_map,
+                            const Axes &a, void *S, void *R, void *U, cudaStream_t st);
+
+// Pair density, pruned forward FFT and gather for P = nv*nc pairs of one k:
+//   M[v*nc+c][g] = N^-3 sum_r sum_alpha conj(u_v,alpha(r)) u_c,alpha(r) e^{-2 pi i f_g.r/N}
+// with f_g the output frequency of G-vector g (G + G0).  Uv: [nv][2][N^3],
+// Uc: [nc][2][N^3] (T-complex); a.s = first kept frequency per axis,
+// a.w = kept widths; gmap[g] = j0*w1*w2 + j1*w2 + j2 (position in the kept
+// cube); A: [P][n0][n1][w2], Bs: [P][n0][w1][w2] scratch; M row stride ldm.
+cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
+                      const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
+                      cudaStream_t st);
+cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
+                      const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
+                      cudaStream_t st);
+
+// ---- bgw_chi0_f64.cu ------------------------------------------------------
+// w[j][v*nc+c] = 2D/(D^2 + freq_j^2), D = ev[v] - ec[c] (the bracket of the
+// polarizability at w -> i w, eta -> 0).
+cudaError_t pair_weights(const double *ev, const double *ec, int nv, int nc,
+                         const double *freq, int nfreq, double *w, cudaStream_t st);
+
+// acc[j][g][g'] += sum_p w[j][p] conj(M[p][g]) M[p][g'] on the lower block
+// triangle (FP64 throughout).  M: complex128 [P][ng].
+cudaError_t herk_f64(const void *M, int P, int ng, const double *w, int nfreq, void *acc,
+                     cudaStream_t st);
+
+// out[j][g][g'] = scale * (g >= g' ? acc[j][g][g'] : conj(acc[j][g'][g])).
+cudaError_t chi0_finalize(const void *acc, int ng, int nfreq, double scale, void *out,
+                          cudaStream_t st);
+
+}  // namespace bgw

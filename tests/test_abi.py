@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every symbol include/*.h
+declares; argument checks that run before any CUDA call reject bad input.
+No GPU is used here."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2206_00808_gb300 import build
+    build.build()
+    from paper_2206_00808_gb300 import binding
+    return binding
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names |= set(re.findall(r"BGW_API\s+[\w\s\*]+?\b(bgw_\w+)\s*\(", text))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ["bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_accumulate", "bgw_chi0_finalize",
+              "bgw_create", "bgw_destroy", "bgw_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import ctypes
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for n in declared_symbols():
+        assert hasattr(so, n), n
+    assert set(lib.EXPORTED) == declared_symbols()
+
+
+def test_version_string(lib):
+    assert "sm_103a" in lib.bgw_version()
+
+
+@pytest.mark.parametrize("fft, msg", [((16, 17, 16), "not supported"), ((0, 16, 16), "not supported")])
+def test_create_rejects_unsupported_box(lib, fft, msg):
+    with pytest.raises(lib.BgwError) as e:
+        lib.bgw_create(fft, np.zeros((1, 3)), 1, 1, "fp64")
+    assert e.value.status == lib.BGW_E_ARG and msg in str(e.value)
+
+
+def test_create_rejects_bad_counts_and_precision(lib):
+    with pytest.raises(lib.BgwError) as e:
+        lib.bgw_create((16, 16, 16), np.zeros((1, 3)), 0, 1, "fp64")
+    assert e.value.status == lib.BGW_E_ARG
+    with pytest.raises(lib.BgwError) as e:
+        lib.bgw_create((16, 16, 16), np.zeros((1, 3)), 2, 2, 7)
+    assert e.value.status == lib.BGW_E_ARG
+    with pytest.raises(lib.BgwError) as e:
+        lib.bgw_create((16, 16, 16), np.array([[np.nan, 0, 0]]), 2, 2, "fp64")
+    assert e.value.status == lib.BGW_E_ARG
+
+
+def test_null_context_calls_are_rejected(lib):
+    import ctypes
+    so = lib._lib
+    assert so.bgw_chi0_reset(None) == lib.BGW_E_ARG
+    assert so.bgw_chi0_finalize(None, 0, None, 0) == lib.BGW_E_ARG
+    so.bgw_destroy(None)
