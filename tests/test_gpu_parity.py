@@ -149,9 +149,11 @@ def test_device_resident_inputs_match_host_inputs(gpu_lib, torch_cuda, problems)
 
 
 def test_aliased_box_warns_and_matches_cyclic_oracle(gpu_lib):
-    """q = (1/2,0,0) needs an 18-box; on a 16-box the library warns and
-    returns the cyclic (box) result, which the oracle defines too."""
-    p = syn.make_problem("si18_qx", box=(16, 16, 16))
+    """A 400-vector eps sphere (extent -5..5) with wavefunction spheres of
+    extent -6..6 and an umklapp needs a box of at least 19; on a 16-box the
+    library warns and returns the cyclic (box) result, which the oracle
+    defines too."""
+    p = syn.make_problem("si18_qx", box=(16, 16, 16), ng=400)
     ref = oracle.chi0(p)
     ctx = gpu_lib.Chi0Context(p, "fp64")
     ctx.upload()
