@@ -28,9 +28,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "si24"
-WORKLOAD_DESC = ("Si-like FCC a=10.26 bohr, 24^3 box, N_w~2000 per spinor component, N_G=350, "
-                 "N_k=64 (4x4x4), N_v=8, N_c=200, 5 imaginary freqs (0..40 eV), q=(1/4,0,0)")
+WORKLOADS = {
+    "si24": (dict(), "Si-like FCC a=10.26 bohr, 24^3 box, N_w~2000 per spinor component, N_G=350, "
+             "N_k=64 (4x4x4), N_v=8, N_c=200, 5 imaginary freqs (0..40 eV), q=(1/4,0,0)"),
+    # profiling case: the same per-launch shapes on a 2x2x2 k-grid (< 1 GB on the device)
+    "si24_small": (dict(kgrid=(2, 2, 2), q=(0.5, 0, 0)),
+                   "si24 shapes (24^3, N_G=350, N_v=8, N_c=200, 5 freqs) on a 2x2x2 k-grid, q=(1/2,0,0)"),
+}
 METRIC = "spinor chi0 q-points/s and TFLOP/s, FP64 vs mixed at ≤2e-5 rel. Frobenius error"
 
 # FP64 issue rate of GB300 derived from its nominal 1.25 TFLOP/s over 152 SMs
@@ -53,6 +57,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")
     return ap.parse_args()
 
 
@@ -190,11 +195,16 @@ def cpu_baseline(p):
 
 # ------------------------------------------------------------------ arms --
 
+def make_workload(name):
+    from paper_2206_00808_gb300 import synthetic as syn
+    over, desc = WORKLOADS[name]
+    return syn.make_problem("si24", **over), desc
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    from paper_2206_00808_gb300 import synthetic as syn
-    p = syn.make_problem(WORKLOAD)
+    p, desc = make_workload(args.workload)
     for _ in range(args.warmup and 1):
         oracle_sample(p, [0])
     times = []
@@ -208,7 +218,7 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD_DESC, "precision": "fp64"},
+            "config": {"workload": desc, "precision": "fp64"},
             "cpu_baseline": {"value": value, "unit": "q-points/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: 1 of {p.nk} k-points, scaled x{p.nk}"},
             "e2e": {"value": value, "unit": "q-points/s", "h2d_bytes_per_step": 0,
@@ -224,9 +234,8 @@ def run_ours(args, world, rank, local):
     from paper_2206_00808_gb300 import build
     build.build()
     from paper_2206_00808_gb300 import binding as B
-    from paper_2206_00808_gb300 import synthetic as syn
 
-    p = syn.make_problem(WORKLOAD)
+    p, desc = make_workload(args.workload)
     q, geps, nc = p.qs[0]
     ng, nf = len(geps), len(p.freq)
     stream = torch.cuda.current_stream()
@@ -313,7 +322,7 @@ def run_ours(args, world, rank, local):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "f32+bf16x3",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD_DESC, "precision": args.precision,
+                "config": {"workload": desc, "precision": args.precision,
                            "pairs_per_q": p.pairs(), "l2": "inputs larger than L2 (coefficients "
                            f"{sum(c.nbytes for c in p.coeff) / 1e9:.2f} GB, grids resident per step)"},
                 "tflops": fl["total"] / (ms * 1e-3) / 1e12,
