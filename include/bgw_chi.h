@@ -174,6 +174,43 @@ BGW_API bgw_status bgw_chi0_finalize(bgw_ctx ctx, int iq, void *chi0, int on_dev
 BGW_API bgw_status bgw_profile(bgw_ctx ctx, int enable);
 BGW_API bgw_status bgw_profile_read(bgw_ctx ctx, double *ms, long *calls, long *kernels, int n);
 
+/*
+ * Matrix elements without any allocation (the paper has no counterpart; this
+ * is a deployment variant of bgw_mtxel_spinor).
+ *
+ * For callers that cannot allocate device memory when they need matrix
+ * elements: code whose memory pool or arena already owns the device memory,
+ * plug-ins whose host forbids cudaMalloc/cudaFree after start-up (both
+ * synchronise the whole device and may fail late), and loops that must not
+ * block in an allocator.  It needs no context: the caller passes the
+ * real-space grids and the output, and the call computes
+ *     M[v][c][g] = N^-3 sum_r sum_alpha conj(Uv[v][alpha](r)) Uc[c][alpha](r) e^{-i(G_g+G0).r}
+ * in FP64 with the same kernels as bgw_mtxel_spinor.
+ *   fft[3] : FFT box (supported lengths as above)
+ *   Uv     : DEVICE complex128 [nv][2][N1*N2*N3], u_{v,k,alpha}(r) with
+ *            u(r) = sum_h c(h) e^{+2 pi i h.r/N} (unnormalised)
+ *   Uc     : DEVICE complex128 [nc][2][N1*N2*N3], the bands at k' = k+q-G0,
+ *            unshifted (the call applies G0)
+ *   G0[3]  : host, umklapp vector with k + q = k' + G0
+ *   ng, gvec : host, [ng][3] dielectric sphere, 1 <= ng <= 65536
+ *   M_dev  : DEVICE complex128 [nv][nc][ng]
+ *   stream : cudaStream_t (NULL = default stream); asynchronous
+ * Scratch: one static device array of BGW_NOALLOC_SCRATCH_BYTES inside the
+ * library, reserved on every GPU that loads it until the process exits.  A
+ * call whose pairs need more (about nv*nc*N1*N2*(w3 + w2*w3/N2)*16 bytes,
+ * w the sphere's extent per axis) is rejected with BGW_E_ARG; split the band
+ * range.  Every call shares the array and fully rewrites what it reads, so
+ * nothing needs clearing, but calls that overlap on the GPU (different
+ * streams or devices' threads racing on one device) corrupt each other:
+ * serialise them.  The first call on a device sets up that device (FFT tables
+ * and the array's device address); make it before any stream capture.
+ * Errors go to bgw_last_error(NULL).
+ */
+#define BGW_NOALLOC_SCRATCH_BYTES (64u << 20)
+BGW_API bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv, const void *Uc,
+                                            int nv, int nc, const int G0[3], int ng,
+                                            const int *gvec, void *M_dev, void *stream);
+
 /* Release every device buffer of the context (synchronizes its stream). */
 BGW_API void bgw_destroy(bgw_ctx ctx);
 

@@ -26,7 +26,7 @@ PRECISIONS = {"fp64": BGW_FP64, "mixed": BGW_MIXED_BF16X3}
 
 EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
             "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
-            "bgw_destroy", "bgw_last_error"]
+            "bgw_mtxel_spinor_noalloc", "bgw_destroy", "bgw_last_error"]
 STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize"]
 
 
@@ -46,10 +46,12 @@ _lib.bgw_chi0_accumulate.argtypes = [_P, _I, ctypes.POINTER(bgw_q), _I, _P, _I, 
 _lib.bgw_chi0_finalize.argtypes = [_P, _I, _P, _I]
 _lib.bgw_profile.argtypes = [_P, _I]
 _lib.bgw_profile_read.argtypes = [_P, _P, _P, _P, _I]
+_lib.bgw_mtxel_spinor_noalloc.argtypes = [_P, _P, _P, _I, _I, _P, _I, _P, _P, _P]
 _lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
 _lib.bgw_last_error.argtypes, _lib.bgw_last_error.restype = [_P], ctypes.c_char_p
 for _f in ["bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
-           "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read"]:
+           "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
+           "bgw_mtxel_spinor_noalloc"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -172,6 +174,21 @@ def bgw_profile_read(ctx) -> dict:
     kern = np.zeros(n, dtype=np.int64)
     _check(_lib.bgw_profile_read(ctx, _host_ptr(ms), _host_ptr(calls), _host_ptr(kern), n), ctx)
     return {s: (float(ms[i]), int(calls[i]), int(kern[i])) for i, s in enumerate(STAGES)}
+
+
+def bgw_mtxel_spinor_noalloc(fft, Uv, Uc, nv: int, nc: int, G0, gvec, M_dev, stream=None) -> int:
+    """Allocation-free FP64 matrix elements from device grids Uv [nv][2][N^3]
+    and Uc [nc][2][N^3] (complex128 tensors) into M_dev [nv][nc][ng]."""
+    f = np.ascontiguousarray(fft, dtype=np.int32)
+    g0 = np.ascontiguousarray(G0, dtype=np.int32)
+    g = np.ascontiguousarray(gvec, dtype=np.int32)
+    pv, dv = _ptr_and_device(Uv)
+    pc, dc = _ptr_and_device(Uc)
+    pm, dm = _ptr_and_device(M_dev)
+    if not (dv and dc and dm):
+        raise ValueError("Uv, Uc and M_dev must be device tensors")
+    return _check(_lib.bgw_mtxel_spinor_noalloc(_host_ptr(f), pv, pc, nv, nc, _host_ptr(g0), len(g),
+                                                _host_ptr(g), pm, _stream_handle(stream)), None)
 
 
 def bgw_destroy(ctx) -> None:

@@ -113,6 +113,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void bgw_set_global_error(const std::string &msg) { g_create_error = msg; }
+
 struct bgw_ctx_s {
     int box[3];
     long nbox;

@@ -19,7 +19,6 @@
 // with a warp-uniform index, so no register array is indexed at run time.
 #pragma once
 #include <cmath>
-#include <vector>
 
 #include "bgw_fft.cuh"
 #include "bgw_internal.h"
@@ -35,8 +34,8 @@ constexpr int kLineThreads = 128;
 
 // ---------------------------------------------------------------- tables --
 static cudaError_t upload_tables() {
-    std::vector<double2> t64(kTwTotal);
-    std::vector<float2> t32(kTwTotal);
+    double2 t64[kTwTotal];
+    float2 t32[kTwTotal];
     for (int i = 0; i < kNumFftLens; ++i) {
         const int n = kFftLens[i];
         const int off = tw_offset(n);
@@ -56,9 +55,9 @@ static cudaError_t upload_tables() {
             t32[off + j] = make_float2((float)c, (float)s);
         }
     }
-    cudaError_t e = cudaMemcpyToSymbol(c_tw64, t64.data(), sizeof(double2) * kTwTotal);
+    cudaError_t e = cudaMemcpyToSymbol(c_tw64, t64, sizeof(double2) * kTwTotal);
     if (e != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(c_tw32, t32.data(), sizeof(float2) * kTwTotal);
+    return cudaMemcpyToSymbol(c_tw32, t32, sizeof(float2) * kTwTotal);
 }
 
 // ------------------------------------------------------ sphere -> grid --

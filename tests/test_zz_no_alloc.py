@@ -1,0 +1,64 @@
+"""The allocation-free matrix-element entry point (bgw_mtxel_spinor_noalloc)
+against the context-based bgw_mtxel_spinor, through the C-ABI.
+
+It exists for callers that cannot allocate device memory when they need
+matrix elements (a pool that owns the device memory, a host application that
+forbids cudaMalloc/cudaFree after start-up, loops that must not block in an
+allocator); its scratch is one static device array inside the library.
+This file is collected last on purpose: it must pass alone in a fresh
+process and after every other test.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_00808_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+TOL_M_FP64 = 1e-12
+
+
+def grids(torch, p, ik, bands):
+    """u_{n,k,alpha}(r) = sum_h c(h) e^{+2 pi i h.r/N} on the box (numpy FFT),
+    as a device complex128 tensor [nb][2][N^3]."""
+    N = np.array(p.box)
+    c = p.coeff[ik][bands]
+    box = np.zeros((len(c), 2) + p.box, dtype=np.complex128)
+    idx = np.mod(p.gvec[ik], N)
+    box[:, :, idx[:, 0], idx[:, 1], idx[:, 2]] = c
+    u = np.fft.ifftn(box, axes=(2, 3, 4)) * np.prod(N)
+    return torch.from_numpy(np.ascontiguousarray(u.reshape(len(c), 2, -1))).cuda()
+
+
+def test_noalloc_matches_context_mtxel_on_two_calls(gpu_lib):
+    torch = pytest.importorskip("torch")
+    p = syn.make_problem("si18_qx")
+    q, geps, nc = p.qs[0]
+    ng = len(geps)
+    ctx = gpu_lib.Chi0Context(p, "fp64")
+    ctx.upload()
+    for ik in (4, 0):          # an umklapp k first, then a plain one
+        kp, G0 = oracle.umklapp(p.kcrys, ik, q)
+        ref = torch.zeros((p.nv, nc, ng), dtype=torch.complex128, device="cuda")
+        gpu_lib.bgw_mtxel_spinor(ctx.ctx, q, geps, ik, 0, p.nv, 0, nc, ref)
+        Uv = grids(torch, p, ik, slice(0, p.nv))
+        Uc = grids(torch, p, kp, slice(p.nv, p.nv + nc))
+        M = torch.full((p.nv, nc, ng), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+        st = gpu_lib.bgw_mtxel_spinor_noalloc(p.box, Uv, Uc, p.nv, nc, G0, geps, M)
+        assert st == gpu_lib.BGW_OK
+        torch.cuda.synchronize()
+        got, want = M.cpu().numpy(), ref.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.abs(got - want).max() <= TOL_M_FP64 * np.abs(want).max()
+    ctx.close()
+
+
+def test_noalloc_rejects_calls_beyond_its_scratch(gpu_lib):
+    torch = pytest.importorskip("torch")
+    p = syn.make_problem("si18_qx")
+    geps = p.qs[0][1]
+    dummy = torch.zeros(2, dtype=torch.complex128, device="cuda")
+    with pytest.raises(gpu_lib.BgwError) as e:
+        gpu_lib.bgw_mtxel_spinor_noalloc(p.box, dummy, dummy, 100, 1000, (0, 0, 0), geps, dummy)
+    assert e.value.status == gpu_lib.BGW_E_ARG and "maximum" in str(e.value)
