@@ -133,6 +133,7 @@ struct bgw_ctx_s {
     DevBuf freq_dev;
     DevBuf out_stage;    // finalize to host
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
+    DevBuf errflag;      // device int: non-zero after a bounded device wait gave up
     // stage timing (bgw_profile)
     static constexpr int kStages = 5;
     bool prof = false;
@@ -382,12 +383,15 @@ bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const double *kcry
     c->k.resize(nk);
     e = c->grids.ensure((size_t)nk * c->grid_elems_per_k() * c->csize, c->st);
     if (e == cudaSuccess) e = c->energy.ensure(sizeof(double) * (size_t)nk * c->nb, c->st);
+    if (e == cudaSuccess) e = c->errflag.ensure(sizeof(int), c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st);
     if (e != cudaSuccess) {
         g_create_error = std::string("bgw_create: allocating grids: ") + cudaGetErrorString(e);
         const bgw_status s = (e == cudaErrorMemoryAllocation) ? BGW_E_NOMEM : BGW_E_CUDA;
         cudaGetLastError();
         c->grids.release();
         c->energy.release();
+        c->errflag.release();
         delete c;
         return s;
     }
@@ -652,7 +656,8 @@ bgw_status bgw_chi0_accumulate(bgw_ctx c, int nq, const bgw_q *qs, int nfreq,
                                       s.acc.p, c->st);
                 else
                     e = bgw::herk_mixed(c->M.p, P, s.ng, static_cast<const double *>(c->W.p), nfreq,
-                                        c->mixed_ws.p, s.acc.p, c->st, &nkern);
+                                        c->mixed_ws.p, s.acc.p, c->st, &nkern,
+                                        static_cast<int *>(c->errflag.p));
                 c->stage_end(rec, nkern);
             }
             if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: kernels");
@@ -685,8 +690,15 @@ bgw_status bgw_chi0_finalize(bgw_ctx c, int iq, void *chi0, int on_device) {
     e = bgw::chi0_finalize(s.acc.p, s.ng, c->nfreq, scale, c->out_stage.p, c->st);
     c->stage_end(rec, 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(chi0, c->out_stage.p, bytes, cudaMemcpyDeviceToHost, c->st);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return c->cuda_fail(e, "finalize: copy to host");
+    if (flag != 0) {
+        cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st);
+        return c->fail(BGW_E_TIMEOUT, "finalize: a device-side wait gave up (code %d); the result is invalid",
+                       flag);
+    }
     return BGW_OK;
 }
 
@@ -737,7 +749,8 @@ void bgw_destroy(bgw_ctx c) {
             s.acc.release();
         }
         DevBuf *bufs[] = {&c->grids, &c->energy, &c->stage, &c->S,  &c->R,        &c->A,
-                          &c->Bs,    &c->M,      &c->W,     &c->mixed_ws, &c->freq_dev, &c->out_stage, &c->gmap_tmp};
+                          &c->Bs,    &c->M,      &c->W,     &c->mixed_ws, &c->freq_dev, &c->out_stage, &c->gmap_tmp,
+                          &c->errflag};
         for (DevBuf *b : bufs) b->release();
     }
     delete c;

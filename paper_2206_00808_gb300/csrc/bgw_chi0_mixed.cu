@@ -1,10 +1,409 @@
-// Mixed-precision contraction: not built yet.
+// Mixed-precision contraction of chi0 on tcgen05 tensor cores (sm_103a).
+//
+// chi0_j[g][g'] += sum_p w_pj conj(M_p[g]) M_p[g']   (the polarizability
+// formula of arXiv:2206.00808 Sec. II on the imaginary axis; M complex64,
+// w FP64).  In real form with the interleaved rows x_{2g} = Re M_g,
+// x_{2g+1} = Im M_g:
+//   D_j[r][r'] = sum_p w_pj x_r(p) x_r'(p),
+//   Re chi = D[2g][2g'] + D[2g+1][2g'+1],  Im chi = D[2g][2g'+1] - D[2g+1][2g'].
+// D_j is a GEMM with K = pairs: A = X (shared by every frequency) and
+// B_j = w_j X.  Each operand is split into BF16 hi + lo (x ~ hi + lo to
+// ~2^-17 relative) and the product runs as ONE tcgen05 kind::f16 GEMM over
+// K' = 3K: [A_hi | A_hi | A_lo] x [B_hi | B_lo | B_hi]^T, FP32 accumulation
+// in tensor memory.  The epilogue folds the 2x2 blocks into complex chi and
+// adds them to the FP64 accumulator (the FP64 reduction across k blocks).
+//
+// Kernels:
+//   k5_split   M -> X planes [1 + nfreq][hi, lo][R][Kp] BF16 (K-major,
+//              zero padded to R = 128-multiple rows, Kp = 64-multiple pairs)
+//   k5_gemm    one CTA per (lower 128x128 tile of D, frequency): TMA loads
+//              (128B swizzle) into a 4-stage ring, one thread issues
+//              tcgen05.mma, all four warps drain TMEM and update chi in FP64.
+// Every mbarrier wait has an iteration limit; on expiry the kernel records
+// an error code in *err, waits (bounded) for its own copies in flight,
+// frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <mutex>
+
 #include "bgw_mixed.h"
 
 namespace bgw {
-size_t mixed_workspace_bytes(long, int, int) { return 0; }
-cudaError_t herk_mixed(const void *, int, int, const double *, int, void *, void *, cudaStream_t,
-                       int *) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr int kTileM = 128;           // rows of D per CTA (A rows)
+constexpr int kTileN = 128;           // columns of D per CTA (B rows)
+constexpr int kBlockK = 64;           // BF16 elements per 128-byte swizzled row
+constexpr int kStages = 4;
+constexpr int kStageBytes = (kTileM + kTileN) * kBlockK * 2;   // 32 KB
+constexpr int kGemmThreads = 128;
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
+
+// ------------------------------------------------------------ split kernel --
+// plane 0: A = X; plane 1 + j: B_j = w_j X.  Output [plane][hi|lo][R][Kp].
+constexpr int kSplitTile = 32;
+
+__global__ void __launch_bounds__(256)
+k5_split(const float2 *__restrict__ M, int P, int ng, const double *__restrict__ w, int R, int Kp,
+         __nv_bfloat16 *__restrict__ X) {
+    __shared__ float2 tile[kSplitTile][kSplitTile + 1];   // [p][g]
+    const int g0 = blockIdx.x * kSplitTile;   // complex column block (rows 2g, 2g+1)
+    const int p0 = blockIdx.y * kSplitTile;
+    const int plane = blockIdx.z;             // 0 = A, 1 + j = B_j
+    const int tx = threadIdx.x % kSplitTile, ty = threadIdx.x / kSplitTile;   // 32 x 8
+    for (int i = ty; i < kSplitTile; i += 8) {
+        const int p = p0 + i, g = g0 + tx;
+        float2 v = make_float2(0.f, 0.f);
+        if (p < P && g < ng) v = M[(long)p * ng + g];
+        if (plane > 0 && p < P) {
+            const float s = (float)w[(long)(plane - 1) * P + p];
+            v.x *= s;
+            v.y *= s;
+        }
+        tile[i][tx] = v;
+    }
+    __syncthreads();
+    const long planeElems = (long)R * Kp;
+    __nv_bfloat16 *hi = X + (long)plane * 2 * planeElems;
+    __nv_bfloat16 *lo = hi + planeElems;
+    // each thread writes pair p0+tx for rows 2g, 2g+1 of eight g
+    for (int i = ty; i < kSplitTile; i += 8) {
+        const int g = g0 + i, p = p0 + tx;
+        if (2 * g >= R || p >= Kp) continue;
+        const float2 v = tile[tx][i];
+        const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hm = __float2bfloat16_rn(v.y);
+        const __nv_bfloat16 lr = __float2bfloat16_rn(v.x - __bfloat162float(hr));
+        const __nv_bfloat16 lm = __float2bfloat16_rn(v.y - __bfloat162float(hm));
+        hi[(long)(2 * g) * Kp + p] = hr;
+        hi[(long)(2 * g + 1) * Kp + p] = hm;
+        lo[(long)(2 * g) * Kp + p] = lr;
+        lo[(long)(2 * g + 1) * Kp + p] = lm;
+    }
 }
+
+// Rows beyond 2*ng and pairs beyond P are zero: the padding rows are written
+// by the block that owns them only when 2g < R; rows 2*ng..R-1 of the last
+// block get zeros above, pairs P..Kp-1 get zeros from the guarded loads.
+
+// --------------------------------------------------------- PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 B, 8-row swizzle atoms 1024 B apart (SBO), version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void lower_tile(int t, int &bi, int &bj) {
+    int i = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    bi = i;
+    bj = t - i * (i + 1) / 2;
+}
+
+// --------------------------------------------------------------- GEMM --
+__global__ void __launch_bounds__(kGemmThreads, 1)
+k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__restrict__ acc,
+        int *__restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kStages];
+    __shared__ __align__(8) uint64_t empty_bar[kStages];
+    __shared__ __align__(8) uint64_t accum_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int ti, tj;
+    lower_tile(blockIdx.x, ti, tj);
+    const int j = blockIdx.y;
+    const int nfreq = gridDim.y;
+    const int nkb = Kp / kBlockK;
+    const int total = 3 * nkb;
+
+    // 1024-byte aligned stage ring
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t ring = (raw + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&accum_bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(kTileN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    // planes: 0 A_hi, 1 A_lo, 2 + 2j B_j hi, 3 + 2j B_j lo
+    const int a_row = ti * kTileM, b_row = tj * kTileN;
+    const int bhi = 2 + 2 * j, blo = 3 + 2 * j;
+    (void)nfreq;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int issued = 0;
+        for (int it = 0; it < total; ++it) {
+            const int s = it % kStages;
+            if (!mbar_wait(smem_u32(&empty_bar[s]), ((it / kStages) & 1) ^ 1)) {
+                atomicExch(err, kErrEmpty);
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (*(volatile int *)&abort_flag) break;
+            const int seg = it / nkb, kb = it % nkb;
+            const int ap = (seg == 2) ? 1 : 0;
+            const int bp = (seg == 1) ? blo : bhi;
+            const uint32_t sa = ring + s * kStageBytes;
+            const uint32_t sb = sa + kTileM * kBlockK * 2;
+            const uint32_t fb = smem_u32(&full_bar[s]);
+            mbar_expect_tx(fb, kStageBytes);
+            tma_load_3d(sa, &xmap, fb, kb * kBlockK, a_row, ap);
+            tma_load_3d(sb, &xmap, fb, kb * kBlockK, b_row, bp);
+            issued = it + 1;
+        }
+        // drain: every issued load must land before the CTA can exit
+        for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it) {
+            if (!mbar_wait(smem_u32(&full_bar[it % kStages]), (it / kStages) & 1)) {
+                atomicExch(err, kErrDrain);
+                break;
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int it = 0; it < total; ++it) {
+            const int s = it % kStages;
+            if (!mbar_wait(smem_u32(&full_bar[s]), (it / kStages) & 1)) {
+                atomicExch(err, kErrFull);
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (*(volatile int *)&abort_flag) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = ring + s * kStageBytes;
+            const uint32_t sb = sa + kTileM * kBlockK * 2;
+            const uint64_t ad = smem_desc(sa), bd = smem_desc(sb);
+#pragma unroll
+            for (int k = 0; k < kBlockK / 16; ++k) {
+                // advance 16 BF16 = 32 bytes along K inside the swizzled row
+                mma_bf16(tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (it > 0 || k > 0) ? 1u : 0u);
+            }
+            mma_commit(smem_u32(&empty_bar[s]));
+        }
+        mma_commit(smem_u32(&accum_bar));
+    }
+    __syncwarp();
+
+    // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.
+    bool ok = mbar_wait(smem_u32(&accum_bar), 0);
+    if (!ok && lane == 0) atomicExch(err, kErrAccum);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);   // warp-uniform
+    if (ok) {
+        const int r = 32 * warp + lane;            // tile row
+        const int g = (a_row + r) >> 1;            // complex row
+        const bool even = (r & 1) == 0;
+        for (int c0 = 0; c0 < kTileN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            float mine[32], other[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                mine[i] = __uint_as_float(v[i]);
+                other[i] = __shfl_xor_sync(0xffffffffu, mine[i], 1);
+            }
+            // rows 2g (re-row) and 2g+1 (im-row) now sit in both lanes of the pair;
+            // the even lane writes column pairs 0..7 of this chunk, the odd lane 8..15.
+            if (g < ng) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int cc = 2 * q;
+                    const float d00 = even ? mine[cc] : other[cc];           // D[2g][2g']
+                    const float d01 = even ? mine[cc + 1] : other[cc + 1];   // D[2g][2g'+1]
+                    const float d10 = even ? other[cc] : mine[cc];           // D[2g+1][2g']
+                    const float d11 = even ? other[cc + 1] : mine[cc + 1];   // D[2g+1][2g'+1]
+                    const int gp = (b_row + c0 + cc) >> 1;
+                    if ((q < 8) == even && gp < ng) {
+                        double2 *o = acc + ((long)j * ng + g) * ng + gp;
+                        double2 t = *o;
+                        t.x += (double)d00 + (double)d11;
+                        t.y += (double)d01 - (double)d10;
+                        *o = t;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTileN)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------- tensor map --
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+cudaError_t g_encode_status = cudaSuccess;
+
+cudaError_t get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            g_encode_status = (e != cudaSuccess) ? e : cudaErrorNotSupported;
+            return;
+        }
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode_status;
+}
+
+long round_up(long x, long m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+size_t mixed_workspace_bytes(long P, int ng, int nfreq) {
+    const long R = round_up(2L * ng, kTileM);
+    const long Kp = round_up(P, kBlockK);
+    return (size_t)(1 + nfreq) * 2 * R * Kp * sizeof(__nv_bfloat16) + 256;
+}
+
+cudaError_t herk_mixed(const void *M, int P, int ng, const double *w, int nfreq, void *ws, void *acc,
+                       cudaStream_t st, int *nkernels, int *err) {
+    *nkernels = 0;
+    if (P == 0) return cudaSuccess;
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    const long R = round_up(2L * ng, kTileM);
+    const long Kp = round_up(P, kBlockK);
+    __nv_bfloat16 *X = static_cast<__nv_bfloat16 *>(ws);
+    const int planes = 2 * (1 + nfreq);
+
+    dim3 sgrid((unsigned)((R / 2 + kSplitTile - 1) / kSplitTile),
+               (unsigned)((Kp + kSplitTile - 1) / kSplitTile), (unsigned)(1 + nfreq));
+    k5_split<<<sgrid, 256, 0, st>>>(static_cast<const float2 *>(M), P, ng, w, (int)R, (int)Kp, X);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
+    const cuuint32_t box[3] = {kBlockK, kTileM, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, X, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+    const int smem = kStages * kStageBytes + 1024;
+    e = cudaFuncSetAttribute(k5_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int nt = (int)(R / kTileM);
+    dim3 ggrid((unsigned)(nt * (nt + 1) / 2), (unsigned)nfreq);
+    k5_gemm<<<ggrid, kGemmThreads, smem, st>>>(map, (int)Kp, ng, static_cast<double2 *>(acc), err);
+    *nkernels = 2;
+    return cudaGetLastError();
+}
+
 }  // namespace bgw

@@ -12,8 +12,10 @@ size_t mixed_workspace_bytes(long P, int ng, int nfreq);
 
 // acc[j][g][g'] (complex128, lower block triangle) += sum_p w[j][p]
 // conj(M[p][g]) M[p][g'] with M complex64 [P][ng] and w FP64 [nfreq][P].
-// *nkernels receives the number of kernels launched.
+// *nkernels receives the number of kernels launched.  A device-side wait
+// that gives up writes a non-zero code to the device int *err (the host
+// reports BGW_E_TIMEOUT when it reads it back).
 cudaError_t herk_mixed(const void *M, int P, int ng, const double *w, int nfreq, void *ws,
-                       void *acc, cudaStream_t st, int *nkernels);
+                       void *acc, cudaStream_t st, int *nkernels, int *err);
 
 }  // namespace bgw
