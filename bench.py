@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")
     return ap.parse_args()
 
@@ -227,22 +228,26 @@ def run_reference(args, world, rank):
     return 0
 
 
-def run_ours(args, world, rank, local):
-    import torch
-    torch.cuda.set_device(local)
-    dist = Dist(world, rank, "nccl")
-    from paper_2206_00808_gb300 import build
-    build.build()
-    from paper_2206_00808_gb300 import binding as B
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
-    p, desc = make_workload(args.workload)
+
+def bf16_peaks():
+    """(burst, sustained) dense BF16 TFLOP/s measured on this machine, else the
+    fallback figures."""
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 1700.0, "fallback"
+
+
+def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_clocks):
+    """Time `args.steps` full steps of one precision; returns a dict."""
     q, geps, nc = p.qs[0]
     ng, nf = len(geps), len(p.freq)
-    stream = torch.cuda.current_stream()
-    dev_in = [(torch.from_numpy(np.ascontiguousarray(p.coeff[ik])).cuda(),
-               torch.from_numpy(np.ascontiguousarray(p.energy[ik])).cuda()) for ik in range(p.nk)]
     out = torch.empty((nf, ng, ng), dtype=torch.complex128, device="cuda")
-    ctx = B.Chi0Context(p, args.precision, stream)
+    ctx = B.Chi0Context(p, precision, stream)
 
     def step():
         ctx.reset()
@@ -257,60 +262,132 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     B.bgw_profile(ctx.ctx, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
+    clk = ClockSampler(local) if with_clocks else None
+    if clk:
+        clk.__enter__()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__(None, None, None)
     dist.barrier()
     torch.cuda.synchronize()
     ms_total = dist.max(ev0.elapsed_time(ev1))
     prof = B.bgw_profile_read(ctx.ctx)
     B.bgw_profile(ctx.ctx, False)
-    ms = ms_total / args.steps
-    value = world * 1e3 / ms
+    res = {"ctx": ctx, "out": out, "ms": ms_total / args.steps, "prof": prof,
+           "clocks": clk.summary() if clk else None}
+    res["stages"] = {s: {"ms_per_step": sms / args.steps, "share": sms / max(1e-9, ms_total),
+                         "launch_groups": calls, "kernels": kern}
+                     for s, (sms, calls, kern) in prof.items() if calls}
+    res["gpu_launches"] = sum(v["kernels"] for v in res["stages"].values())
+    return res
 
-    fl = flop_model(p)
-    stages = {}
-    for s, (sms, calls, kern) in prof.items():
-        stages[s] = {"ms_per_step": sms / args.steps, "share": sms / max(1e-9, ms_total),
-                     "launch_groups": calls, "kernels": kern}
-    con_ms, con_calls, _ = prof["contraction"]
-    per_launch_flop = fl["contraction"] / p.nk
-    achieved = per_launch_flop / (con_ms / con_calls * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS
-    roofline = {"bound": "alu", "kernel": "k4_herk_f64", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC.get("k4_herk_f64"),
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal FP64 1.25 TFLOP/s)"}
-    gpu_launches = sum(v["kernels"] for v in stages.values())
 
-    e2e = None
-    if not args.no_e2e:
-        pin = [(torch.from_numpy(np.ascontiguousarray(p.coeff[ik])).pin_memory(),
-                torch.from_numpy(np.ascontiguousarray(p.energy[ik])).pin_memory()) for ik in range(p.nk)]
-        host_out = torch.empty((nf, ng, ng), dtype=torch.complex128).pin_memory()
-        h2d = sum(c.numel() * c.element_size() + e.numel() * e.element_size() for c, e in pin)
-        d2h = host_out.numel() * host_out.element_size()
+def e2e_measure(B, torch, p, res, args, dist, stream):
+    """Same step from pinned host buffers, chi0 read back to host."""
+    ctx = res["ctx"]
+    q, geps, nc = p.qs[0]
+    ng, nf = len(geps), len(p.freq)
+    pin = [(torch.from_numpy(np.ascontiguousarray(p.coeff[ik])).pin_memory(),
+            torch.from_numpy(np.ascontiguousarray(p.energy[ik])).pin_memory()) for ik in range(p.nk)]
+    host_out = torch.empty((nf, ng, ng), dtype=torch.complex128).pin_memory()
+    h2d = sum(c.numel() * c.element_size() + e.numel() * e.element_size() for c, e in pin)
+    d2h = host_out.numel() * host_out.element_size()
 
-        def e2e_step():
-            ctx.reset()
-            ctx.upload(device_inputs=pin)
-            ctx.accumulate()
-            B.bgw_chi0_finalize(ctx.ctx, 0, host_out.numpy())
+    def e2e_step():
+        ctx.reset()
+        ctx.upload(device_inputs=pin)
+        ctx.accumulate()
+        B.bgw_chi0_finalize(ctx.ctx, 0, host_out.numpy())
 
+    e2e_step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.e2e_steps):
         e2e_step()
-        torch.cuda.synchronize()
-        dist.barrier()
-        ev0.record(stream)
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ems = dist.max(ev0.elapsed_time(ev1)) / args.e2e_steps
-        e2e = {"value": world * 1e3 / ems, "unit": "q-points/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ems = dist.max(ev0.elapsed_time(ev1)) / args.e2e_steps
+    return {"value": dist.world * 1e3 / ems, "unit": "q-points/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = Dist(world, rank, "nccl")
+    from paper_2206_00808_gb300 import build
+    build.build()
+    from paper_2206_00808_gb300 import binding as B
+
+    p, desc = make_workload(args.workload)
+    q, geps, nc = p.qs[0]
+    ng, nf = len(geps), len(p.freq)
+    stream = torch.cuda.current_stream()
+    dev_in = [(torch.from_numpy(np.ascontiguousarray(p.coeff[ik])).cuda(),
+               torch.from_numpy(np.ascontiguousarray(p.energy[ik])).cuda()) for ik in range(p.nk)]
+    fl = flop_model(p)
+    per_launch_flop = fl["contraction"] / p.nk
+
+    head = measure(B, torch, p, args.precision, args, dist, stream, dev_in, local, True)
+    ms = head["ms"]
+    value = world * 1e3 / ms
+    con_ms, con_calls, _ = head["prof"]["contraction"]
+    achieved = per_launch_flop / (con_ms / con_calls * 1e-3) / 1e12
+    burst, sustained, src = bf16_peaks()
+    if args.precision == "fp64":
+        roofline = {"bound": "alu", "kernel": "k4_herk_f64", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": TRAFFIC.get("k4_herk_f64"),
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                                   "(nominal FP64 1.25 TFLOP/s)"}
+    else:
+        roofline = {"bound": "tensor", "kernel": "k5_gemm", "achieved": achieved,
+                    "peak": sustained / 3, "unit": "TFLOP/s", "frac": achieved / (sustained / 3),
+                    "traffic": TRAFFIC.get("k5_gemm"),
+                    "peak_source": f"{src} BF16 sustained {sustained} / 3 products"}
+    e2e = None if args.no_e2e else e2e_measure(B, torch, p, head, args, dist, stream)
+
+    other = None
+    if args.precision == "fp64" and not args.no_mixed:
+        ref = head["out"].cpu().numpy()
+        mix = measure(B, torch, p, "mixed", args, dist, stream, dev_in, local, False)
+        got = mix["out"].cpu().numpy()
+        gm_ms, gm_calls, _ = mix["prof"]["contraction"]
+        gm_ach = per_launch_flop / (gm_ms / gm_calls * 1e-3) / 1e12
+        pad_r = -(-2 * ng // 128) * 128
+        nt = pad_r // 128
+        pad_k = -(-(p.nv * nc) // 64) * 64
+        executed = 3 * 2.0 * nt * (nt + 1) / 2 * 128 * 128 * pad_k * nf
+        offd = ~np.eye(ng, dtype=bool)
+        other = {"precision": "mixed (FP32 grids/FFT, complex64 M, split-BF16 x3 tcgen05, "
+                              "FP64 weights and k-reduction)",
+                 "value": world * 1e3 / mix["ms"], "unit": "q-points/s", "ms_per_step": mix["ms"],
+                 "speedup_vs_fp64": ms / mix["ms"],
+                 "rel_fro_err_vs_fp64": rel_fro(got, ref),
+                 "rel_fro_err_per_freq_max": max(rel_fro(got[j], ref[j]) for j in range(nf)),
+                 "offdiag_rel_fro_err": max(rel_fro(got[j][offd], ref[j][offd]) for j in range(nf)),
+                 "max_entry_err_rel_to_max": float(np.abs(got - ref).max() / np.abs(ref).max()),
+                 "error_reference": "the FP64 GPU path (itself within 1e-10 of the CPU oracle)",
+                 "tflops": fl["total"] / (mix["ms"] * 1e-3) / 1e12,
+                 "stages": mix["stages"], "gpu_launches": mix["gpu_launches"],
+                 "roofline": {"bound": "tensor", "kernel": "k5_gemm", "achieved": gm_ach,
+                              "peak": sustained / 3, "unit": "TFLOP/s",
+                              "frac": gm_ach / (sustained / 3),
+                              "executed_bf16_tflops": executed / (gm_ms / gm_calls * 1e-3) / 1e12,
+                              "executed_frac_of_bf16": executed / (gm_ms / gm_calls * 1e-3) / 1e12 / sustained,
+                              "traffic": TRAFFIC.get("k5_gemm"),
+                              "peak_source": f"{src} BF16 sustained {sustained} TFLOP/s / 3 products"}}
+        mix["ctx"].close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -327,11 +404,12 @@ def run_ours(args, world, rank, local):
                            f"{sum(c.nbytes for c in p.coeff) / 1e9:.2f} GB, grids resident per step)"},
                 "tflops": fl["total"] / (ms * 1e-3) / 1e12,
                 "pairs_per_s": value * p.pairs(),
-                "stages": stages,
+                "stages": head["stages"],
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": gpu_launches, "clocks": clk.summary()}
+                "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+                "mixed": other}
         print(json.dumps(line), flush=True)
-    ctx.close()
+    head["ctx"].close()
     dist.close()
     return 0
 

@@ -165,7 +165,7 @@ BGW_API bgw_status bgw_chi0_finalize(bgw_ctx ctx, int iq, void *chi0, int on_dev
 /*
  * Stage timing with CUDA events recorded on the context stream around each
  * launch group.  Stages: 0 sphere->grid (bgw_wfn_upload), 1 matrix elements,
- * 2 pair weights, 3 contraction, 4 finalize.
+ * 2 pair weights, 3 contraction, 4 finalize, 5 operand split (mixed path).
  *   bgw_profile(ctx, 1) clears the totals and starts recording; 0 stops.
  *   bgw_profile_read(ctx, ms, calls, kernels, n) fills the first n stages:
  *   device milliseconds, launch groups and kernels launched since the last

@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": BGW_FP64, "mixed": BGW_MIXED_BF16X3}
 EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
             "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
             "bgw_mtxel_spinor_noalloc", "bgw_destroy", "bgw_last_error"]
-STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize"]
+STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split"]
 
 
 class bgw_q(ctypes.Structure):

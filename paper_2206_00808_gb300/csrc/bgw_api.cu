@@ -135,7 +135,7 @@ struct bgw_ctx_s {
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
     DevBuf errflag;      // device int: non-zero after a bounded device wait gave up
     // stage timing (bgw_profile)
-    static constexpr int kStages = 5;
+    static constexpr int kStages = 6;
     bool prof = false;
     struct Rec { int stage; long kernels; cudaEvent_t a, b; };
     std::vector<Rec> recs;
@@ -648,17 +648,21 @@ bgw_status bgw_chi0_accumulate(bgw_ctx c, int nq, const bgw_q *qs, int nfreq,
                                       nfreq, static_cast<double *>(c->W.p), c->st);
                 c->stage_end(rec, 1);
             }
+            if (e == cudaSuccess && c->prec != BGW_FP64) {
+                const int rec = c->stage_begin(5);
+                e = bgw::mixed_split(c->M.p, P, s.ng, static_cast<const double *>(c->W.p), nfreq,
+                                     c->mixed_ws.p, c->st);
+                c->stage_end(rec, 1);
+            }
             if (e == cudaSuccess) {
                 const int rec = c->stage_begin(3);
-                int nkern = 1;
                 if (c->prec == BGW_FP64)
                     e = bgw::herk_f64(c->M.p, P, s.ng, static_cast<const double *>(c->W.p), nfreq,
                                       s.acc.p, c->st);
                 else
-                    e = bgw::herk_mixed(c->M.p, P, s.ng, static_cast<const double *>(c->W.p), nfreq,
-                                        c->mixed_ws.p, s.acc.p, c->st, &nkern,
+                    e = bgw::mixed_gemm(P, s.ng, nfreq, c->mixed_ws.p, s.acc.p, c->st,
                                         static_cast<int *>(c->errflag.p));
-                c->stage_end(rec, nkern);
+                c->stage_end(rec, 1);
             }
             if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: kernels");
         }
@@ -722,7 +726,7 @@ bgw_status bgw_profile_read(bgw_ctx c, double *ms, long *calls, long *kernels, i
     if (!c) return BGW_E_ARG;
     DeviceGuard dg(c->device);
     c->err.clear();
-    if (n < 0 || n > bgw_ctx_s::kStages) return c->fail(BGW_E_ARG, "profile_read: n outside 0..5");
+    if (n < 0 || n > bgw_ctx_s::kStages) return c->fail(BGW_E_ARG, "profile_read: n outside 0..6");
     cudaError_t e = c->drain();
     if (e != cudaSuccess) return c->cuda_fail(e, "profile_read: stream");
     for (int i = 0; i < n; ++i) {

@@ -8,16 +8,21 @@
 //   Re chi = D[2g][2g'] + D[2g+1][2g'+1],  Im chi = D[2g][2g'+1] - D[2g+1][2g'].
 // D_j is a GEMM with K = pairs: A = X (shared by every frequency) and
 // B_j = w_j X.  Each operand is split into BF16 hi + lo (x ~ hi + lo to
-// ~2^-17 relative) and the product runs as ONE tcgen05 kind::f16 GEMM over
-// K' = 3K: [A_hi | A_hi | A_lo] x [B_hi | B_lo | B_hi]^T, FP32 accumulation
-// in tensor memory.  The epilogue folds the 2x2 blocks into complex chi and
-// adds them to the FP64 accumulator (the FP64 reduction across k blocks).
+// ~2^-17 relative) and D = A_hi B_hi + A_hi B_lo + A_lo B_hi runs on tcgen05
+// kind::f16 with FP32 accumulation in tensor memory.  Each 64-pair K block
+// loads the four tiles once and issues all three products.  The accumulator
+// truncates on every add, so the large hi.hi products go to three TMEM
+// accumulators (one per third of K) and the two small cross products to a
+// fourth: no accumulator takes more than a third of the large adds, and the
+// small terms are not rounded against the large sum.  The epilogue adds the
+// four, folds the 2x2 blocks into complex chi and adds them to the FP64
+// accumulator (the FP64 reduction across k blocks).
 //
 // Kernels:
 //   k5_split   M -> X planes [1 + nfreq][hi, lo][R][Kp] BF16 (K-major,
 //              zero padded to R = 128-multiple rows, Kp = 64-multiple pairs)
 //   k5_gemm    one CTA per (lower 128x128 tile of D, frequency): TMA loads
-//              (128B swizzle) into a 4-stage ring, one thread issues
+//              (128B swizzle) into a 3-stage ring of 64 KB, one thread issues
 //              tcgen05.mma, all four warps drain TMEM and update chi in FP64.
 // Every mbarrier wait has an iteration limit; on expiry the kernel records
 // an error code in *err, waits (bounded) for its own copies in flight,
@@ -37,8 +42,10 @@ namespace {
 constexpr int kTileM = 128;           // rows of D per CTA (A rows)
 constexpr int kTileN = 128;           // columns of D per CTA (B rows)
 constexpr int kBlockK = 64;           // BF16 elements per 128-byte swizzled row
-constexpr int kStages = 4;
-constexpr int kStageBytes = (kTileM + kTileN) * kBlockK * 2;   // 32 KB
+constexpr int kStages = 3;
+constexpr int kTileBytes = kTileM * kBlockK * 2;                 // 16 KB per operand tile
+constexpr int kStageBytes = 4 * kTileBytes;                      // A_hi, A_lo, B_hi, B_lo
+constexpr int kAccCols = 4 * kTileN;                             // 3 hi.hi + 1 cross accumulator
 constexpr int kGemmThreads = 128;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
@@ -204,7 +211,6 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
     const int j = blockIdx.y;
     const int nfreq = gridDim.y;
     const int nkb = Kp / kBlockK;
-    const int total = 3 * nkb;
 
     // 1024-byte aligned stage ring
     const uint32_t raw = smem_u32(smem_raw);
@@ -223,7 +229,7 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
-                     "r"(kTileN)
+                     "r"(kAccCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -235,12 +241,13 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
     // planes: 0 A_hi, 1 A_lo, 2 + 2j B_j hi, 3 + 2j B_j lo
     const int a_row = ti * kTileM, b_row = tj * kTileN;
     const int bhi = 2 + 2 * j, blo = 3 + 2 * j;
+    const int nchunks = nkb < 3 ? nkb : 3;   // hi.hi accumulators in use
     (void)nfreq;
 
     if (warp == 0 && lane == 0) {
         // TMA producer
         int issued = 0;
-        for (int it = 0; it < total; ++it) {
+        for (int it = 0; it < nkb; ++it) {
             const int s = it % kStages;
             if (!mbar_wait(smem_u32(&empty_bar[s]), ((it / kStages) & 1) ^ 1)) {
                 atomicExch(err, kErrEmpty);
@@ -248,15 +255,14 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
                 break;
             }
             if (*(volatile int *)&abort_flag) break;
-            const int seg = it / nkb, kb = it % nkb;
-            const int ap = (seg == 2) ? 1 : 0;
-            const int bp = (seg == 1) ? blo : bhi;
-            const uint32_t sa = ring + s * kStageBytes;
-            const uint32_t sb = sa + kTileM * kBlockK * 2;
+            const uint32_t st0 = ring + s * kStageBytes;
             const uint32_t fb = smem_u32(&full_bar[s]);
+            const int x = it * kBlockK;
             mbar_expect_tx(fb, kStageBytes);
-            tma_load_3d(sa, &xmap, fb, kb * kBlockK, a_row, ap);
-            tma_load_3d(sb, &xmap, fb, kb * kBlockK, b_row, bp);
+            tma_load_3d(st0, &xmap, fb, x, a_row, 0);
+            tma_load_3d(st0 + kTileBytes, &xmap, fb, x, a_row, 1);
+            tma_load_3d(st0 + 2 * kTileBytes, &xmap, fb, x, b_row, bhi);
+            tma_load_3d(st0 + 3 * kTileBytes, &xmap, fb, x, b_row, blo);
             issued = it + 1;
         }
         // drain: every issued load must land before the CTA can exit
@@ -268,7 +274,8 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        for (int it = 0; it < total; ++it) {
+        int prev_chunk = -1;
+        for (int it = 0; it < nkb; ++it) {
             const int s = it % kStages;
             if (!mbar_wait(smem_u32(&full_bar[s]), (it / kStages) & 1)) {
                 atomicExch(err, kErrFull);
@@ -277,13 +284,21 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
             }
             if (*(volatile int *)&abort_flag) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = ring + s * kStageBytes;
-            const uint32_t sb = sa + kTileM * kBlockK * 2;
-            const uint64_t ad = smem_desc(sa), bd = smem_desc(sb);
+            const uint32_t st0 = ring + s * kStageBytes;
+            const uint64_t ahi = smem_desc(st0), alo = smem_desc(st0 + kTileBytes);
+            const uint64_t bhd = smem_desc(st0 + 2 * kTileBytes), bld = smem_desc(st0 + 3 * kTileBytes);
+            const int chunk = it * nchunks / nkb;
+            const bool fresh_hh = chunk != prev_chunk;
+            prev_chunk = chunk;
+            const uint32_t acc_hh = tmem + (uint32_t)(chunk * kTileN);
+            const uint32_t acc_x = tmem + (uint32_t)(3 * kTileN);
 #pragma unroll
             for (int k = 0; k < kBlockK / 16; ++k) {
                 // advance 16 BF16 = 32 bytes along K inside the swizzled row
-                mma_bf16(tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (it > 0 || k > 0) ? 1u : 0u);
+                const uint64_t o = (uint64_t)(2 * k);
+                mma_bf16(acc_hh, ahi + o, bhd + o, (fresh_hh && k == 0) ? 0u : 1u);
+                mma_bf16(acc_x, ahi + o, bld + o, (it == 0 && k == 0) ? 0u : 1u);
+                mma_bf16(acc_x, alo + o, bhd + o, 1u);
             }
             mma_commit(smem_u32(&empty_bar[s]));
         }
@@ -300,15 +315,23 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
         const int r = 32 * warp + lane;            // tile row
         const int g = (a_row + r) >> 1;            // complex row
         const bool even = (r & 1) == 0;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
         for (int c0 = 0; c0 < kTileN; c0 += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-            float mine[32], other[32];
+            float mine[32];
+            {
+                uint32_t v[32];
+                tmem_ld32(lane_base + (uint32_t)(3 * kTileN + c0), v);   // cross terms
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                mine[i] = __uint_as_float(v[i]);
-                other[i] = __shfl_xor_sync(0xffffffffu, mine[i], 1);
+                for (int i = 0; i < 32; ++i) mine[i] = __uint_as_float(v[i]);
+                for (int a = 0; a < nchunks; ++a) {
+                    tmem_ld32(lane_base + (uint32_t)(a * kTileN + c0), v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) mine[i] += __uint_as_float(v[i]);
+                }
             }
+            float other[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) other[i] = __shfl_xor_sync(0xffffffffu, mine[i], 1);
             // rows 2g (re-row) and 2g+1 (im-row) now sit in both lanes of the pair;
             // the even lane writes column pairs 0..7 of this chunk, the odd lane 8..15.
             if (g < ng) {
@@ -334,7 +357,7 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 2) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTileN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccCols)
                      : "memory");
     }
 }
@@ -369,40 +392,40 @@ size_t mixed_workspace_bytes(long P, int ng, int nfreq) {
     return (size_t)(1 + nfreq) * 2 * R * Kp * sizeof(__nv_bfloat16) + 256;
 }
 
-cudaError_t herk_mixed(const void *M, int P, int ng, const double *w, int nfreq, void *ws, void *acc,
-                       cudaStream_t st, int *nkernels, int *err) {
-    *nkernels = 0;
+cudaError_t mixed_split(const void *M, int P, int ng, const double *w, int nfreq, void *ws,
+                        cudaStream_t st) {
+    if (P == 0) return cudaSuccess;
+    const long R = round_up(2L * ng, kTileM);
+    const long Kp = round_up(P, kBlockK);
+    dim3 sgrid((unsigned)((R / 2 + kSplitTile - 1) / kSplitTile),
+               (unsigned)((Kp + kSplitTile - 1) / kSplitTile), (unsigned)(1 + nfreq));
+    k5_split<<<sgrid, 256, 0, st>>>(static_cast<const float2 *>(M), P, ng, w, (int)R, (int)Kp,
+                                    static_cast<__nv_bfloat16 *>(ws));
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_gemm(int P, int ng, int nfreq, void *ws, void *acc, cudaStream_t st, int *err) {
     if (P == 0) return cudaSuccess;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
     const long R = round_up(2L * ng, kTileM);
     const long Kp = round_up(P, kBlockK);
-    __nv_bfloat16 *X = static_cast<__nv_bfloat16 *>(ws);
     const int planes = 2 * (1 + nfreq);
-
-    dim3 sgrid((unsigned)((R / 2 + kSplitTile - 1) / kSplitTile),
-               (unsigned)((Kp + kSplitTile - 1) / kSplitTile), (unsigned)(1 + nfreq));
-    k5_split<<<sgrid, 256, 0, st>>>(static_cast<const float2 *>(M), P, ng, w, (int)R, (int)Kp, X);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-
     CUtensorMap map;
     const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)planes};
     const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
     const cuuint32_t box[3] = {kBlockK, kTileM, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, X, dims, strides, box, estr,
+    CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
-
     const int smem = kStages * kStageBytes + 1024;
     e = cudaFuncSetAttribute(k5_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int nt = (int)(R / kTileM);
     dim3 ggrid((unsigned)(nt * (nt + 1) / 2), (unsigned)nfreq);
     k5_gemm<<<ggrid, kGemmThreads, smem, st>>>(map, (int)Kp, ng, static_cast<double2 *>(acc), err);
-    *nkernels = 2;
     return cudaGetLastError();
 }
 

@@ -192,6 +192,122 @@ k2_xpass_gather(const C *__restrict__ Bs, int w0, int w1, int w2, int s0,
     }
 }
 
+// ----------------------------------------- plane-fused passes (FP32) --
+// Band planes staged through shared memory with coalesced loads; every line
+// is then read from a padded shared row.  Used when the box has n1 == n2.
+constexpr int kPlaneThreads = 256;
+
+// Pair density + z pass + y pass for one x-plane and a tile of tv x tc pairs.
+// Shared: planes[(tv+tc)][2][N][N+1], then Z[tv*tc][N][w2].
+template <int N>
+__global__ void __launch_bounds__(kPlaneThreads)
+k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int TV, int TC,
+            int w1, int w2, int s1, int s2, C *__restrict__ Bs) {
+    extern __shared__ unsigned char smem_raw[];
+    C *planes = reinterpret_cast<C *>(smem_raw);
+    const int x = blockIdx.x;
+    const int v0 = blockIdx.y * TV, c0 = blockIdx.z * TC;
+    const int tv = min(TV, nv - v0), tc = min(TC, nc - c0);
+    const int n0 = gridDim.x;
+    constexpr int RS = N + 1;                   // padded row
+    constexpr int PS = N * RS;                  // one spin component of a plane
+    C *Z = planes + (long)(TV + TC) * 2 * PS;
+    const long vol = (long)n0 * N * N;
+    // 1. stage the x-plane of every band of the tile (both spin components)
+    const int nb = tv + tc;
+    for (int i = threadIdx.x; i < nb * 2 * N * N; i += blockDim.x) {
+        const int b = i / (2 * N * N), rem = i % (2 * N * N);
+        const int a = rem / (N * N), yz = rem % (N * N);
+        const C *src = (b < tv) ? Uv + ((long)(v0 + b) * 2 + a) * vol
+                                : Uc + ((long)(c0 + b - tv) * 2 + a) * vol;
+        planes[(b * 2 + a) * PS + (yz / N) * RS + (yz % N)] = src[(long)x * N * N + yz];
+    }
+    __syncthreads();
+    // 2. z lines: rho(z) = sum_alpha conj(u_v) u_c, forward FFT, keep w2 outputs
+    const int npair = tv * tc;
+    for (int l = threadIdx.x; l < npair * N; l += blockDim.x) {
+        const int pr = l / N, y = l % N;
+        const int v = pr / tc, c = pr % tc;
+        const C *pv = planes + (v * 2) * PS + y * RS;
+        const C *pc = planes + ((tv + c) * 2) * PS + y * RS;
+        C a[N];
+#pragma unroll
+        for (int z = 0; z < N; ++z) {
+            const C r = cadd(cconjmul(pv[z], pc[z]), cconjmul(pv[PS + z], pc[PS + z]));
+            a[z] = cmul(r, root_fwd<T, N>((s2 * z) % N));
+        }
+        fft_line<T, -1, N>(a);
+        C *zo = Z + ((long)pr * N + y) * w2;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < w2) zo[j] = a[j];
+    }
+    __syncthreads();
+    // 3. y lines over the kept z outputs; keep w1 outputs -> Bs[p][x][jy][jz]
+    for (int l = threadIdx.x; l < npair * w2; l += blockDim.x) {
+        const int pr = l / w2, jz = l % w2;
+        const int v = pr / tc, c = pr % tc;
+        const C *zi = Z + (long)pr * N * w2 + jz;
+        C a[N];
+#pragma unroll
+        for (int y = 0; y < N; ++y) a[y] = cmul(zi[y * w2], root_fwd<T, N>((s1 * y) % N));
+        fft_line<T, -1, N>(a);
+        const long p = (long)(v0 + v) * nc + (c0 + c);
+        C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < w1) bo[j * w2] = a[j];
+    }
+}
+
+// Sphere -> grid y and z passes for one x-plane of TB band components:
+// S[b][x][w1][w2] -> U[b][x][N][N].  Shared: in[TB][w1][w2], P[TB][N][w2+1],
+// out[TB][N][N].
+template <int N>
+__global__ void __launch_bounds__(kPlaneThreads)
+k1_yz_plane(const C *__restrict__ S, long B, int TB, int w1, int w2, int s1, int s2,
+            C *__restrict__ U) {
+    extern __shared__ unsigned char smem_raw[];
+    C *in = reinterpret_cast<C *>(smem_raw);
+    const int x = blockIdx.x, n0 = gridDim.x;
+    const long b0 = (long)blockIdx.y * TB;
+    const int tb = (int)min((long)TB, B - b0);
+    const int PW = w2 + 1;
+    C *P = in + (long)TB * w1 * w2;
+    C *out = P + (long)TB * N * PW;
+    const int wsz = w1 * w2;
+    for (int i = threadIdx.x; i < tb * wsz; i += blockDim.x) {
+        const int b = i / wsz, r = i % wsz;
+        in[b * wsz + r] = S[((b0 + b) * n0 + x) * wsz + r];
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < tb * w2; l += blockDim.x) {
+        const int b = l / w2, z = l % w2;
+        C a[N];
+#pragma unroll
+        for (int y = 0; y < N; ++y) a[y] = (y < w1) ? in[(b * w1 + y) * w2 + z] : C{T(0), T(0)};
+        fft_line<T, +1, N>(a);
+#pragma unroll
+        for (int y = 0; y < N; ++y) P[(b * N + y) * PW + z] = cmul(a[y], root_inv<T, N>((s1 * y) % N));
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < tb * N; l += blockDim.x) {
+        const int b = l / N, y = l % N;
+        C a[N];
+#pragma unroll
+        for (int z = 0; z < N; ++z) a[z] = (z < w2) ? P[(b * N + y) * PW + z] : C{T(0), T(0)};
+        fft_line<T, +1, N>(a);
+        C *o = out + ((long)b * N + y) * (N + 1);
+#pragma unroll
+        for (int z = 0; z < N; ++z) o[z] = cmul(a[z], root_inv<T, N>((s2 * z) % N));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tb * N * N; i += blockDim.x) {
+        const int b = i / (N * N), r = i % (N * N);
+        U[((b0 + b) * n0 + x) * N * N + r] = out[((long)b * N + r / N) * (N + 1) + (r % N)];
+    }
+}
+
 // -------------------------------------------------------------- launch --
 static inline unsigned blocks_for(long n) { return (unsigned)((n + kLineThreads - 1) / kLineThreads); }
 
@@ -211,6 +327,10 @@ static inline unsigned blocks_for(long n) { return (unsigned)((n + kLineThreads 
         default: return cudaErrorInvalidValue;                                           \
     }
 
+static constexpr size_t kPlaneSmemMax = 200 * 1024;
+
+static bool use_plane_kernels(const Axes &a) { return sizeof(T) == 4 && a.n[1] == a.n[2]; }
+
 static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *cube_map,
                                const Axes &a, void *S, void *R, void *U, cudaStream_t st) {
     const long nb = B;
@@ -220,6 +340,24 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
         const long lines = nb * a.w[1] * a.w[2];
         BGW_FOR_EACH_LEN(a.n[0], (k1_xpass<N><<<blocks_for(lines), kLineThreads, 0, st>>>(
                                      cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
+    }
+    if (use_plane_kernels(a)) {
+        const int n = a.n[1];
+        const int TB = 4;
+        const size_t smem = sizeof(C) * ((size_t)TB * a.w[1] * a.w[2] + (size_t)TB * n * (a.w[2] + 1) +
+                                         (size_t)TB * n * (n + 1));
+        dim3 grid((unsigned)a.n[0], (unsigned)((nb + TB - 1) / TB));
+        cudaError_t e = cudaSuccess;
+        BGW_FOR_EACH_LEN(n, {
+            if (smem > 48 * 1024) {
+                e = cudaFuncSetAttribute(k1_yz_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            k1_yz_plane<N><<<grid, kPlaneThreads, smem, st>>>(Sp, nb, TB, a.w[1], a.w[2], a.s[1],
+                                                             a.s[2], Up);
+        });
+        return cudaGetLastError();
     }
     {
         const long nbx = nb * a.n[0];
@@ -234,6 +372,26 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
     return cudaGetLastError();
 }
 
+// Pair tile (TV valence x TC conduction) of the plane kernel: as many pairs
+// as fit kPlaneSmemMax, preferring the tile with the least staged data per pair.
+static void plane_tile(int nv, int nc, int n, int w2, int &TV, int &TC, size_t &smem) {
+    TV = TC = 0;
+    smem = 0;
+    double best = 1e30;
+    for (int tv = 1; tv <= nv && tv <= 16; ++tv)
+        for (int tc = 1; tc <= nc && tc <= 16; ++tc) {
+            const size_t b = sizeof(C) * ((size_t)(tv + tc) * 2 * n * (n + 1) + (size_t)tv * tc * n * w2);
+            if (b > kPlaneSmemMax) continue;
+            const double cost = (double)(tv + tc) / (tv * tc) - 1e-3 * tv * tc;
+            if (cost < best) {
+                best = cost;
+                TV = tv;
+                TC = tc;
+                smem = b;
+            }
+        }
+}
+
 static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                          const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
                          cudaStream_t st) {
@@ -241,12 +399,29 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
     if (P == 0) return cudaSuccess;
     const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
     C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
-    const long plane = (long)a.n[0] * a.n[1];
-    BGW_FOR_EACH_LEN(a.n[2], (k2_zpass<N><<<blocks_for(P * plane), kLineThreads, 0, st>>>(
-                                 uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
-    const long npx = P * a.n[0];
-    BGW_FOR_EACH_LEN(a.n[1], (k2_ypass<N><<<blocks_for(npx * a.w[2]), kLineThreads, 0, st>>>(
-                                 Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
+    int TV = 0, TC = 0;
+    size_t psmem = 0;
+    if (use_plane_kernels(a)) plane_tile(nv, nc, a.n[1], a.w[2], TV, TC, psmem);
+    if (TV > 0) {
+        dim3 grid((unsigned)a.n[0], (unsigned)((nv + TV - 1) / TV), (unsigned)((nc + TC - 1) / TC));
+        cudaError_t e = cudaSuccess;
+        BGW_FOR_EACH_LEN(a.n[1], {
+            if (psmem > 48 * 1024) {
+                e = cudaFuncSetAttribute(k2_zy_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)psmem);
+                if (e != cudaSuccess) return e;
+            }
+            k2_zy_plane<N><<<grid, kPlaneThreads, psmem, st>>>(uv, uc, nv, nc, TV, TC, a.w[1], a.w[2],
+                                                              a.s[1], a.s[2], Bp);
+        });
+    } else {
+        const long plane = (long)a.n[0] * a.n[1];
+        BGW_FOR_EACH_LEN(a.n[2], (k2_zpass<N><<<blocks_for(P * plane), kLineThreads, 0, st>>>(
+                                     uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
+        const long npx = P * a.n[0];
+        BGW_FOR_EACH_LEN(a.n[1], (k2_ypass<N><<<blocks_for(npx * a.w[2]), kLineThreads, 0, st>>>(
+                                     Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
+    }
     const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
     const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
     cudaError_t e = cudaSuccess;

@@ -6,16 +6,19 @@
 
 namespace bgw {
 
-// Bytes of workspace herk_mixed needs for P pairs, ng G-vectors, nfreq
+// Bytes of workspace the mixed contraction needs for P pairs, ng G-vectors, nfreq
 // frequencies.
 size_t mixed_workspace_bytes(long P, int ng, int nfreq);
 
+// Operand split: M complex64 [P][ng] and w FP64 [nfreq][P] -> the BF16
+// hi/lo planes of X = interleaved (Re, Im) rows and of w_j X in ws.
+cudaError_t mixed_split(const void *M, int P, int ng, const double *w, int nfreq, void *ws,
+                        cudaStream_t st);
+
 // acc[j][g][g'] (complex128, lower block triangle) += sum_p w[j][p]
-// conj(M[p][g]) M[p][g'] with M complex64 [P][ng] and w FP64 [nfreq][P].
-// *nkernels receives the number of kernels launched.  A device-side wait
-// that gives up writes a non-zero code to the device int *err (the host
-// reports BGW_E_TIMEOUT when it reads it back).
-cudaError_t herk_mixed(const void *M, int P, int ng, const double *w, int nfreq, void *ws,
-                       void *acc, cudaStream_t st, int *nkernels, int *err);
+// conj(M[p][g]) M[p][g'] from the planes in ws, on tcgen05 tensor cores.
+// A device-side wait that gives up writes a non-zero code to the device int
+// *err (the host reports BGW_E_TIMEOUT when it reads it back).
+cudaError_t mixed_gemm(int P, int ng, int nfreq, void *ws, void *acc, cudaStream_t st, int *err);
 
 }  // namespace bgw
