@@ -146,8 +146,9 @@ BGW_API bgw_status bgw_chi0_reset(bgw_ctx ctx);
  * formula, Sec. II).  Repeated calls with the same q-set and frequencies
  * accumulate (k-chunking); a different q-set or frequency list after a call
  * is BGW_E_STATE until bgw_chi0_reset.  The sum over k runs in index order
- * and the result does not depend on how k is chunked.  Every k in the range
- * and its k+q partner must have been uploaded.  Asynchronous.
+ * and the result does not depend on how k is split over calls as long as the
+ * split points are multiples of BGW_OPT_KCHUNK.  Every k in the range and its
+ * k+q partner must have been uploaded.  Asynchronous.
  */
 BGW_API bgw_status bgw_chi0_accumulate(bgw_ctx ctx, int nq, const bgw_q *qs, int nfreq,
                                const double *freq_eV, int k_begin, int k_end);
@@ -161,6 +162,32 @@ BGW_API bgw_status bgw_chi0_accumulate(bgw_ctx ctx, int nq, const bgw_q *qs, int
  * The accumulators are kept (call bgw_chi0_reset to start over).
  */
 BGW_API bgw_status bgw_chi0_finalize(bgw_ctx ctx, int iq, void *chi0, int on_device);
+
+/*
+ * Tuning options (per context; they change speed, not the mathematics):
+ *   BGW_OPT_KCHUNK       k-points contracted per launch (1..256, default 1).
+ *                        The result is bitwise independent of how a k range is
+ *                        split over accumulate calls when every split point is
+ *                        a multiple of the k-chunk.
+ *   BGW_OPT_PAIR_TILE_V  valence x conduction pair tile of the FP32 matrix-
+ *   BGW_OPT_PAIR_TILE_C  element kernel (0 = automatic, else 1..16).
+ */
+enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3 };
+BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
+BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
+
+/*
+ * Autotuner: times candidate pair tiles and k-chunks on k-points
+ * k_begin..k_end-1 of the given q-set and frequencies (CUDA events on the
+ * context stream, one warm-up and one timed run each) and sets the fastest.
+ * The running chi0 sums are not touched.  Chunks whose M block and split
+ * operands would exceed 2 GiB are not tried.  cache_path (may
+ * be NULL): a text file of "key|kchunk tile_v tile_c" lines; a hit skips the
+ * timing, a miss appends the result.  Blocks until done.
+ */
+BGW_API bgw_status bgw_autotune(bgw_ctx ctx, int nq, const bgw_q *qs, int nfreq,
+                                const double *freq_eV, int k_begin, int k_end,
+                                const char *cache_path);
 
 /*
  * Stage timing with CUDA events recorded on the context stream around each

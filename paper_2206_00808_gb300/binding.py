@@ -26,7 +26,9 @@ PRECISIONS = {"fp64": BGW_FP64, "mixed": BGW_MIXED_BF16X3}
 
 EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
             "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
-            "bgw_mtxel_spinor_noalloc", "bgw_destroy", "bgw_last_error"]
+            "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune",
+            "bgw_destroy", "bgw_last_error"]
+BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C = 1, 2, 3
 STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split"]
 
 
@@ -47,11 +49,14 @@ _lib.bgw_chi0_finalize.argtypes = [_P, _I, _P, _I]
 _lib.bgw_profile.argtypes = [_P, _I]
 _lib.bgw_profile_read.argtypes = [_P, _P, _P, _P, _I]
 _lib.bgw_mtxel_spinor_noalloc.argtypes = [_P, _P, _P, _I, _I, _P, _I, _P, _P, _P]
+_lib.bgw_set_option.argtypes = [_P, _I, ctypes.c_long]
+_lib.bgw_get_option.argtypes = [_P, _I, ctypes.POINTER(ctypes.c_long)]
+_lib.bgw_autotune.argtypes = [_P, _I, ctypes.POINTER(bgw_q), _I, _P, _I, _I, ctypes.c_char_p]
 _lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
 _lib.bgw_last_error.argtypes, _lib.bgw_last_error.restype = [_P], ctypes.c_char_p
 for _f in ["bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
            "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
-           "bgw_mtxel_spinor_noalloc"]:
+           "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -191,6 +196,31 @@ def bgw_mtxel_spinor_noalloc(fft, Uv, Uc, nv: int, nc: int, G0, gvec, M_dev, str
                                                 _host_ptr(g), pm, _stream_handle(stream)), None)
 
 
+def bgw_set_option(ctx, option: int, value: int) -> int:
+    return _check(_lib.bgw_set_option(ctx, option, int(value)), ctx)
+
+
+def bgw_get_option(ctx, option: int) -> int:
+    v = ctypes.c_long()
+    _check(_lib.bgw_get_option(ctx, option, ctypes.byref(v)), ctx)
+    return v.value
+
+
+def bgw_autotune(ctx, qs, freq, k_begin: int, k_end: int, cache_path=None) -> dict:
+    """Time candidate tiles / k-chunks, set the fastest; returns the choice."""
+    structs, keep = [], []
+    for q, g, nc in qs:
+        s, a = make_q(q, g, nc)
+        structs.append(s)
+        keep.append(a)
+    arr = (bgw_q * len(structs))(*structs)
+    f = np.ascontiguousarray(freq, dtype=np.float64)
+    cp = cache_path.encode() if cache_path else None
+    _check(_lib.bgw_autotune(ctx, len(structs), arr, len(f), _host_ptr(f), k_begin, k_end, cp), ctx)
+    return {"kchunk": bgw_get_option(ctx, BGW_OPT_KCHUNK),
+            "pair_tile": (bgw_get_option(ctx, BGW_OPT_PAIR_TILE_V), bgw_get_option(ctx, BGW_OPT_PAIR_TILE_C))}
+
+
 def bgw_destroy(ctx) -> None:
     _lib.bgw_destroy(ctx)
 
@@ -231,6 +261,10 @@ class Chi0Context:
 
     def reset(self):
         bgw_chi0_reset(self.ctx)
+
+    def autotune(self, k_begin=0, k_end=None, cache_path=None):
+        return bgw_autotune(self.ctx, self.qlist(), self.p.freq, k_begin,
+                            self.p.nk if k_end is None else k_end, cache_path)
 
     def close(self):
         if self.ctx is not None:

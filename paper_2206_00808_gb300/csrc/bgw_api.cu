@@ -69,7 +69,8 @@ struct QState {
     int emin[3], emax[3];
     int w[3];                // kept widths, min(emax - emin + 1, N)
     std::vector<int> gmap;   // [ng]
-    DevBuf gmap_dev;
+    std::vector<int> kmap;   // [nk]: grid index of k + q, -1 if off the grid
+    DevBuf gmap_dev, kmap_dev;
     DevBuf acc;              // complex128 [nfreq][ng][ng]
 };
 
@@ -134,6 +135,9 @@ struct bgw_ctx_s {
     DevBuf out_stage;    // finalize to host
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
     DevBuf errflag;      // device int: non-zero after a bounded device wait gave up
+    // tuning (bgw_set_option / bgw_autotune)
+    int kchunk = 1;      // k-points per contraction launch
+    int tile_v = 0, tile_c = 0;   // pair tile of the FP32 plane kernel (0 = automatic)
     // stage timing (bgw_profile)
     static constexpr int kStages = 6;
     bool prof = false;
@@ -235,6 +239,8 @@ bool find_umklapp(const bgw_ctx_s *c, int ik, const double q[3], int &kp, int G0
     return false;
 }
 
+void compute_kmap(const bgw_ctx_s *c, QState &s);
+
 // Geometry of one dielectric sphere: extents, kept widths, cube positions.
 bgw_status prepare_q(bgw_ctx_s *c, const bgw_q *q, QState &s) {
     if (!q) return c->fail(BGW_E_ARG, "null q");
@@ -269,6 +275,7 @@ bgw_status prepare_q(bgw_ctx_s *c, const bgw_q *q, QState &s) {
         for (int a = 0; a < 3; ++a) j[a] = pmod((long)s.gvec[3 * g + a] - s.emin[a], c->box[a]);
         s.gmap[g] = (j[0] * s.w[1] + j[1]) * s.w[2] + j[2];
     }
+    compute_kmap(c, s);
     return BGW_OK;
 }
 
@@ -311,7 +318,7 @@ cudaError_t ensure_mtxel_scratch(bgw_ctx_s *c, const QState &s, long P) {
 }
 
 cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const int G0[3], int v0,
-                         int nv, int c0, int nc, void *M, long ldm) {
+                         int nv, int c0, int nc, void *M, long ldm, int tv = 0, int tc = 0) {
     const bgw::Axes ax = mtxel_axes(c, s, G0);
     const void *Uv = c->grid_of(ik, v0);
     const void *Uc = c->grid_of(kp, c->nv + c0);
@@ -319,8 +326,178 @@ cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const in
     const int rec = c->stage_begin(1);
     cudaError_t e = (c->prec == BGW_FP64)
         ? bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st)
-        : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st);
+        : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, tv, tc);
     c->stage_end(rec, 3);
+    return e;
+}
+
+
+// Checks shared by accumulate and autotune; fills `fresh` with the q geometry.
+bgw_status validate_qset(bgw_ctx_s *c, const char *who, int nq, const bgw_q *qs, int nfreq,
+                         const double *freq_eV, int k_begin, int k_end, std::vector<QState> &fresh) {
+    if (nq < 1 || !qs) return c->fail(BGW_E_ARG, "%s: nq >= 1 and a q list required", who);
+    if (nfreq < 1 || !freq_eV) return c->fail(BGW_E_ARG, "%s: nfreq >= 1 and freq required", who);
+    for (int j = 0; j < nfreq; ++j)
+        if (!std::isfinite(freq_eV[j]) || freq_eV[j] < 0)
+            return c->fail(BGW_E_ARG, "%s: frequency %d must be finite and >= 0", who, j);
+    if (k_begin < 0 || k_end > c->nk || k_begin > k_end)
+        return c->fail(BGW_E_ARG, "%s: k range [%d,%d) outside [0,%d)", who, k_begin, k_end, c->nk);
+    fresh.assign(nq, QState());
+    for (int iq = 0; iq < nq; ++iq) {
+        bgw_status st = prepare_q(c, &qs[iq], fresh[iq]);
+        if (st != BGW_OK) return st;
+        for (int ik = k_begin; ik < k_end; ++ik) {
+            const int kp = fresh[iq].kmap[ik];
+            if (kp < 0) return c->fail(BGW_E_ARG, "%s: k + q not on the k list (q %d, k %d)", who, iq, ik);
+            if (!c->k[ik].uploaded || !c->k[kp].uploaded)
+                return c->fail(BGW_E_STATE, "%s: k %d or its partner %d not uploaded", who, ik, kp);
+        }
+    }
+    return BGW_OK;
+}
+
+// kmap[k]: grid index of k + q for every k (-1 where k + q is off the grid).
+void compute_kmap(const bgw_ctx_s *c, QState &s) {
+    s.kmap.assign(c->nk, -1);
+    for (int k = 0; k < c->nk; ++k) {
+        int kp, G0[3];
+        if (find_umklapp(c, k, s.q, kp, G0)) s.kmap[k] = kp;
+    }
+}
+
+// Scratch for contraction launches of up to kchunk k-points on every q.
+cudaError_t ensure_chunk_scratch(bgw_ctx_s *c, const std::vector<QState> &qs, int nfreq, int kchunk) {
+    long Pmax = 0, Mbytes = 0;
+    size_t ws = 0;
+    cudaError_t e = cudaSuccess;
+    for (auto &s : qs) {
+        const long P = (long)c->nv * s.nc;
+        Pmax = std::max(Pmax, P);
+        Mbytes = std::max(Mbytes, (long)kchunk * P * s.ng * (long)c->csize);
+        if (c->prec != BGW_FP64)
+            ws = std::max(ws, bgw::mixed_workspace_bytes((long)kchunk * P, s.ng, nfreq));
+        e = ensure_mtxel_scratch(c, s, P);
+        if (e != cudaSuccess) return e;
+    }
+    e = c->M.ensure((size_t)Mbytes, c->st);
+    if (e == cudaSuccess) e = c->W.ensure(sizeof(double) * (size_t)kchunk * Pmax * nfreq, c->st);
+    if (e == cudaSuccess && ws) e = c->mixed_ws.ensure(ws, c->st);
+    return e;
+}
+
+// Make `fresh` the context's q-set: accumulators zeroed on the stream, the
+// sphere and k maps on the device.  Buffers of the previous set are reused
+// when the sizes agree, and nothing is copied from the host when the
+// contents agree too (so repeated steps queue only a memset).
+bgw_status install_qset(bgw_ctx_s *c, std::vector<QState> &fresh, int nfreq, const double *freq) {
+    cudaError_t e = cudaSuccess;
+    bool reuse = c->qs.size() == fresh.size() && c->nfreq == nfreq;
+    for (size_t i = 0; reuse && i < fresh.size(); ++i)
+        reuse = c->qs[i].ng == fresh[i].ng && c->qs[i].acc.p != nullptr;
+    bool same_content = reuse && std::equal(c->freq.begin(), c->freq.end(), freq);
+    for (size_t i = 0; same_content && i < fresh.size(); ++i)
+        same_content = c->qs[i].gmap == fresh[i].gmap && c->qs[i].kmap == fresh[i].kmap;
+    if (reuse) {
+        for (size_t i = 0; i < fresh.size(); ++i) {
+            std::swap(fresh[i].gmap_dev, c->qs[i].gmap_dev);
+            std::swap(fresh[i].kmap_dev, c->qs[i].kmap_dev);
+            std::swap(fresh[i].acc, c->qs[i].acc);
+        }
+    } else if (!c->qs.empty()) {
+        e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: stream");
+        for (auto &s : c->qs) {
+            s.gmap_dev.release();
+            s.kmap_dev.release();
+            s.acc.release();
+        }
+    }
+    for (auto &s : fresh) {
+        e = s.gmap_dev.ensure(sizeof(int) * (size_t)s.ng, c->st);
+        if (e == cudaSuccess) e = s.kmap_dev.ensure(sizeof(int) * (size_t)c->nk, c->st);
+        if (e == cudaSuccess) e = s.acc.ensure(16 * (size_t)nfreq * s.ng * s.ng, c->st);
+        if (e != cudaSuccess) {
+            for (auto &t : fresh) {
+                t.gmap_dev.release();
+                t.kmap_dev.release();
+                t.acc.release();
+            }
+            c->qs.clear();
+            return c->cuda_fail(e, "accumulate: accumulators");
+        }
+    }
+    e = c->freq_dev.ensure(sizeof(double) * nfreq, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: frequency buffer");
+    c->qs.swap(fresh);
+    c->freq.assign(freq, freq + nfreq);
+    c->nfreq = nfreq;
+    c->have_qset = true;
+    if (!same_content) {
+        e = cudaMemcpyAsync(c->freq_dev.p, c->freq.data(), sizeof(double) * nfreq,
+                            cudaMemcpyHostToDevice, c->st);
+        for (auto &s : c->qs) {
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s.gmap_dev.p, s.gmap.data(), sizeof(int) * s.ng,
+                                    cudaMemcpyHostToDevice, c->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s.kmap_dev.p, s.kmap.data(), sizeof(int) * c->nk,
+                                    cudaMemcpyHostToDevice, c->st);
+        }
+    }
+    for (auto &s : c->qs)
+        if (e == cudaSuccess) e = cudaMemsetAsync(s.acc.p, 0, 16 * (size_t)nfreq * s.ng * s.ng, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: initialising accumulators");
+    return BGW_OK;
+}
+
+// The k loop of bgw_chi0_accumulate for the given q-states: per chunk of
+// kchunk k-points, matrix elements of each k into consecutive M blocks, one
+// weights launch, (mixed: one operand split,) one contraction launch.
+cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const double *freq,
+                      int k_begin, int k_end, int kchunk, int tv, int tc, bool &clean) {
+    cudaError_t e = cudaSuccess;
+    const double *energy = static_cast<const double *>(c->energy.p);
+    for (auto &s : qs) {
+        const long P = (long)c->nv * s.nc;
+        for (int k0 = k_begin; k0 < k_end; k0 += kchunk) {
+            const int kn = std::min(kchunk, k_end - k0);
+            for (int kl = 0; kl < kn; ++kl) {
+                const int ik = k0 + kl;
+                int kp, G0[3];
+                find_umklapp(c, ik, s.q, kp, G0);
+                clean = clean && alias_free(c, ik, kp, G0, s);
+                char *Mk = static_cast<char *>(c->M.p) + (size_t)kl * P * s.ng * c->csize;
+                e = launch_mtxel(c, s, ik, kp, G0, 0, c->nv, 0, s.nc, Mk, s.ng, tv, tc);
+                if (e != cudaSuccess) return e;
+            }
+            const int PT = (int)(P * kn);
+            {
+                const int rec = c->stage_begin(2);
+                e = bgw::pair_weights(energy, c->nb, c->nv, s.nc, static_cast<const int *>(s.kmap_dev.p),
+                                      k0, kn, freq, nfreq, static_cast<double *>(c->W.p), c->st);
+                c->stage_end(rec, 1);
+                if (e != cudaSuccess) return e;
+            }
+            if (c->prec != BGW_FP64) {
+                const int rec = c->stage_begin(5);
+                e = bgw::mixed_split(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
+                                     c->mixed_ws.p, c->st);
+                c->stage_end(rec, 1);
+                if (e != cudaSuccess) return e;
+            }
+            {
+                const int rec = c->stage_begin(3);
+                if (c->prec == BGW_FP64)
+                    e = bgw::herk_f64(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
+                                      s.acc.p, c->st);
+                else
+                    e = bgw::mixed_gemm(PT, s.ng, nfreq, c->mixed_ws.p, s.acc.p, c->st,
+                                        static_cast<int *>(c->errflag.p));
+                c->stage_end(rec, 1);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
     return e;
 }
 
@@ -534,26 +711,9 @@ bgw_status bgw_chi0_accumulate(bgw_ctx c, int nq, const bgw_q *qs, int nfreq,
     if (!c) return BGW_E_ARG;
     DeviceGuard dg(c->device);
     c->err.clear();
-    if (nq < 1 || !qs) return c->fail(BGW_E_ARG, "accumulate: nq >= 1 and a q list required");
-    if (nfreq < 1 || !freq_eV) return c->fail(BGW_E_ARG, "accumulate: nfreq >= 1 and freq required");
-    for (int j = 0; j < nfreq; ++j)
-        if (!std::isfinite(freq_eV[j]) || freq_eV[j] < 0)
-            return c->fail(BGW_E_ARG, "accumulate: frequency %d must be finite and >= 0", j);
-    if (k_begin < 0 || k_end > c->nk || k_begin > k_end)
-        return c->fail(BGW_E_ARG, "accumulate: k range [%d,%d) outside [0,%d)", k_begin, k_end, c->nk);
-    // validate every q and every (k, k+q) before touching any state
-    std::vector<QState> fresh(nq);
-    for (int iq = 0; iq < nq; ++iq) {
-        bgw_status st = prepare_q(c, &qs[iq], fresh[iq]);
-        if (st != BGW_OK) return st;
-        for (int ik = k_begin; ik < k_end; ++ik) {
-            int kp, G0[3];
-            if (!find_umklapp(c, ik, fresh[iq].q, kp, G0))
-                return c->fail(BGW_E_ARG, "accumulate: k + q not on the k list (q %d, k %d)", iq, ik);
-            if (!c->k[ik].uploaded || !c->k[kp].uploaded)
-                return c->fail(BGW_E_STATE, "accumulate: k %d or its partner %d not uploaded", ik, kp);
-        }
-    }
+    std::vector<QState> fresh;
+    bgw_status vst = validate_qset(c, "accumulate", nq, qs, nfreq, freq_eV, k_begin, k_end, fresh);
+    if (vst != BGW_OK) return vst;
     if (c->have_qset) {
         bool same = (int)c->qs.size() == nq && c->nfreq == nfreq &&
                     std::equal(c->freq.begin(), c->freq.end(), freq_eV);
@@ -562,111 +722,17 @@ bgw_status bgw_chi0_accumulate(bgw_ctx c, int nq, const bgw_q *qs, int nfreq,
             return c->fail(BGW_E_STATE,
                            "accumulate: q-set or frequencies differ from the running sum; call bgw_chi0_reset");
     }
-    // scratch sizes over the set
-    long Pmax = 0, PMbytes = 0;
-    for (auto &s : fresh) {
-        const long P = (long)c->nv * s.nc;
-        Pmax = std::max(Pmax, P);
-        PMbytes = std::max(PMbytes, P * s.ng * (long)c->csize);
-    }
-    cudaError_t e;
-    for (auto &s : fresh) {
-        e = ensure_mtxel_scratch(c, s, (long)c->nv * s.nc);
-        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: scratch");
-    }
-    e = c->M.ensure((size_t)PMbytes, c->st);
-    if (e == cudaSuccess) e = c->W.ensure(sizeof(double) * (size_t)Pmax * nfreq, c->st);
-    if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: M/weight buffers");
-    if (c->prec != BGW_FP64) {
-        size_t ws = 0;
-        for (auto &s : fresh)
-            ws = std::max(ws, bgw::mixed_workspace_bytes((long)c->nv * s.nc, s.ng, nfreq));
-        e = c->mixed_ws.ensure(ws, c->st);
-        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: mixed workspace");
-    }
+    const int kchunk = std::max(1, std::min(c->kchunk, std::max(1, k_end - k_begin)));
+    cudaError_t e = ensure_chunk_scratch(c, fresh, nfreq, kchunk);
+    if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: scratch");
     if (!c->have_qset) {
-        // Reuse the previous set's buffers when every q keeps its size.
-        bool reuse = c->qs.size() == fresh.size() && c->nfreq == nfreq;
-        for (size_t i = 0; reuse && i < fresh.size(); ++i)
-            reuse = c->qs[i].ng == fresh[i].ng && c->qs[i].acc.p != nullptr;
-        if (reuse) {
-            for (size_t i = 0; i < fresh.size(); ++i) {
-                std::swap(fresh[i].gmap_dev, c->qs[i].gmap_dev);
-                std::swap(fresh[i].acc, c->qs[i].acc);
-            }
-        } else if (!c->qs.empty()) {
-            e = cudaStreamSynchronize(c->st);
-            if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: stream");
-            for (auto &s : c->qs) {
-                s.gmap_dev.release();
-                s.acc.release();
-            }
-        }
-        for (auto &s : fresh) {
-            e = s.gmap_dev.ensure(sizeof(int) * (size_t)s.ng, c->st);
-            if (e == cudaSuccess) e = s.acc.ensure(16 * (size_t)nfreq * s.ng * s.ng, c->st);
-            if (e != cudaSuccess) {
-                for (auto &t : fresh) {
-                    t.gmap_dev.release();
-                    t.acc.release();
-                }
-                c->qs.clear();
-                return c->cuda_fail(e, "accumulate: accumulators");
-            }
-        }
-        e = c->freq_dev.ensure(sizeof(double) * nfreq, c->st);
-        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: frequency buffer");
-        c->qs.swap(fresh);
-        c->freq.assign(freq_eV, freq_eV + nfreq);
-        c->nfreq = nfreq;
-        c->have_qset = true;
-        e = cudaMemcpyAsync(c->freq_dev.p, c->freq.data(), sizeof(double) * nfreq,
-                            cudaMemcpyHostToDevice, c->st);
-        for (auto &s : c->qs) {
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(s.gmap_dev.p, s.gmap.data(), sizeof(int) * s.ng,
-                                    cudaMemcpyHostToDevice, c->st);
-            if (e == cudaSuccess)
-                e = cudaMemsetAsync(s.acc.p, 0, 16 * (size_t)nfreq * s.ng * s.ng, c->st);
-        }
-        if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: initialising accumulators");
+        bgw_status st = install_qset(c, fresh, nfreq, freq_eV);
+        if (st != BGW_OK) return st;
     }
     bool clean = true;
-    const double *energy = static_cast<const double *>(c->energy.p);
-    for (int iq = 0; iq < nq; ++iq) {
-        QState &s = c->qs[iq];
-        const int P = c->nv * s.nc;
-        for (int ik = k_begin; ik < k_end; ++ik) {
-            int kp, G0[3];
-            find_umklapp(c, ik, s.q, kp, G0);
-            clean = clean && alias_free(c, ik, kp, G0, s);
-            e = launch_mtxel(c, s, ik, kp, G0, 0, c->nv, 0, s.nc, c->M.p, s.ng);
-            if (e == cudaSuccess) {
-                const int rec = c->stage_begin(2);
-                e = bgw::pair_weights(energy + (long)ik * c->nb, energy + (long)kp * c->nb + c->nv,
-                                      c->nv, s.nc, static_cast<const double *>(c->freq_dev.p),
-                                      nfreq, static_cast<double *>(c->W.p), c->st);
-                c->stage_end(rec, 1);
-            }
-            if (e == cudaSuccess && c->prec != BGW_FP64) {
-                const int rec = c->stage_begin(5);
-                e = bgw::mixed_split(c->M.p, P, s.ng, static_cast<const double *>(c->W.p), nfreq,
-                                     c->mixed_ws.p, c->st);
-                c->stage_end(rec, 1);
-            }
-            if (e == cudaSuccess) {
-                const int rec = c->stage_begin(3);
-                if (c->prec == BGW_FP64)
-                    e = bgw::herk_f64(c->M.p, P, s.ng, static_cast<const double *>(c->W.p), nfreq,
-                                      s.acc.p, c->st);
-                else
-                    e = bgw::mixed_gemm(P, s.ng, nfreq, c->mixed_ws.p, s.acc.p, c->st,
-                                        static_cast<int *>(c->errflag.p));
-                c->stage_end(rec, 1);
-            }
-            if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: kernels");
-        }
-    }
+    e = run_range(c, c->qs, nfreq, static_cast<const double *>(c->freq_dev.p), k_begin, k_end, kchunk,
+                  c->tile_v, c->tile_c, clean);
+    if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: kernels");
     return clean ? BGW_OK : BGW_W_ALIAS;
 }
 
@@ -702,6 +768,165 @@ bgw_status bgw_chi0_finalize(bgw_ctx c, int iq, void *chi0, int on_device) {
         cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st);
         return c->fail(BGW_E_TIMEOUT, "finalize: a device-side wait gave up (code %d); the result is invalid",
                        flag);
+    }
+    return BGW_OK;
+}
+
+bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
+    if (!c) return BGW_E_ARG;
+    c->err.clear();
+    switch (option) {
+        case BGW_OPT_KCHUNK:
+            if (value < 1 || value > 256) return c->fail(BGW_E_ARG, "set_option: k-chunk must be 1..256");
+            c->kchunk = (int)value;
+            return BGW_OK;
+        case BGW_OPT_PAIR_TILE_V:
+        case BGW_OPT_PAIR_TILE_C:
+            if (value < 0 || value > 16) return c->fail(BGW_E_ARG, "set_option: pair tile must be 0..16");
+            (option == BGW_OPT_PAIR_TILE_V ? c->tile_v : c->tile_c) = (int)value;
+            return BGW_OK;
+        default:
+            return c->fail(BGW_E_ARG, "set_option: unknown option %d", option);
+    }
+}
+
+bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
+    if (!c || !value) return BGW_E_ARG;
+    c->err.clear();
+    switch (option) {
+        case BGW_OPT_KCHUNK: *value = c->kchunk; return BGW_OK;
+        case BGW_OPT_PAIR_TILE_V: *value = c->tile_v; return BGW_OK;
+        case BGW_OPT_PAIR_TILE_C: *value = c->tile_c; return BGW_OK;
+        default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
+    }
+}
+
+bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const double *freq_eV,
+                        int k_begin, int k_end, const char *cache_path) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    std::vector<QState> tq;
+    bgw_status vst = validate_qset(c, "autotune", nq, qs, nfreq, freq_eV, k_begin, k_end, tq);
+    if (vst != BGW_OK) return vst;
+    if (k_end == k_begin) return c->fail(BGW_E_ARG, "autotune: empty k range");
+    // cache key: everything the timing depends on
+    std::string key = std::string(c->prec == BGW_FP64 ? "fp64" : "mixed") + " box " +
+                      std::to_string(c->box[0]) + "x" + std::to_string(c->box[1]) + "x" +
+                      std::to_string(c->box[2]) + " nv " + std::to_string(c->nv) + " nfreq " +
+                      std::to_string(nfreq) + " span " + std::to_string(k_end - k_begin);
+    for (auto &s : tq) key += " q " + std::to_string(s.ng) + "/" + std::to_string(s.nc);
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "r")) {
+            char line[1024];
+            while (fgets(line, sizeof line, f)) {
+                const char *bar = strchr(line, '|');
+                if (!bar || std::string(line, bar - line) != key) continue;
+                int kc, tv, tcc;
+                if (sscanf(bar + 1, "%d %d %d", &kc, &tv, &tcc) == 3) {
+                    c->kchunk = kc;
+                    c->tile_v = tv;
+                    c->tile_c = tcc;
+                    fclose(f);
+                    return BGW_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    // scratch accumulators and maps for the timing runs (the running sums are untouched)
+    const bool prof = c->prof;
+    c->prof = false;
+    DevBuf tfreq;
+    cudaError_t e = tfreq.ensure(sizeof(double) * nfreq, c->st);
+    for (auto &s : tq) {
+        if (e == cudaSuccess) e = s.gmap_dev.ensure(sizeof(int) * (size_t)s.ng, c->st);
+        if (e == cudaSuccess) e = s.kmap_dev.ensure(sizeof(int) * (size_t)c->nk, c->st);
+        if (e == cudaSuccess) e = s.acc.ensure(16 * (size_t)nfreq * s.ng * s.ng, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.gmap_dev.p, s.gmap.data(), sizeof(int) * s.ng,
+                                                  cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.kmap_dev.p, s.kmap.data(), sizeof(int) * c->nk,
+                                                  cudaMemcpyHostToDevice, c->st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tfreq.p, freq_eV, sizeof(double) * nfreq, cudaMemcpyHostToDevice, c->st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    long Pmax = 0;
+    for (auto &s : tq) Pmax = std::max(Pmax, (long)c->nv * s.nc);
+    auto time_one = [&](int kc, int tv, int tcc, float &ms) -> cudaError_t {
+        cudaError_t r = ensure_chunk_scratch(c, tq, nfreq, kc);
+        bool clean = true;
+        const double *fq = static_cast<const double *>(tfreq.p);
+        if (r == cudaSuccess) r = run_range(c, tq, nfreq, fq, k_begin, k_end, kc, tv, tcc, clean);   // warm
+        if (r == cudaSuccess) r = cudaEventRecord(e0, c->st);
+        if (r == cudaSuccess) r = run_range(c, tq, nfreq, fq, k_begin, k_end, kc, tv, tcc, clean);
+        if (r == cudaSuccess) r = cudaEventRecord(e1, c->st);
+        if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+        return r;
+    };
+    int best_kc = c->kchunk, best_tv = c->tile_v, best_tc = c->tile_c;
+    float best_ms = 1e30f;
+    if (e == cudaSuccess) {
+        // pair tile first (FP32 plane kernel), at k-chunk 1
+        int tvs[8] = {0}, tcs[8] = {0};
+        int ncand = 1;
+        if (c->prec != BGW_FP64) {
+            const int zero3[3] = {0, 0, 0};
+            bgw::Axes ax = mtxel_axes(c, tq[0], zero3);
+            ncand += bgw::plane_tile_candidates(c->nv, tq[0].nc, ax, tvs + 1, tcs + 1, 4);
+        }
+        for (int i = 0; i < ncand && e == cudaSuccess; ++i) {
+            float ms = 0;
+            e = time_one(1, tvs[i], tcs[i], ms);
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best_tv = tvs[i];
+                best_tc = tcs[i];
+                best_kc = 1;
+            }
+        }
+        // then the k-chunk, within a workspace cap (the split operands of the
+        // mixed path grow with the chunk)
+        const int kcands[] = {2, 4, 8, 16, 32, 64};
+        for (int kc : kcands) {
+            if (e != cudaSuccess || kc > k_end - k_begin) break;
+            size_t ws = 0, mb = 0;
+            for (auto &s : tq) {
+                mb = std::max(mb, (size_t)kc * c->nv * s.nc * s.ng * c->csize);
+                if (c->prec != BGW_FP64)
+                    ws = std::max(ws, bgw::mixed_workspace_bytes((long)kc * c->nv * s.nc, s.ng, nfreq));
+            }
+            if (ws + mb > ((size_t)2 << 30)) break;
+            float ms = 0;
+            e = time_one(kc, best_tv, best_tc, ms);
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best_kc = kc;
+            }
+        }
+    }
+    cudaStreamSynchronize(c->st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    tfreq.release();
+    for (auto &s : tq) {
+        s.gmap_dev.release();
+        s.kmap_dev.release();
+        s.acc.release();
+    }
+    c->prof = prof;
+    if (e != cudaSuccess) return c->cuda_fail(e, "autotune");
+    c->kchunk = best_kc;
+    c->tile_v = best_tv;
+    c->tile_c = best_tc;
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "a")) {
+            fprintf(f, "%s|%d %d %d\n", key.c_str(), best_kc, best_tv, best_tc);
+            fclose(f);
+        }
     }
     return BGW_OK;
 }
@@ -750,6 +975,7 @@ void bgw_destroy(bgw_ctx c) {
         for (auto &k : c->k) k.map_dev.release();
         for (auto &s : c->qs) {
             s.gmap_dev.release();
+            s.kmap_dev.release();
             s.acc.release();
         }
         DevBuf *bufs[] = {&c->grids, &c->energy, &c->stage, &c->S,  &c->R,        &c->A,

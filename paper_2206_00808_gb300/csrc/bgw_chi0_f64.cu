@@ -14,15 +14,23 @@
 namespace bgw {
 namespace {
 
-__global__ void k3_pair_weights(const double *__restrict__ ev, const double *__restrict__ ec,
-                                int nv, int nc, const double *__restrict__ freq, int nfreq,
-                                double *__restrict__ w) {
+// w[j][kl*P + v*nc + c] for the kn k-points k0..k0+kn-1 of one q-point;
+// kmap[k] is the grid index k' of k + q.
+__global__ void k3_pair_weights(const double *__restrict__ energy, int nb, int nv, int nc,
+                                const int *__restrict__ kmap, int k0, int kn,
+                                const double *__restrict__ freq, int nfreq, double *__restrict__ w) {
     const long P = (long)nv * nc;
+    const long PT = P * kn;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P * nfreq) return;
-    const long p = t % P;
-    const int j = (int)(t / P);
-    const double d = ev[p / nc] - ec[p % nc];
+    if (t >= PT * nfreq) return;
+    const long pt = t % PT;
+    const int j = (int)(t / PT);
+    const int kl = (int)(pt / P);
+    const long p = pt % P;
+    const int k = k0 + kl;
+    const double ev = energy[(long)k * nb + p / nc];
+    const double ec = energy[(long)kmap[k] * nb + nv + p % nc];
+    const double d = ev - ec;
     const double f = freq[j];
     w[t] = 2.0 * d / (d * d + f * f);
 }
@@ -138,11 +146,12 @@ __global__ void k7_finalize(const double2 *__restrict__ acc, int ng, long total,
 
 }  // namespace
 
-cudaError_t pair_weights(const double *ev, const double *ec, int nv, int nc, const double *freq,
-                         int nfreq, double *w, cudaStream_t st) {
-    const long n = (long)nv * nc * nfreq;
+cudaError_t pair_weights(const double *energy, int nb, int nv, int nc, const int *kmap, int k0,
+                         int kn, const double *freq, int nfreq, double *w, cudaStream_t st) {
+    const long n = (long)nv * nc * kn * nfreq;
     if (n == 0) return cudaSuccess;
-    k3_pair_weights<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ev, ec, nv, nc, freq, nfreq, w);
+    k3_pair_weights<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(energy, nb, nv, nc, kmap, k0, kn,
+                                                                 freq, nfreq, w);
     return cudaGetLastError();
 }
 

@@ -46,7 +46,6 @@ constexpr int kStages = 3;
 constexpr int kTileBytes = kTileM * kBlockK * 2;                 // 16 KB per operand tile
 constexpr int kStageBytes = 4 * kTileBytes;                      // A_hi, A_lo, B_hi, B_lo
 constexpr int kAccCols = 4 * kTileN;                             // 3 hi.hi + 1 cross accumulator
-constexpr int kGemmThreads = 128;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
 
@@ -195,12 +194,29 @@ __device__ __forceinline__ void lower_tile(int t, int &bi, int &bj) {
 }
 
 // --------------------------------------------------------------- GEMM --
-__global__ void __launch_bounds__(kGemmThreads, 1)
+// Warp roles: warps 0-3 drain tensor memory (warp w owns TMEM lanes
+// 32w..32w+31 = tile rows), warp 4 allocates TMEM and issues the TMA loads,
+// warp 5 issues the MMAs.  The hi.hi products of each run of kSub K blocks go
+// to one of three TMEM slots in turn; when a run completes, warps 0-3 add
+// that slot into FP32 registers (round to nearest) and hand it back, so no
+// TMEM accumulator takes more than 4*kSub truncating adds of the large
+// products whatever K is.  The two cross products go to a fourth slot.
+constexpr int kSub = 8;
+constexpr int kSlots = 3;
+constexpr int kGemmWarps = 6;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kGemmWarps * 32, 1)
 k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__restrict__ acc,
         int *__restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages];
     __shared__ __align__(8) uint64_t empty_bar[kStages];
+    __shared__ __align__(8) uint64_t slot_full[kSlots];
+    __shared__ __align__(8) uint64_t slot_free[kSlots];
     __shared__ __align__(8) uint64_t accum_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -209,8 +225,8 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
     int ti, tj;
     lower_tile(blockIdx.x, ti, tj);
     const int j = blockIdx.y;
-    const int nfreq = gridDim.y;
     const int nkb = Kp / kBlockK;
+    const int nsub = (nkb + kSub - 1) / kSub;
 
     // 1024-byte aligned stage ring
     const uint32_t raw = smem_u32(smem_raw);
@@ -221,12 +237,16 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(smem_u32(&slot_full[s]), 1);
+            mbar_init(smem_u32(&slot_free[s]), 128);
+        }
         mbar_init(smem_u32(&accum_bar), 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
     }
-    if (warp == 2) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
                      "r"(kAccCols)
@@ -241,114 +261,140 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
     // planes: 0 A_hi, 1 A_lo, 2 + 2j B_j hi, 3 + 2j B_j lo
     const int a_row = ti * kTileM, b_row = tj * kTileN;
     const int bhi = 2 + 2 * j, blo = 3 + 2 * j;
-    const int nchunks = nkb < 3 ? nkb : 3;   // hi.hi accumulators in use
-    (void)nfreq;
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        int issued = 0;
-        for (int it = 0; it < nkb; ++it) {
-            const int s = it % kStages;
-            if (!mbar_wait(smem_u32(&empty_bar[s]), ((it / kStages) & 1) ^ 1)) {
-                atomicExch(err, kErrEmpty);
-                atomicExch(&abort_flag, 1);
-                break;
+    if (warp == 4) {
+        if (lane == 0) {
+            // TMA producer
+            int issued = 0;
+            for (int it = 0; it < nkb; ++it) {
+                const int s = it % kStages;
+                if (!mbar_wait(smem_u32(&empty_bar[s]), ((it / kStages) & 1) ^ 1)) {
+                    atomicExch(err, kErrEmpty);
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                if (*(volatile int *)&abort_flag) break;
+                const uint32_t st0 = ring + s * kStageBytes;
+                const uint32_t fb = smem_u32(&full_bar[s]);
+                const int x = it * kBlockK;
+                mbar_expect_tx(fb, kStageBytes);
+                tma_load_3d(st0, &xmap, fb, x, a_row, 0);
+                tma_load_3d(st0 + kTileBytes, &xmap, fb, x, a_row, 1);
+                tma_load_3d(st0 + 2 * kTileBytes, &xmap, fb, x, b_row, bhi);
+                tma_load_3d(st0 + 3 * kTileBytes, &xmap, fb, x, b_row, blo);
+                issued = it + 1;
             }
-            if (*(volatile int *)&abort_flag) break;
-            const uint32_t st0 = ring + s * kStageBytes;
-            const uint32_t fb = smem_u32(&full_bar[s]);
-            const int x = it * kBlockK;
-            mbar_expect_tx(fb, kStageBytes);
-            tma_load_3d(st0, &xmap, fb, x, a_row, 0);
-            tma_load_3d(st0 + kTileBytes, &xmap, fb, x, a_row, 1);
-            tma_load_3d(st0 + 2 * kTileBytes, &xmap, fb, x, b_row, bhi);
-            tma_load_3d(st0 + 3 * kTileBytes, &xmap, fb, x, b_row, blo);
-            issued = it + 1;
-        }
-        // drain: every issued load must land before the CTA can exit
-        for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it) {
-            if (!mbar_wait(smem_u32(&full_bar[it % kStages]), (it / kStages) & 1)) {
-                atomicExch(err, kErrDrain);
-                break;
-            }
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        int prev_chunk = -1;
-        for (int it = 0; it < nkb; ++it) {
-            const int s = it % kStages;
-            if (!mbar_wait(smem_u32(&full_bar[s]), (it / kStages) & 1)) {
-                atomicExch(err, kErrFull);
-                atomicExch(&abort_flag, 1);
-                break;
-            }
-            if (*(volatile int *)&abort_flag) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st0 = ring + s * kStageBytes;
-            const uint64_t ahi = smem_desc(st0), alo = smem_desc(st0 + kTileBytes);
-            const uint64_t bhd = smem_desc(st0 + 2 * kTileBytes), bld = smem_desc(st0 + 3 * kTileBytes);
-            const int chunk = it * nchunks / nkb;
-            const bool fresh_hh = chunk != prev_chunk;
-            prev_chunk = chunk;
-            const uint32_t acc_hh = tmem + (uint32_t)(chunk * kTileN);
-            const uint32_t acc_x = tmem + (uint32_t)(3 * kTileN);
-#pragma unroll
-            for (int k = 0; k < kBlockK / 16; ++k) {
-                // advance 16 BF16 = 32 bytes along K inside the swizzled row
-                const uint64_t o = (uint64_t)(2 * k);
-                mma_bf16(acc_hh, ahi + o, bhd + o, (fresh_hh && k == 0) ? 0u : 1u);
-                mma_bf16(acc_x, ahi + o, bld + o, (it == 0 && k == 0) ? 0u : 1u);
-                mma_bf16(acc_x, alo + o, bhd + o, 1u);
-            }
-            mma_commit(smem_u32(&empty_bar[s]));
-        }
-        mma_commit(smem_u32(&accum_bar));
-    }
-    __syncwarp();
-
-    // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.
-    bool ok = mbar_wait(smem_u32(&accum_bar), 0);
-    if (!ok && lane == 0) atomicExch(err, kErrAccum);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);   // warp-uniform
-    if (ok) {
-        const int r = 32 * warp + lane;            // tile row
-        const int g = (a_row + r) >> 1;            // complex row
-        const bool even = (r & 1) == 0;
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-        for (int c0 = 0; c0 < kTileN; c0 += 32) {
-            float mine[32];
-            {
-                uint32_t v[32];
-                tmem_ld32(lane_base + (uint32_t)(3 * kTileN + c0), v);   // cross terms
-#pragma unroll
-                for (int i = 0; i < 32; ++i) mine[i] = __uint_as_float(v[i]);
-                for (int a = 0; a < nchunks; ++a) {
-                    tmem_ld32(lane_base + (uint32_t)(a * kTileN + c0), v);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) mine[i] += __uint_as_float(v[i]);
+            // drain: every issued load must land before the CTA can exit
+            for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it) {
+                if (!mbar_wait(smem_u32(&full_bar[it % kStages]), (it / kStages) & 1)) {
+                    atomicExch(err, kErrDrain);
+                    break;
                 }
             }
-            float other[32];
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer
+            const uint32_t acc_x = tmem + (uint32_t)(kSlots * kTileN);
+            for (int it = 0; it < nkb; ++it) {
+                const int sub = it / kSub, slot = sub % kSlots;
+                const bool first_in_sub = (it % kSub) == 0;
+                if (first_in_sub && !mbar_wait(smem_u32(&slot_free[slot]), ((sub / kSlots) & 1) ^ 1)) {
+                    atomicExch(err, kErrAccum);
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                const int s = it % kStages;
+                if (!mbar_wait(smem_u32(&full_bar[s]), (it / kStages) & 1)) {
+                    atomicExch(err, kErrFull);
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                if (*(volatile int *)&abort_flag) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st0 = ring + s * kStageBytes;
+                const uint64_t ahi = smem_desc(st0), alo = smem_desc(st0 + kTileBytes);
+                const uint64_t bhd = smem_desc(st0 + 2 * kTileBytes), bld = smem_desc(st0 + 3 * kTileBytes);
+                const uint32_t acc_hh = tmem + (uint32_t)(slot * kTileN);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) other[i] = __shfl_xor_sync(0xffffffffu, mine[i], 1);
-            // rows 2g (re-row) and 2g+1 (im-row) now sit in both lanes of the pair;
-            // the even lane writes column pairs 0..7 of this chunk, the odd lane 8..15.
-            if (g < ng) {
+                for (int k = 0; k < kBlockK / 16; ++k) {
+                    // advance 16 BF16 = 32 bytes along K inside the swizzled row
+                    const uint64_t o = (uint64_t)(2 * k);
+                    mma_bf16(acc_hh, ahi + o, bhd + o, (first_in_sub && k == 0) ? 0u : 1u);
+                    mma_bf16(acc_x, ahi + o, bld + o, (it == 0 && k == 0) ? 0u : 1u);
+                    mma_bf16(acc_x, alo + o, bhd + o, 1u);
+                }
+                mma_commit(smem_u32(&empty_bar[s]));
+                if ((it % kSub) == kSub - 1 || it == nkb - 1) mma_commit(smem_u32(&slot_full[slot]));
+            }
+            mma_commit(smem_u32(&accum_bar));
+        }
+        __syncwarp();
+    } else {
+        // warps 0-3: promote each finished hi.hi slot into FP32 registers
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+        float racc[kTileN];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int cc = 2 * q;
-                    const float d00 = even ? mine[cc] : other[cc];           // D[2g][2g']
-                    const float d01 = even ? mine[cc + 1] : other[cc + 1];   // D[2g][2g'+1]
-                    const float d10 = even ? other[cc] : mine[cc];           // D[2g+1][2g']
-                    const float d11 = even ? other[cc + 1] : mine[cc + 1];   // D[2g+1][2g'+1]
-                    const int gp = (b_row + c0 + cc) >> 1;
-                    if ((q < 8) == even && gp < ng) {
-                        double2 *o = acc + ((long)j * ng + g) * ng + gp;
-                        double2 t = *o;
-                        t.x += (double)d00 + (double)d11;
-                        t.y += (double)d01 - (double)d10;
-                        *o = t;
+        for (int i = 0; i < kTileN; ++i) racc[i] = 0.f;
+        bool ok = true;
+        for (int sub = 0; sub < nsub; ++sub) {
+            const int slot = sub % kSlots;
+            bool got = mbar_wait(smem_u32(&slot_full[slot]), (sub / kSlots) & 1);
+            got = __all_sync(0xffffffffu, got && !*(volatile int *)&abort_flag);
+            if (!got) {
+                if (lane == 0) atomicExch(err, kErrAccum);
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int c0 = 0; c0 < kTileN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(lane_base + (uint32_t)(slot * kTileN + c0), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) racc[c0 + i] += __uint_as_float(v[i]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&slot_free[slot]));
+        }
+        if (ok) {
+            ok = mbar_wait(smem_u32(&accum_bar), 0);
+            if (!ok && lane == 0) atomicExch(err, kErrAccum);
+            ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);   // warp-uniform
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
+            const int r = 32 * warp + lane;            // tile row
+            const int g = (a_row + r) >> 1;            // complex row
+            const bool even = (r & 1) == 0;
+#pragma unroll
+            for (int c0 = 0; c0 < kTileN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(lane_base + (uint32_t)(kSlots * kTileN + c0), v);   // cross terms
+#pragma unroll
+                for (int i = 0; i < 32; ++i) racc[c0 + i] += __uint_as_float(v[i]);
+                float other[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) other[i] = __shfl_xor_sync(0xffffffffu, racc[c0 + i], 1);
+                // rows 2g (re-row) and 2g+1 (im-row) now sit in both lanes of the pair;
+                // the even lane writes column pairs 0..7 of this chunk, the odd lane 8..15.
+                if (g < ng) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int cc = 2 * q;
+                        const float d00 = even ? racc[c0 + cc] : other[cc];           // D[2g][2g']
+                        const float d01 = even ? racc[c0 + cc + 1] : other[cc + 1];   // D[2g][2g'+1]
+                        const float d10 = even ? other[cc] : racc[c0 + cc];           // D[2g+1][2g']
+                        const float d11 = even ? other[cc + 1] : racc[c0 + cc + 1];   // D[2g+1][2g'+1]
+                        const int gp = (b_row + c0 + cc) >> 1;
+                        if ((q < 8) == even && gp < ng) {
+                            double2 *o = acc + ((long)j * ng + g) * ng + gp;
+                            double2 t = *o;
+                            t.x += (double)d00 + (double)d11;
+                            t.y += (double)d01 - (double)d10;
+                            *o = t;
+                        }
                     }
                 }
             }
@@ -356,7 +402,7 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 2) {
+    if (warp == 4) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAccCols)
                      : "memory");
     }
@@ -425,7 +471,7 @@ cudaError_t mixed_gemm(int P, int ng, int nfreq, void *ws, void *acc, cudaStream
     if (e != cudaSuccess) return e;
     const int nt = (int)(R / kTileM);
     dim3 ggrid((unsigned)(nt * (nt + 1) / 2), (unsigned)nfreq);
-    k5_gemm<<<ggrid, kGemmThreads, smem, st>>>(map, (int)Kp, ng, static_cast<double2 *>(acc), err);
+    k5_gemm<<<ggrid, kGemmWarps * 32, smem, st>>>(map, (int)Kp, ng, static_cast<double2 *>(acc), err);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,17 @@ static cudaError_t upload_tables() {
     return cudaMemcpyToSymbol(c_tw32, t32, sizeof(float2) * kTwTotal);
 }
 
+// Cube origins.  A pruned input that starts at box index s (entries j = 0..w-1
+// at positions (s + j) mod N) is placed by reading slot (f - s) mod N into
+// register f; a pruned output that starts at s is written by sending register
+// f to slot (f - s) mod N.  Register indices stay compile-time; only the
+// memory index is rotated.  ns = N - s, in [1, N].
+template <int N>
+__device__ __forceinline__ int rot(int f, int ns) {
+    const int j = f + ns;
+    return j >= N ? j - N : j;
+}
+
 // ------------------------------------------------------ sphere -> grid --
 // Pass x: one thread per (band component b, y', z') line of the cube.
 template <int N>
@@ -71,23 +82,25 @@ k1_xpass(const double2 *__restrict__ coeff, int ngw, long B, const int *__restri
     if (t >= B * yzs) return;
     const long yz = t % yzs;
     const long b = t / yzs;
+    const int ns = N - s0;
     C a[N];
 #pragma unroll
-    for (int x = 0; x < N; ++x) {
+    for (int f = 0; f < N; ++f) {
+        const int j = rot<N>(f, ns);
         C v = {T(0), T(0)};
-        if (x < w0) {
-            const int idx = __ldg(cube_map + x * yzs + yz);
+        if (j < w0) {
+            const int idx = __ldg(cube_map + j * yzs + yz);
             if (idx >= 0) {
                 const double2 c = __ldg(coeff + b * ngw + idx);
                 v = {(T)c.x, (T)c.y};
             }
         }
-        a[x] = v;
+        a[f] = v;
     }
     fft_line<T, +1, N>(a);
     C *out = S + b * N * yzs + yz;
 #pragma unroll
-    for (int x = 0; x < N; ++x) out[x * yzs] = cmul(a[x], root_inv<T, N>((s0 * x) % N));
+    for (int x = 0; x < N; ++x) out[x * yzs] = a[x];
 }
 
 // Pass y: one thread per (b, x, z') line; input rows y' < w1 of S.
@@ -98,12 +111,16 @@ k1_ypass(const C *__restrict__ S, long nbx, int w1, int w2, int s1, C *__restric
     if (t >= nbx * w2) return;
     const long z = t % w2;
     const long bx = t / w2;
+    const int ns = N - s1;
     C a[N];
 #pragma unroll
-    for (int y = 0; y < N; ++y) a[y] = (y < w1) ? S[(bx * w1 + y) * w2 + z] : C{T(0), T(0)};
+    for (int f = 0; f < N; ++f) {
+        const int j = rot<N>(f, ns);
+        a[f] = (j < w1) ? S[(bx * w1 + j) * w2 + z] : C{T(0), T(0)};
+    }
     fft_line<T, +1, N>(a);
 #pragma unroll
-    for (int y = 0; y < N; ++y) R[(bx * N + y) * w2 + z] = cmul(a[y], root_inv<T, N>((s1 * y) % N));
+    for (int y = 0; y < N; ++y) R[(bx * N + y) * w2 + z] = a[y];
 }
 
 // Pass z: one thread per (b, x, y) line; writes full grid lines.
@@ -112,12 +129,16 @@ __global__ void __launch_bounds__(kLineThreads)
 k1_zpass(const C *__restrict__ R, long nbxy, int w2, int s2, C *__restrict__ U) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nbxy) return;
+    const int ns = N - s2;
     C a[N];
 #pragma unroll
-    for (int z = 0; z < N; ++z) a[z] = (z < w2) ? R[t * w2 + z] : C{T(0), T(0)};
+    for (int f = 0; f < N; ++f) {
+        const int j = rot<N>(f, ns);
+        a[f] = (j < w2) ? R[t * w2 + j] : C{T(0), T(0)};
+    }
     fft_line<T, +1, N>(a);
 #pragma unroll
-    for (int z = 0; z < N; ++z) U[t * N + z] = cmul(a[z], root_inv<T, N>((s2 * z) % N));
+    for (int z = 0; z < N; ++z) U[t * N + z] = a[z];
 }
 
 // ------------------------------------------------ pair density -> M --
@@ -137,15 +158,15 @@ k2_zpass(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, lon
     const C *c0 = Uc + (2 * c) * vol + xy * N;
     C a[N];
 #pragma unroll
-    for (int z = 0; z < N; ++z) {
-        const C r0 = cconjmul(v0[z], c0[z]);
-        const C r1 = cconjmul(v0[vol + z], c0[vol + z]);
-        a[z] = cmul(cadd(r0, r1), root_fwd<T, N>((s2 * z) % N));
-    }
+    for (int z = 0; z < N; ++z)
+        a[z] = cadd(cconjmul(v0[z], c0[z]), cconjmul(v0[vol + z], c0[vol + z]));
     fft_line<T, -1, N>(a);
+    const int ns = N - s2;
 #pragma unroll
-    for (int j = 0; j < N; ++j)
-        if (j < w2) A[t * w2 + j] = a[j];
+    for (int f = 0; f < N; ++f) {
+        const int j = rot<N>(f, ns);
+        if (j < w2) A[t * w2 + j] = a[f];
+    }
 }
 
 // Pass y: one thread per (p, x, j2); keep outputs s1 .. s1+w1-1.
@@ -158,11 +179,14 @@ k2_ypass(const C *__restrict__ A, long npx, int w1, int w2, int s1, C *__restric
     const long px = t / w2;
     C a[N];
 #pragma unroll
-    for (int y = 0; y < N; ++y) a[y] = cmul(A[(px * N + y) * w2 + jz], root_fwd<T, N>((s1 * y) % N));
+    for (int y = 0; y < N; ++y) a[y] = A[(px * N + y) * w2 + jz];
     fft_line<T, -1, N>(a);
+    const int ns = N - s1;
 #pragma unroll
-    for (int j = 0; j < N; ++j)
-        if (j < w1) Bs[(px * w1 + j) * w2 + jz] = a[j];
+    for (int f = 0; f < N; ++f) {
+        const int j = rot<N>(f, ns);
+        if (j < w1) Bs[(px * w1 + j) * w2 + jz] = a[f];
+    }
 }
 
 // Pass x + gather: one block per pair; the kept w0*w1*w2 cube goes to shared
@@ -175,15 +199,17 @@ k2_xpass_gather(const C *__restrict__ Bs, int w0, int w1, int w2, int s0,
     C *cube = reinterpret_cast<C *>(smem_raw);
     const long p = blockIdx.x;
     const int lines = w1 * w2;
+    const int ns = N - s0;
     for (int l = threadIdx.x; l < lines; l += blockDim.x) {
         C a[N];
 #pragma unroll
-        for (int x = 0; x < N; ++x)
-            a[x] = cmul(Bs[(p * N + x) * lines + l], root_fwd<T, N>((s0 * x) % N));
+        for (int x = 0; x < N; ++x) a[x] = Bs[(p * N + x) * lines + l];
         fft_line<T, -1, N>(a);
 #pragma unroll
-        for (int j = 0; j < N; ++j)
-            if (j < w0) cube[j * lines + l] = a[j];
+        for (int f = 0; f < N; ++f) {
+            const int j = rot<N>(f, ns);
+            if (j < w0) cube[j * lines + l] = a[f];
+        }
     }
     __syncthreads();
     for (int g = threadIdx.x; g < ng; g += blockDim.x) {
@@ -193,14 +219,16 @@ k2_xpass_gather(const C *__restrict__ Bs, int w0, int w1, int w2, int s0,
 }
 
 // ----------------------------------------- plane-fused passes (FP32) --
-// Band planes staged through shared memory with coalesced loads; every line
-// is then read from a padded shared row.  Used when the box has n1 == n2.
+// Band planes staged through shared memory with batched loads (kStageU in
+// flight per thread); every line is then read from a padded shared row.
+// Used when the box has n1 == n2.
 constexpr int kPlaneThreads = 256;
+constexpr int kStageU = 8;
 
 // Pair density + z pass + y pass for one x-plane and a tile of tv x tc pairs.
 // Shared: planes[(tv+tc)][2][N][N+1], then Z[tv*tc][N][w2].
 template <int N>
-__global__ void __launch_bounds__(kPlaneThreads)
+__global__ void __launch_bounds__(kPlaneThreads, 2)
 k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int TV, int TC,
             int w1, int w2, int s1, int s2, C *__restrict__ Bs) {
     extern __shared__ unsigned char smem_raw[];
@@ -211,60 +239,79 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
     const int n0 = gridDim.x;
     constexpr int RS = N + 1;                   // padded row
     constexpr int PS = N * RS;                  // one spin component of a plane
+    constexpr int NN = N * N;
     C *Z = planes + (long)(TV + TC) * 2 * PS;
-    const long vol = (long)n0 * N * N;
+    const long vol = (long)n0 * NN;
     // 1. stage the x-plane of every band of the tile (both spin components)
-    const int nb = tv + tc;
-    for (int i = threadIdx.x; i < nb * 2 * N * N; i += blockDim.x) {
-        const int b = i / (2 * N * N), rem = i % (2 * N * N);
-        const int a = rem / (N * N), yz = rem % (N * N);
-        const C *src = (b < tv) ? Uv + ((long)(v0 + b) * 2 + a) * vol
-                                : Uc + ((long)(c0 + b - tv) * 2 + a) * vol;
-        planes[(b * 2 + a) * PS + (yz / N) * RS + (yz % N)] = src[(long)x * N * N + yz];
+    const int total = (tv + tc) * 2 * NN;
+    for (int base = threadIdx.x; base < total; base += kPlaneThreads * kStageU) {
+        C tmp[kStageU];
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+            const int i = base + u * kPlaneThreads;
+            if (i < total) {
+                const int ba = i / NN, yz = i % NN;     // ba = band * 2 + alpha
+                const int b = ba >> 1, a = ba & 1;
+                const C *src = (b < tv) ? Uv + ((long)(v0 + b) * 2 + a) * vol
+                                        : Uc + ((long)(c0 + b - tv) * 2 + a) * vol;
+                tmp[u] = src[(long)x * NN + yz];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+            const int i = base + u * kPlaneThreads;
+            if (i < total) {
+                const int ba = i / NN, yz = i % NN;
+                planes[ba * PS + (yz / N) * RS + (yz % N)] = tmp[u];
+            }
+        }
     }
     __syncthreads();
     // 2. z lines: rho(z) = sum_alpha conj(u_v) u_c, forward FFT, keep w2 outputs
     const int npair = tv * tc;
-    for (int l = threadIdx.x; l < npair * N; l += blockDim.x) {
+    const int ns2 = N - s2, ns1 = N - s1;
+    for (int l = threadIdx.x; l < npair * N; l += kPlaneThreads) {
         const int pr = l / N, y = l % N;
         const int v = pr / tc, c = pr % tc;
         const C *pv = planes + (v * 2) * PS + y * RS;
         const C *pc = planes + ((tv + c) * 2) * PS + y * RS;
         C a[N];
 #pragma unroll
-        for (int z = 0; z < N; ++z) {
-            const C r = cadd(cconjmul(pv[z], pc[z]), cconjmul(pv[PS + z], pc[PS + z]));
-            a[z] = cmul(r, root_fwd<T, N>((s2 * z) % N));
-        }
+        for (int z = 0; z < N; ++z)
+            a[z] = cadd(cconjmul(pv[z], pc[z]), cconjmul(pv[PS + z], pc[PS + z]));
         fft_line<T, -1, N>(a);
         C *zo = Z + ((long)pr * N + y) * w2;
 #pragma unroll
-        for (int j = 0; j < N; ++j)
-            if (j < w2) zo[j] = a[j];
+        for (int f = 0; f < N; ++f) {
+            const int j = rot<N>(f, ns2);
+            if (j < w2) zo[j] = a[f];
+        }
     }
     __syncthreads();
     // 3. y lines over the kept z outputs; keep w1 outputs -> Bs[p][x][jy][jz]
-    for (int l = threadIdx.x; l < npair * w2; l += blockDim.x) {
+    for (int l = threadIdx.x; l < npair * w2; l += kPlaneThreads) {
         const int pr = l / w2, jz = l % w2;
         const int v = pr / tc, c = pr % tc;
         const C *zi = Z + (long)pr * N * w2 + jz;
         C a[N];
 #pragma unroll
-        for (int y = 0; y < N; ++y) a[y] = cmul(zi[y * w2], root_fwd<T, N>((s1 * y) % N));
+        for (int y = 0; y < N; ++y) a[y] = zi[y * w2];
         fft_line<T, -1, N>(a);
         const long p = (long)(v0 + v) * nc + (c0 + c);
         C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
 #pragma unroll
-        for (int j = 0; j < N; ++j)
-            if (j < w1) bo[j * w2] = a[j];
+        for (int f = 0; f < N; ++f) {
+            const int j = rot<N>(f, ns1);
+            if (j < w1) bo[j * w2] = a[f];
+        }
     }
 }
 
 // Sphere -> grid y and z passes for one x-plane of TB band components:
 // S[b][x][w1][w2] -> U[b][x][N][N].  Shared: in[TB][w1][w2], P[TB][N][w2+1],
-// out[TB][N][N].
+// out[TB][N][N+1].
 template <int N>
-__global__ void __launch_bounds__(kPlaneThreads)
+__global__ void __launch_bounds__(kPlaneThreads, 2)
 k1_yz_plane(const C *__restrict__ S, long B, int TB, int w1, int w2, int s1, int s2,
             C *__restrict__ U) {
     extern __shared__ unsigned char smem_raw[];
@@ -276,33 +323,50 @@ k1_yz_plane(const C *__restrict__ S, long B, int TB, int w1, int w2, int s1, int
     C *P = in + (long)TB * w1 * w2;
     C *out = P + (long)TB * N * PW;
     const int wsz = w1 * w2;
-    for (int i = threadIdx.x; i < tb * wsz; i += blockDim.x) {
-        const int b = i / wsz, r = i % wsz;
-        in[b * wsz + r] = S[((b0 + b) * n0 + x) * wsz + r];
+    const int total = tb * wsz;
+    for (int base = threadIdx.x; base < total; base += kPlaneThreads * kStageU) {
+        C tmp[kStageU];
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+            const int i = base + u * kPlaneThreads;
+            if (i < total) tmp[u] = S[((b0 + i / wsz) * n0 + x) * wsz + i % wsz];
+        }
+#pragma unroll
+        for (int u = 0; u < kStageU; ++u) {
+            const int i = base + u * kPlaneThreads;
+            if (i < total) in[i] = tmp[u];
+        }
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < tb * w2; l += blockDim.x) {
+    const int ns1 = N - s1, ns2 = N - s2;
+    for (int l = threadIdx.x; l < tb * w2; l += kPlaneThreads) {
         const int b = l / w2, z = l % w2;
         C a[N];
 #pragma unroll
-        for (int y = 0; y < N; ++y) a[y] = (y < w1) ? in[(b * w1 + y) * w2 + z] : C{T(0), T(0)};
+        for (int f = 0; f < N; ++f) {
+            const int j = rot<N>(f, ns1);
+            a[f] = (j < w1) ? in[(b * w1 + j) * w2 + z] : C{T(0), T(0)};
+        }
         fft_line<T, +1, N>(a);
 #pragma unroll
-        for (int y = 0; y < N; ++y) P[(b * N + y) * PW + z] = cmul(a[y], root_inv<T, N>((s1 * y) % N));
+        for (int y = 0; y < N; ++y) P[(b * N + y) * PW + z] = a[y];
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < tb * N; l += blockDim.x) {
+    for (int l = threadIdx.x; l < tb * N; l += kPlaneThreads) {
         const int b = l / N, y = l % N;
         C a[N];
 #pragma unroll
-        for (int z = 0; z < N; ++z) a[z] = (z < w2) ? P[(b * N + y) * PW + z] : C{T(0), T(0)};
+        for (int f = 0; f < N; ++f) {
+            const int j = rot<N>(f, ns2);
+            a[f] = (j < w2) ? P[(b * N + y) * PW + j] : C{T(0), T(0)};
+        }
         fft_line<T, +1, N>(a);
         C *o = out + ((long)b * N + y) * (N + 1);
 #pragma unroll
-        for (int z = 0; z < N; ++z) o[z] = cmul(a[z], root_inv<T, N>((s2 * z) % N));
+        for (int z = 0; z < N; ++z) o[z] = a[z];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < tb * N * N; i += blockDim.x) {
+    for (int i = threadIdx.x; i < tb * N * N; i += kPlaneThreads) {
         const int b = i / (N * N), r = i % (N * N);
         U[((b0 + b) * n0 + x) * N * N + r] = out[((long)b * N + r / N) * (N + 1) + (r % N)];
     }
@@ -327,7 +391,7 @@ static inline unsigned blocks_for(long n) { return (unsigned)((n + kLineThreads 
         default: return cudaErrorInvalidValue;                                           \
     }
 
-static constexpr size_t kPlaneSmemMax = 200 * 1024;
+static constexpr size_t kPlaneSmemMax = 110 * 1024;   // two blocks per SM
 
 static bool use_plane_kernels(const Axes &a) { return sizeof(T) == 4 && a.n[1] == a.n[2]; }
 
@@ -372,36 +436,56 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
     return cudaGetLastError();
 }
 
-// Pair tile (TV valence x TC conduction) of the plane kernel: as many pairs
-// as fit kPlaneSmemMax, preferring the tile with the least staged data per pair.
-static void plane_tile(int nv, int nc, int n, int w2, int &TV, int &TC, size_t &smem) {
-    TV = TC = 0;
-    smem = 0;
-    double best = 1e30;
+// Pair tiles (TV valence x TC conduction) of the plane kernel that fit
+// kPlaneSmemMax, best first: least staged data per pair, then most pairs.
+static size_t plane_smem(int tv, int tc, int n, int w2) {
+    return sizeof(C) * ((size_t)(tv + tc) * 2 * n * (n + 1) + (size_t)tv * tc * n * w2);
+}
+
+static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int max) {
+    if (!use_plane_kernels(a)) return 0;
+    struct Cand { double cost; int tv, tc; };
+    Cand best[64];
+    int nbest = 0;
     for (int tv = 1; tv <= nv && tv <= 16; ++tv)
         for (int tc = 1; tc <= nc && tc <= 16; ++tc) {
-            const size_t b = sizeof(C) * ((size_t)(tv + tc) * 2 * n * (n + 1) + (size_t)tv * tc * n * w2);
-            if (b > kPlaneSmemMax) continue;
-            const double cost = (double)(tv + tc) / (tv * tc) - 1e-3 * tv * tc;
-            if (cost < best) {
-                best = cost;
-                TV = tv;
-                TC = tc;
-                smem = b;
+            if (plane_smem(tv, tc, a.n[1], a.w[2]) > kPlaneSmemMax) continue;
+            const Cand c{(double)(tv + tc) / (tv * tc) - 1e-3 * tv * tc, tv, tc};
+            int pos = nbest < 64 ? nbest++ : 63;
+            if (pos == 63 && c.cost >= best[63].cost) continue;
+            best[pos] = c;
+            while (pos > 0 && best[pos].cost < best[pos - 1].cost) {
+                const Cand t = best[pos];
+                best[pos] = best[pos - 1];
+                best[pos - 1] = t;
+                --pos;
             }
         }
+    const int n = nbest < max ? nbest : max;
+    for (int i = 0; i < n; ++i) {
+        TV[i] = best[i].tv;
+        TC[i] = best[i].tc;
+    }
+    return n;
 }
 
 static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                          const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                         cudaStream_t st) {
+                         cudaStream_t st, int tv_req, int tc_req) {
     const long P = (long)nv * nc;
     if (P == 0) return cudaSuccess;
     const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
     C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
     int TV = 0, TC = 0;
-    size_t psmem = 0;
-    if (use_plane_kernels(a)) plane_tile(nv, nc, a.n[1], a.w[2], TV, TC, psmem);
+    if (use_plane_kernels(a)) {
+        if (tv_req > 0 && tc_req > 0 && plane_smem(tv_req, tc_req, a.n[1], a.w[2]) <= kPlaneSmemMax) {
+            TV = tv_req < nv ? tv_req : nv;
+            TC = tc_req < nc ? tc_req : nc;
+        } else {
+            plane_tile_list(nv, nc, a, &TV, &TC, 1);
+        }
+    }
+    const size_t psmem = TV > 0 ? plane_smem(TV, TC, a.n[1], a.w[2]) : 0;
     if (TV > 0) {
         dim3 grid((unsigned)a.n[0], (unsigned)((nv + TV - 1) / TV), (unsigned)((nc + TC - 1) / TC));
         cudaError_t e = cudaSuccess;

@@ -33,18 +33,23 @@ cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube
 // Uc: [nc][2][N^3] (T-complex); a.s = first kept frequency per axis,
 // a.w = kept widths; gmap[g] = j0*w1*w2 + j1*w2 + j2 (position in the kept
 // cube); A: [P][n0][n1][w2], Bs: [P][n0][w1][w2] scratch; M row stride ldm.
+// tv, tc: pair tile of the plane-fused FP32 kernel (0 = choose automatically).
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st);
+                      cudaStream_t st, int tv = 0, int tc = 0);
 cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st);
+                      cudaStream_t st, int tv = 0, int tc = 0);
+// Candidate pair tiles (tv, tc) of the plane-fused FP32 kernel for this shape,
+// best first by the staging heuristic; returns how many were written.
+int plane_tile_candidates(int nv, int nc, const Axes &a, int *tv, int *tc, int max);
 
 // ---- bgw_chi0_f64.cu ------------------------------------------------------
-// w[j][v*nc+c] = 2D/(D^2 + freq_j^2), D = ev[v] - ec[c] (the bracket of the
-// polarizability at w -> i w, eta -> 0).
-cudaError_t pair_weights(const double *ev, const double *ec, int nv, int nc,
-                         const double *freq, int nfreq, double *w, cudaStream_t st);
+// w[j][kl*P + v*nc + c] = 2D/(D^2 + freq_j^2), D = e[k][v] - e[k'][nv + c],
+// k = k0 + kl, k' = kmap[k], P = nv*nc (the bracket of the polarizability at
+// w -> i w, eta -> 0) for kl < kn.  energy: [nk][nb].
+cudaError_t pair_weights(const double *energy, int nb, int nv, int nc, const int *kmap, int k0,
+                         int kn, const double *freq, int nfreq, double *w, cudaStream_t st);
 
 // acc[j][g][g'] += sum_p w[j][p] conj(M[p][g]) M[p][g'] on the lower block
 // triangle (FP64 throughout).  M: complex128 [P][ng].
