@@ -130,13 +130,14 @@ struct bgw_ctx_s {
     DevBuf stage;        // host-uploaded coefficients
     DevBuf S, R;         // sphere -> grid scratch
     DevBuf A, Bs, M, W;  // mtxel scratch, M block, weights
-    DevBuf mixed_ws;     // mixed contraction workspace
+    DevBuf mixed_ws;     // contraction workspace (split operands / FP64 partial sums)
     DevBuf freq_dev;
     DevBuf out_stage;    // finalize to host
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
     DevBuf errflag;      // device int: non-zero after a bounded device wait gave up
     // tuning (bgw_set_option / bgw_autotune)
     int kchunk = 1;      // k-points per contraction launch
+    int sm_count = 0;
     int tile_v = 0, tile_c = 0;   // pair tile of the FP32 plane kernel (0 = automatic)
     // stage timing (bgw_profile)
     static constexpr int kStages = 6;
@@ -376,6 +377,8 @@ cudaError_t ensure_chunk_scratch(bgw_ctx_s *c, const std::vector<QState> &qs, in
         Mbytes = std::max(Mbytes, (long)kchunk * P * s.ng * (long)c->csize);
         if (c->prec != BGW_FP64)
             ws = std::max(ws, bgw::mixed_workspace_bytes((long)kchunk * P, s.ng, nfreq));
+        else
+            ws = std::max(ws, bgw::herk_f64_workspace_bytes((int)(kchunk * P), s.ng, nfreq, c->sm_count));
         e = ensure_mtxel_scratch(c, s, P);
         if (e != cudaSuccess) return e;
     }
@@ -489,7 +492,7 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
                 const int rec = c->stage_begin(3);
                 if (c->prec == BGW_FP64)
                     e = bgw::herk_f64(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
-                                      s.acc.p, c->st);
+                                      s.acc.p, c->mixed_ws.p, c->sm_count, c->st);
                 else
                     e = bgw::mixed_gemm(PT, s.ng, nfreq, c->mixed_ws.p, s.acc.p, c->st,
                                         static_cast<int *>(c->errflag.p));
@@ -557,6 +560,9 @@ bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const double *kcry
     c->st = static_cast<cudaStream_t>(stream);
     c->device = dev;
     c->csize = (prec == BGW_FP64) ? 16 : 8;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        c->sm_count < 1)
+        c->sm_count = 1;
     c->k.resize(nk);
     e = c->grids.ensure((size_t)nk * c->grid_elems_per_k() * c->csize, c->st);
     if (e == cudaSuccess) e = c->energy.ensure(sizeof(double) * (size_t)nk * c->nb, c->st);
@@ -898,6 +904,9 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
                 mb = std::max(mb, (size_t)kc * c->nv * s.nc * s.ng * c->csize);
                 if (c->prec != BGW_FP64)
                     ws = std::max(ws, bgw::mixed_workspace_bytes((long)kc * c->nv * s.nc, s.ng, nfreq));
+                else
+                    ws = std::max(ws, bgw::herk_f64_workspace_bytes(kc * c->nv * s.nc, s.ng, nfreq,
+                                                                    c->sm_count));
             }
             if (ws + mb > ((size_t)2 << 30)) break;
             float ms = 0;

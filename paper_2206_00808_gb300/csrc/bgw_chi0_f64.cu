@@ -4,9 +4,11 @@
 //
 // chi0_j[g][g'] = (1/N_k) sum_p w_pj conj(M_p[g]) M_p[g'], w_pj = 2D_p/(D_p^2 + omega_j^2).
 // GB300 issues FP64 at a small fraction of its FP32 rate, so these kernels
-// are bound by the FP64 pipe: the tiling only has to keep it busy (a few
-// warps per SM with 16 independent complex accumulators each) and every
-// operand comes from shared memory or L2.
+// are bound by the FP64 pipe: what matters is the FP64 operation count per
+// useful multiply-add and keeping every SM busy to the end (the pair range
+// is split so the blocks fill several waves; the partial sums are reduced in
+// a fixed order, so results are reproducible).
+#include <algorithm>
 #include <cmath>
 
 #include "bgw_internal.h"
@@ -37,7 +39,8 @@ __global__ void k3_pair_weights(const double *__restrict__ energy, int nb, int n
 
 constexpr int kTB = 32;   // chi0 tile edge (complex entries)
 constexpr int kPK = 16;   // pairs staged per step
-constexpr int kHerkThreads = 64;
+constexpr int kHerkThreads = 256;   // 16 x 16 threads, 2 x 2 outputs each
+constexpr int kMaxW = 5;  // frequencies per block (more spill at two blocks per SM)
 
 // Tile index t -> (bi, bj) with bi >= bj, row-major over the lower triangle.
 __device__ __forceinline__ void lower_tile(int t, int &bi, int &bj) {
@@ -48,80 +51,114 @@ __device__ __forceinline__ void lower_tile(int t, int &bi, int &bj) {
     bj = t - i * (i + 1) / 2;
 }
 
-// acc[j][g][g'] += sum_p w[j][p] conj(M[p][g]) M[p][g'] for one 32x32 tile of
-// the lower block triangle and one frequency j.  Each (tile, j) belongs to
-// exactly one block, so the read-modify-write of acc needs no atomics and the
-// order of the sum over p is fixed.
-__global__ void __launch_bounds__(kHerkThreads)
-k4_herk_f64(const double2 *__restrict__ M, int P, int ng, const double *__restrict__ w,
-            double2 *__restrict__ acc) {
+// Partial sums part[s][j][g][g'] = sum_{p in range s} w[j][p] conj(M[p][g]) M[p][g']
+// for one 32x32 tile of the lower block triangle, pair range s and
+// frequencies j0..j0+NW-1.  The product conj(M_g) M_g' is formed once per
+// pair and weighted for every frequency (4 + 2 NW FP64 operations per entry
+// and pair instead of 4 NW).
+template <int NW>
+__global__ void __launch_bounds__(kHerkThreads, 2)
+k4_herk_f64(const double2 *__restrict__ M, int P, int ng, const double *__restrict__ w, int nfreq,
+            int prange, double2 *__restrict__ part) {
     __shared__ double2 sa[kPK][kTB];
     __shared__ double2 sb[kPK][kTB];
-    __shared__ double sw[kPK];
+    __shared__ double sw[NW][kPK];
     int bi, bj;
     lower_tile(blockIdx.x, bi, bj);
-    const int j = blockIdx.y;
-    const double *wj = w + (long)j * P;
-    const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;
+    const int s = blockIdx.y;
+    const int j0 = blockIdx.z * NW;
+    const int nw = min(NW, nfreq - j0);
+    const int p_begin = s * prange, p_end = min(P, p_begin + prange);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int g0 = bi * kTB, h0 = bj * kTB;
 
-    double re[4][4], im[4][4];
+    double re[NW][2][2], im[NW][2][2];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int j = 0; j < NW; ++j)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) re[r][c] = im[r][c] = 0.0;
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) re[j][r][c] = im[j][r][c] = 0.0;
 
-    for (int p0 = 0; p0 < P; p0 += kPK) {
+    for (int p0 = p_begin; p0 < p_end; p0 += kPK) {
         for (int e = threadIdx.x; e < kPK * kTB; e += kHerkThreads) {
             const int pp = e / kTB, i = e % kTB;
             const long p = p0 + pp;
             double2 va = make_double2(0.0, 0.0), vb = va;
-            if (p < P) {
+            if (p < p_end) {
                 if (g0 + i < ng) va = M[p * ng + g0 + i];
                 if (h0 + i < ng) vb = M[p * ng + h0 + i];
             }
             sa[pp][i] = va;
             sb[pp][i] = vb;
         }
-        if (threadIdx.x < kPK) sw[threadIdx.x] = (p0 + threadIdx.x < P) ? wj[p0 + threadIdx.x] : 0.0;
+        if (threadIdx.x < NW * kPK) {
+            const int j = threadIdx.x / kPK, pp = threadIdx.x % kPK;
+            sw[j][pp] = (j < nw && p0 + pp < p_end) ? w[(long)(j0 + j) * P + p0 + pp] : 0.0;
+        }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int pp = 0; pp < kPK; ++pp) {
-            const double wp = sw[pp];
-            double2 a[4], b[4];
+            const double2 a0 = sa[pp][ty * 2], a1 = sa[pp][ty * 2 + 1];
+            const double2 b0 = sb[pp][tx * 2], b1 = sb[pp][tx * 2 + 1];
+            double pr[2][2], pi[2][2];
+            // conj(a) * b
+            pr[0][0] = fma(a0.x, b0.x, a0.y * b0.y);
+            pi[0][0] = fma(a0.x, b0.y, -a0.y * b0.x);
+            pr[0][1] = fma(a0.x, b1.x, a0.y * b1.y);
+            pi[0][1] = fma(a0.x, b1.y, -a0.y * b1.x);
+            pr[1][0] = fma(a1.x, b0.x, a1.y * b0.y);
+            pi[1][0] = fma(a1.x, b0.y, -a1.y * b0.x);
+            pr[1][1] = fma(a1.x, b1.x, a1.y * b1.y);
+            pi[1][1] = fma(a1.x, b1.y, -a1.y * b1.x);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = sa[pp][ty * 4 + r];
+            for (int j = 0; j < NW; ++j) {
+                const double wj = sw[j][pp];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const double2 v = sb[pp][tx * 4 + c];
-                b[c] = make_double2(v.x * wp, v.y * wp);
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        re[j][r][c] = fma(wj, pr[r][c], re[j][r][c]);
+                        im[j][r][c] = fma(wj, pi[r][c], im[j][r][c]);
+                    }
             }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    // conj(a) * (w b)
-                    re[r][c] = fma(a[r].x, b[c].x, fma(a[r].y, b[c].y, re[r][c]));
-                    im[r][c] = fma(a[r].x, b[c].y, fma(-a[r].y, b[c].x, im[r][c]));
-                }
         }
         __syncthreads();
     }
+    const long nn = (long)ng * ng;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int g = g0 + ty * 4 + r;
-        if (g >= ng) continue;
+    for (int j = 0; j < NW; ++j) {
+        if (j >= nw) break;
+        double2 *pj = part + ((long)s * nfreq + j0 + j) * nn;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int h = h0 + tx * 4 + c;
-            if (h >= ng) continue;
-            double2 *o = acc + ((long)j * ng + g) * ng + h;
-            double2 v = *o;
-            v.x += re[r][c];
-            v.y += im[r][c];
-            *o = v;
+        for (int r = 0; r < 2; ++r) {
+            const int g = g0 + ty * 2 + r;
+            if (g >= ng) continue;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int h = h0 + tx * 2 + c;
+                if (h < ng) pj[(long)g * ng + h] = make_double2(re[j][r][c], im[j][r][c]);
+            }
         }
     }
+}
+
+// acc[j][g][g'] += sum_{s < S} part[s][j][g][g'] in order of s, on the lower
+// block triangle (the entries the partial kernel wrote).
+__global__ void k4_reduce(const double2 *__restrict__ part, int S, int ng, int nfreq,
+                          double2 *__restrict__ acc) {
+    const long nn = (long)ng * ng;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nn * nfreq) return;
+    const int g = (int)((t % nn) / ng), h = (int)(t % ng);
+    if (g / kTB < h / kTB) return;
+    double2 v = acc[t];
+    for (int s = 0; s < S; ++s) {
+        const double2 q = part[(long)s * nn * nfreq + t];
+        v.x += q.x;
+        v.y += q.y;
+    }
+    acc[t] = v;
 }
 
 __global__ void k7_finalize(const double2 *__restrict__ acc, int ng, long total, double scale,
@@ -155,13 +192,43 @@ cudaError_t pair_weights(const double *energy, int nb, int nv, int nc, const int
     return cudaGetLastError();
 }
 
-cudaError_t herk_f64(const void *M, int P, int ng, const double *w, int nfreq, void *acc,
-                     cudaStream_t st) {
+int herk_f64_splits(int P, int ng, int nfreq, int sm_count) {
+    const int nb = (ng + kTB - 1) / kTB;
+    const int tiles = nb * (nb + 1) / 2;
+    const int nwc = (nfreq + kMaxW - 1) / kMaxW;
+    const int target = 4 * 2 * sm_count;   // four waves of two blocks per SM
+    int S = (target + tiles * nwc - 1) / (tiles * nwc);
+    S = std::max(1, std::min(S, (P + 63) / 64));
+    return S;
+}
+
+size_t herk_f64_workspace_bytes(int P, int ng, int nfreq, int sm_count) {
+    return sizeof(double2) * (size_t)herk_f64_splits(P, ng, nfreq, sm_count) * nfreq * ng * ng;
+}
+
+cudaError_t herk_f64(const void *M, int P, int ng, const double *w, int nfreq, void *acc, void *ws,
+                     int sm_count, cudaStream_t st) {
     if (P == 0) return cudaSuccess;
     const int nb = (ng + kTB - 1) / kTB;
-    dim3 grid(nb * (nb + 1) / 2, nfreq);
-    k4_herk_f64<<<grid, kHerkThreads, 0, st>>>(static_cast<const double2 *>(M), P, ng, w,
-                                               static_cast<double2 *>(acc));
+    const int S = herk_f64_splits(P, ng, nfreq, sm_count);
+    const int prange = (((P + S - 1) / S) + kPK - 1) / kPK * kPK;
+    // frequencies per block: all of them up to kMaxW, else chunks of kMaxW
+    const int NWr = std::min(nfreq, kMaxW);
+    dim3 grid(nb * (nb + 1) / 2, S, (nfreq + NWr - 1) / NWr);
+    const double2 *Mp = static_cast<const double2 *>(M);
+    double2 *part = static_cast<double2 *>(ws);
+    switch (NWr) {
+        case 1: k4_herk_f64<1><<<grid, kHerkThreads, 0, st>>>(Mp, P, ng, w, nfreq, prange, part); break;
+        case 2: k4_herk_f64<2><<<grid, kHerkThreads, 0, st>>>(Mp, P, ng, w, nfreq, prange, part); break;
+        case 3: k4_herk_f64<3><<<grid, kHerkThreads, 0, st>>>(Mp, P, ng, w, nfreq, prange, part); break;
+        case 4: k4_herk_f64<4><<<grid, kHerkThreads, 0, st>>>(Mp, P, ng, w, nfreq, prange, part); break;
+        default: k4_herk_f64<5><<<grid, kHerkThreads, 0, st>>>(Mp, P, ng, w, nfreq, prange, part); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long total = (long)nfreq * ng * ng;
+    k4_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, S, ng, nfreq,
+                                                               static_cast<double2 *>(acc));
     return cudaGetLastError();
 }
 

@@ -52,9 +52,11 @@ cudaError_t pair_weights(const double *energy, int nb, int nv, int nc, const int
                          int kn, const double *freq, int nfreq, double *w, cudaStream_t st);
 
 // acc[j][g][g'] += sum_p w[j][p] conj(M[p][g]) M[p][g'] on the lower block
-// triangle (FP64 throughout).  M: complex128 [P][ng].
-cudaError_t herk_f64(const void *M, int P, int ng, const double *w, int nfreq, void *acc,
-                     cudaStream_t st);
+// triangle (FP64 throughout).  M: complex128 [P][ng].  ws: workspace of
+// herk_f64_workspace_bytes for the partial sums of the split pair range.
+size_t herk_f64_workspace_bytes(int P, int ng, int nfreq, int sm_count);
+cudaError_t herk_f64(const void *M, int P, int ng, const double *w, int nfreq, void *acc, void *ws,
+                     int sm_count, cudaStream_t st);
 
 // out[j][g][g'] = scale * (g >= g' ? acc[j][g][g'] : conj(acc[j][g'][g])).
 cudaError_t chi0_finalize(const void *acc, int ng, int nfreq, double scale, void *out,
