@@ -164,6 +164,25 @@ BGW_API bgw_status bgw_chi0_accumulate(bgw_ctx ctx, int nq, const bgw_q *qs, int
 BGW_API bgw_status bgw_chi0_finalize(bgw_ctx ctx, int iq, void *chi0, int on_device);
 
 /*
+ * CUDA-graph capture of a sequence of calls on this context (for repeated
+ * identical steps, e.g. serving the same workload).  bgw_graph_begin starts
+ * capturing the context stream (which must not be the legacy default
+ * stream); the calls that follow queue their device work into the graph
+ * instead of running it; bgw_graph_end instantiates it (replacing any
+ * earlier graph); bgw_graph_launch replays it on the stream.  A replay
+ * repeats exactly the captured device work with the same buffers and
+ * arguments; host-side state is what the captured calls left.  Captured
+ * calls must be capture-safe: device-resident inputs (on_device = 1 or
+ * pinned host buffers), a device finalize, spheres and q-sets already seen
+ * (no new host-to-device metadata copies) and scratch already sized by an
+ * identical uncaptured sequence; otherwise the call or bgw_graph_end fails
+ * with BGW_E_CUDA and the context can be used uncaptured again.
+ */
+BGW_API bgw_status bgw_graph_begin(bgw_ctx ctx);
+BGW_API bgw_status bgw_graph_end(bgw_ctx ctx);
+BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
+
+/*
  * Tuning options (per context; they change speed, not the mathematics):
  *   BGW_OPT_KCHUNK       k-points contracted per launch (1..256, default 1).
  *                        The result is bitwise independent of how a k range is

@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": BGW_FP64, "mixed": BGW_MIXED_BF16X3}
 EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
             "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
             "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune",
-            "bgw_destroy", "bgw_last_error"]
+            "bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch", "bgw_destroy", "bgw_last_error"]
 BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C = 1, 2, 3
 STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split"]
 
@@ -52,6 +52,9 @@ _lib.bgw_mtxel_spinor_noalloc.argtypes = [_P, _P, _P, _I, _I, _P, _I, _P, _P, _P
 _lib.bgw_set_option.argtypes = [_P, _I, ctypes.c_long]
 _lib.bgw_get_option.argtypes = [_P, _I, ctypes.POINTER(ctypes.c_long)]
 _lib.bgw_autotune.argtypes = [_P, _I, ctypes.POINTER(bgw_q), _I, _P, _I, _I, ctypes.c_char_p]
+for _f in ["bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch"]:
+    getattr(_lib, _f).argtypes = [_P]
+    getattr(_lib, _f).restype = ctypes.c_int
 _lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
 _lib.bgw_last_error.argtypes, _lib.bgw_last_error.restype = [_P], ctypes.c_char_p
 for _f in ["bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
@@ -219,6 +222,18 @@ def bgw_autotune(ctx, qs, freq, k_begin: int, k_end: int, cache_path=None) -> di
     _check(_lib.bgw_autotune(ctx, len(structs), arr, len(f), _host_ptr(f), k_begin, k_end, cp), ctx)
     return {"kchunk": bgw_get_option(ctx, BGW_OPT_KCHUNK),
             "pair_tile": (bgw_get_option(ctx, BGW_OPT_PAIR_TILE_V), bgw_get_option(ctx, BGW_OPT_PAIR_TILE_C))}
+
+
+def bgw_graph_begin(ctx) -> int:
+    return _check(_lib.bgw_graph_begin(ctx), ctx)
+
+
+def bgw_graph_end(ctx) -> int:
+    return _check(_lib.bgw_graph_end(ctx), ctx)
+
+
+def bgw_graph_launch(ctx) -> int:
+    return _check(_lib.bgw_graph_launch(ctx), ctx)
 
 
 def bgw_destroy(ctx) -> None:

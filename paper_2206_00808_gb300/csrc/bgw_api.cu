@@ -33,6 +33,9 @@ struct DevBuf {
     // stream first so no queued kernel still reads the old allocation.
     cudaError_t ensure(size_t bytes, cudaStream_t st) {
         if (bytes <= cap) return cudaSuccess;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            return cudaErrorNotPermitted;   // no allocation inside a graph capture
         if (p) {
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return e;
@@ -135,6 +138,9 @@ struct bgw_ctx_s {
     DevBuf out_stage;    // finalize to host
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
     DevBuf errflag;      // device int: non-zero after a bounded device wait gave up
+    // graph capture (bgw_graph_*)
+    bool capturing = false;
+    cudaGraphExec_t gexec = nullptr;
     // tuning (bgw_set_option / bgw_autotune)
     int kchunk = 1;      // k-points per contraction launch
     int sm_count = 0;
@@ -159,7 +165,7 @@ struct bgw_ctx_s {
     }
     // Bracket a launch group; returns the index to close, or -1.
     int stage_begin(int stage) {
-        if (!prof) return -1;
+        if (!prof || capturing) return -1;
         Rec r{stage, 0, take_event(), take_event()};
         if (!r.a || !r.b) return -1;
         cudaEventRecord(r.a, st);
@@ -196,6 +202,9 @@ struct bgw_ctx_s {
     bgw_status fail(bgw_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
     bgw_status cuda_fail(cudaError_t e, const char *what) {
         err = std::string(what) + ": " + cudaGetErrorString(e);
+        if (e == cudaErrorNotPermitted && capturing)
+            err += " (a buffer would have to grow during graph capture: run the same calls once "
+                   "before bgw_graph_begin)";
         return e == cudaErrorMemoryAllocation ? BGW_E_NOMEM : BGW_E_CUDA;
     }
     long grid_elems_per_k() const { return (long)nb * 2 * nbox; }
@@ -940,6 +949,55 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
     return BGW_OK;
 }
 
+bgw_status bgw_graph_begin(bgw_ctx c) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (!c->st) return c->fail(BGW_E_ARG, "graph_begin: the context stream is the legacy default stream");
+    if (c->capturing) return c->fail(BGW_E_STATE, "graph_begin: already capturing");
+    cudaError_t e = c->drain();
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return c->cuda_fail(e, "graph_begin");
+    c->capturing = true;
+    return BGW_OK;
+}
+
+bgw_status bgw_graph_end(bgw_ctx c) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (!c->capturing) return c->fail(BGW_E_STATE, "graph_end: not capturing");
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    if (e != cudaSuccess || !g) {
+        cudaGetLastError();
+        return c->cuda_fail(e != cudaSuccess ? e : cudaErrorStreamCaptureInvalidated, "graph_end");
+    }
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return c->cuda_fail(e, "graph_end: instantiate");
+    }
+    return BGW_OK;
+}
+
+bgw_status bgw_graph_launch(bgw_ctx c) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (!c->gexec) return c->fail(BGW_E_STATE, "graph_launch: nothing captured");
+    if (c->capturing) return c->fail(BGW_E_STATE, "graph_launch: still capturing");
+    cudaError_t e = cudaGraphLaunch(c->gexec, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "graph_launch");
+    return BGW_OK;
+}
+
 bgw_status bgw_profile(bgw_ctx c, int enable) {
     if (!c) return BGW_E_ARG;
     DeviceGuard dg(c->device);
@@ -960,6 +1018,7 @@ bgw_status bgw_profile_read(bgw_ctx c, double *ms, long *calls, long *kernels, i
     if (!c) return BGW_E_ARG;
     DeviceGuard dg(c->device);
     c->err.clear();
+    if (c->capturing) return c->fail(BGW_E_STATE, "profile_read: not allowed during graph capture");
     if (n < 0 || n > bgw_ctx_s::kStages) return c->fail(BGW_E_ARG, "profile_read: n outside 0..6");
     cudaError_t e = c->drain();
     if (e != cudaSuccess) return c->cuda_fail(e, "profile_read: stream");
@@ -975,7 +1034,14 @@ void bgw_destroy(bgw_ctx c) {
     if (!c) return;
     {
         DeviceGuard dg(c->device);
+        if (c->capturing) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(c->st, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+        }
         cudaStreamSynchronize(c->st);
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
         for (auto &r : c->recs) {
             cudaEventDestroy(r.a);
             cudaEventDestroy(r.b);
