@@ -375,19 +375,36 @@ void compute_kmap(const bgw_ctx_s *c, QState &s) {
     }
 }
 
-// Scratch for contraction launches of up to kchunk k-points on every q.
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bytes of split operands the mixed contraction keeps for q-point s.
+size_t mixed_q_bytes(const bgw_ctx_s *c, const QState &s, int nfreq, int kchunk) {
+    return align256(bgw::mixed_workspace_bytes((long)kchunk * c->nv * s.nc, s.ng, nfreq));
+}
+
+// Scratch for contraction launches of up to kchunk k-points on every q
+// (mixed: the split operands of a whole group of q-points at once).
 cudaError_t ensure_chunk_scratch(bgw_ctx_s *c, const std::vector<QState> &qs, int nfreq, int kchunk) {
     long Pmax = 0, Mbytes = 0;
     size_t ws = 0;
     cudaError_t e = cudaSuccess;
+    const int G = bgw::mixed_max_group();
+    for (size_t g0 = 0; g0 < qs.size(); g0 += G) {
+        size_t sum = 0;
+        for (size_t i = g0; i < qs.size() && i < g0 + G; ++i) {
+            const QState &s = qs[i];
+            if (c->prec != BGW_FP64)
+                sum += mixed_q_bytes(c, s, nfreq, kchunk);
+            else
+                sum = std::max(sum, bgw::herk_f64_workspace_bytes((int)(kchunk * c->nv * s.nc), s.ng,
+                                                                  nfreq, c->sm_count));
+        }
+        ws = std::max(ws, sum);
+    }
     for (auto &s : qs) {
         const long P = (long)c->nv * s.nc;
         Pmax = std::max(Pmax, P);
         Mbytes = std::max(Mbytes, (long)kchunk * P * s.ng * (long)c->csize);
-        if (c->prec != BGW_FP64)
-            ws = std::max(ws, bgw::mixed_workspace_bytes((long)kchunk * P, s.ng, nfreq));
-        else
-            ws = std::max(ws, bgw::herk_f64_workspace_bytes((int)(kchunk * P), s.ng, nfreq, c->sm_count));
         e = ensure_mtxel_scratch(c, s, P);
         if (e != cudaSuccess) return e;
     }
@@ -462,49 +479,63 @@ bgw_status install_qset(bgw_ctx_s *c, std::vector<QState> &fresh, int nfreq, con
     return BGW_OK;
 }
 
-// The k loop of bgw_chi0_accumulate for the given q-states: per chunk of
-// kchunk k-points, matrix elements of each k into consecutive M blocks, one
-// weights launch, (mixed: one operand split,) one contraction launch.
+// The k loop of bgw_chi0_accumulate for the given q-states.  Per chunk of
+// kchunk k-points and per q: matrix elements of each k into consecutive M
+// blocks and one weights launch; then FP64: one contraction launch per q;
+// mixed: one operand split per q into its own workspace slice and ONE
+// persistent grouped contraction for a whole group of q-points.
 cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const double *freq,
                       int k_begin, int k_end, int kchunk, int tv, int tc, bool &clean) {
     cudaError_t e = cudaSuccess;
     const double *energy = static_cast<const double *>(c->energy.p);
-    for (auto &s : qs) {
-        const long P = (long)c->nv * s.nc;
-        for (int k0 = k_begin; k0 < k_end; k0 += kchunk) {
-            const int kn = std::min(kchunk, k_end - k0);
-            for (int kl = 0; kl < kn; ++kl) {
-                const int ik = k0 + kl;
-                int kp, G0[3];
-                find_umklapp(c, ik, s.q, kp, G0);
-                clean = clean && alias_free(c, ik, kp, G0, s);
-                char *Mk = static_cast<char *>(c->M.p) + (size_t)kl * P * s.ng * c->csize;
-                e = launch_mtxel(c, s, ik, kp, G0, 0, c->nv, 0, s.nc, Mk, s.ng, tv, tc);
-                if (e != cudaSuccess) return e;
-            }
-            const int PT = (int)(P * kn);
-            {
-                const int rec = c->stage_begin(2);
-                e = bgw::pair_weights(energy, c->nb, c->nv, s.nc, static_cast<const int *>(s.kmap_dev.p),
-                                      k0, kn, freq, nfreq, static_cast<double *>(c->W.p), c->st);
-                c->stage_end(rec, 1);
-                if (e != cudaSuccess) return e;
-            }
-            if (c->prec != BGW_FP64) {
-                const int rec = c->stage_begin(5);
-                e = bgw::mixed_split(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
-                                     c->mixed_ws.p, c->st);
-                c->stage_end(rec, 1);
-                if (e != cudaSuccess) return e;
-            }
-            {
-                const int rec = c->stage_begin(3);
-                if (c->prec == BGW_FP64)
+    const int G = c->prec == BGW_FP64 ? 1 : bgw::mixed_max_group();
+    std::vector<bgw::MixedQ> group;
+    for (int k0 = k_begin; k0 < k_end; k0 += kchunk) {
+        const int kn = std::min(kchunk, k_end - k0);
+        for (size_t g0 = 0; g0 < qs.size(); g0 += G) {
+            group.clear();
+            size_t off = 0;
+            for (size_t iq = g0; iq < qs.size() && iq < g0 + G; ++iq) {
+                QState &s = qs[iq];
+                const long P = (long)c->nv * s.nc;
+                for (int kl = 0; kl < kn; ++kl) {
+                    const int ik = k0 + kl;
+                    int kp, G0[3];
+                    find_umklapp(c, ik, s.q, kp, G0);
+                    clean = clean && alias_free(c, ik, kp, G0, s);
+                    char *Mk = static_cast<char *>(c->M.p) + (size_t)kl * P * s.ng * c->csize;
+                    e = launch_mtxel(c, s, ik, kp, G0, 0, c->nv, 0, s.nc, Mk, s.ng, tv, tc);
+                    if (e != cudaSuccess) return e;
+                }
+                const int PT = (int)(P * kn);
+                {
+                    const int rec = c->stage_begin(2);
+                    e = bgw::pair_weights(energy, c->nb, c->nv, s.nc, static_cast<const int *>(s.kmap_dev.p),
+                                          k0, kn, freq, nfreq, static_cast<double *>(c->W.p), c->st);
+                    c->stage_end(rec, 1);
+                    if (e != cudaSuccess) return e;
+                }
+                if (c->prec == BGW_FP64) {
+                    const int rec = c->stage_begin(3);
                     e = bgw::herk_f64(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
                                       s.acc.p, c->mixed_ws.p, c->sm_count, c->st);
-                else
-                    e = bgw::mixed_gemm(PT, s.ng, nfreq, c->mixed_ws.p, s.acc.p, c->st,
-                                        static_cast<int *>(c->errflag.p));
+                    c->stage_end(rec, 2);
+                    if (e != cudaSuccess) return e;
+                } else {
+                    void *ws = static_cast<char *>(c->mixed_ws.p) + off;
+                    off += mixed_q_bytes(c, s, nfreq, kchunk);
+                    const int rec = c->stage_begin(5);
+                    e = bgw::mixed_split(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq, ws,
+                                         c->st);
+                    c->stage_end(rec, 1);
+                    if (e != cudaSuccess) return e;
+                    group.push_back(bgw::MixedQ{ws, PT, s.ng, s.acc.p});
+                }
+            }
+            if (c->prec != BGW_FP64) {
+                const int rec = c->stage_begin(3);
+                e = bgw::mixed_gemm(group.data(), (int)group.size(), nfreq, c->sm_count, c->st,
+                                    static_cast<int *>(c->errflag.p));
                 c->stage_end(rec, 1);
                 if (e != cudaSuccess) return e;
             }
@@ -512,7 +543,6 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
     }
     return e;
 }
-
 }  // namespace
 
 extern "C" {

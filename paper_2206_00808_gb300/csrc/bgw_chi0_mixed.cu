@@ -32,6 +32,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "bgw_mixed.h"
@@ -46,6 +47,7 @@ constexpr int kStages = 3;
 constexpr int kTileBytes = kTileM * kBlockK * 2;                 // 16 KB per operand tile
 constexpr int kStageBytes = 4 * kTileBytes;                      // A_hi, A_lo, B_hi, B_lo
 constexpr int kAccCols = 4 * kTileN;                             // 3 hi.hi + 1 cross accumulator
+constexpr int kMaxGroup = 48;                                    // q-points per grouped launch
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
 
@@ -194,39 +196,65 @@ __device__ __forceinline__ void lower_tile(int t, int &bi, int &bj) {
 }
 
 // --------------------------------------------------------------- GEMM --
+// Persistent grouped kernel: the work items of every q-point of a group
+// (lower 128x128 tiles x frequencies, tile-major so the CTAs of one wave
+// share A tiles in L2) are dealt round-robin to one CTA per SM.
 // Warp roles: warps 0-3 drain tensor memory (warp w owns TMEM lanes
 // 32w..32w+31 = tile rows), warp 4 allocates TMEM and issues the TMA loads,
 // warp 5 issues the MMAs.  The hi.hi products of each run of kSub K blocks go
 // to one of three TMEM slots in turn; when a run completes, warps 0-3 add
 // that slot into FP32 registers (round to nearest) and hand it back, so no
 // TMEM accumulator takes more than 4*kSub truncating adds of the large
-// products whatever K is.  The two cross products go to a fourth slot.
+// products whatever K is.  The two cross products go to a fourth slot, read
+// once per item; the next item's MMAs start once it has been read.  Barrier
+// phases run on across items.
 constexpr int kSub = 8;
 constexpr int kSlots = 3;
 constexpr int kGemmWarps = 6;
+
+struct GroupParams {
+    CUtensorMap map[kMaxGroup];   // operand planes of each q-point
+    double2 *acc[kMaxGroup];      // FP64 accumulator [nfreq][ng][ng]
+    int kp[kMaxGroup];            // padded pair count (multiple of kBlockK)
+    int ng[kMaxGroup];
+    int first[kMaxGroup + 1];     // first work item of each q-point
+    int nq, nfreq;
+};
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+struct Item {
+    int q, ti, tj, j, nkb;
+};
+
+__device__ __forceinline__ Item decode(const GroupParams &gp, int item) {
+    Item it;
+    int q = 0;
+    while (q + 1 < gp.nq && gp.first[q + 1] <= item) ++q;
+    const int local = item - gp.first[q];
+    lower_tile(local / gp.nfreq, it.ti, it.tj);
+    it.q = q;
+    it.j = local % gp.nfreq;
+    it.nkb = gp.kp[q] / kBlockK;
+    return it;
+}
+
 __global__ void __launch_bounds__(kGemmWarps * 32, 1)
-k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__restrict__ acc,
-        int *__restrict__ err) {
+k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages];
     __shared__ __align__(8) uint64_t empty_bar[kStages];
     __shared__ __align__(8) uint64_t slot_full[kSlots];
     __shared__ __align__(8) uint64_t slot_free[kSlots];
     __shared__ __align__(8) uint64_t accum_bar;
+    __shared__ __align__(8) uint64_t tmem_free;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    int ti, tj;
-    lower_tile(blockIdx.x, ti, tj);
-    const int j = blockIdx.y;
-    const int nkb = Kp / kBlockK;
-    const int nsub = (nkb + kSub - 1) / kSub;
+    const int total = gp.first[gp.nq];
 
     // 1024-byte aligned stage ring
     const uint32_t raw = smem_u32(smem_raw);
@@ -242,9 +270,9 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
             mbar_init(smem_u32(&slot_free[s]), 128);
         }
         mbar_init(smem_u32(&accum_bar), 1);
+        mbar_init(smem_u32(&tmem_free), 128);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
     }
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -258,35 +286,39 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
-    // planes: 0 A_hi, 1 A_lo, 2 + 2j B_j hi, 3 + 2j B_j lo
-    const int a_row = ti * kTileM, b_row = tj * kTileN;
-    const int bhi = 2 + 2 * j, blo = 3 + 2 * j;
-
     if (warp == 4) {
         if (lane == 0) {
-            // TMA producer
-            int issued = 0;
-            for (int it = 0; it < nkb; ++it) {
-                const int s = it % kStages;
-                if (!mbar_wait(smem_u32(&empty_bar[s]), ((it / kStages) & 1) ^ 1)) {
-                    atomicExch(err, kErrEmpty);
-                    atomicExch(&abort_flag, 1);
-                    break;
+            // TMA producer; planes: 0 A_hi, 1 A_lo, 2 + 2j B_j hi, 3 + 2j B_j lo
+            long pit = 0, issued_from = 0;
+            for (int item = blockIdx.x; item < total; item += gridDim.x) {
+                const Item w = decode(gp, item);
+                const CUtensorMap *map = &gp.map[w.q];
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+                const int a_row = w.ti * kTileM, b_row = w.tj * kTileN;
+                const int bhi = 2 + 2 * w.j, blo = 3 + 2 * w.j;
+                for (int it = 0; it < w.nkb; ++it, ++pit) {
+                    const int s = (int)(pit % kStages);
+                    if (!mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((pit / kStages) & 1) ^ 1))) {
+                        atomicExch(err, kErrEmpty);
+                        atomicExch(&abort_flag, 1);
+                        break;
+                    }
+                    if (*(volatile int *)&abort_flag) break;
+                    const uint32_t st0 = ring + s * kStageBytes;
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    const int x = it * kBlockK;
+                    mbar_expect_tx(fb, kStageBytes);
+                    tma_load_3d(st0, map, fb, x, a_row, 0);
+                    tma_load_3d(st0 + kTileBytes, map, fb, x, a_row, 1);
+                    tma_load_3d(st0 + 2 * kTileBytes, map, fb, x, b_row, bhi);
+                    tma_load_3d(st0 + 3 * kTileBytes, map, fb, x, b_row, blo);
                 }
                 if (*(volatile int *)&abort_flag) break;
-                const uint32_t st0 = ring + s * kStageBytes;
-                const uint32_t fb = smem_u32(&full_bar[s]);
-                const int x = it * kBlockK;
-                mbar_expect_tx(fb, kStageBytes);
-                tma_load_3d(st0, &xmap, fb, x, a_row, 0);
-                tma_load_3d(st0 + kTileBytes, &xmap, fb, x, a_row, 1);
-                tma_load_3d(st0 + 2 * kTileBytes, &xmap, fb, x, b_row, bhi);
-                tma_load_3d(st0 + 3 * kTileBytes, &xmap, fb, x, b_row, blo);
-                issued = it + 1;
             }
-            // drain: every issued load must land before the CTA can exit
-            for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it) {
-                if (!mbar_wait(smem_u32(&full_bar[it % kStages]), (it / kStages) & 1)) {
+            // every issued load must land before the CTA can exit
+            issued_from = pit > kStages ? pit - kStages : 0;
+            for (long q = issued_from; q < pit; ++q) {
+                if (!mbar_wait(smem_u32(&full_bar[q % kStages]), (uint32_t)((q / kStages) & 1))) {
                     atomicExch(err, kErrDrain);
                     break;
                 }
@@ -297,83 +329,123 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
         if (lane == 0) {
             // MMA issuer
             const uint32_t acc_x = tmem + (uint32_t)(kSlots * kTileN);
-            for (int it = 0; it < nkb; ++it) {
-                const int sub = it / kSub, slot = sub % kSlots;
-                const bool first_in_sub = (it % kSub) == 0;
-                if (first_in_sub && !mbar_wait(smem_u32(&slot_free[slot]), ((sub / kSlots) & 1) ^ 1)) {
+            long pit = 0, gsub = 0;
+            int nitem = 0;
+            bool stop = false;
+            for (int item = blockIdx.x; item < total && !stop; item += gridDim.x, ++nitem) {
+                const Item w = decode(gp, item);
+                if (nitem > 0 && !mbar_wait(smem_u32(&tmem_free), (uint32_t)((nitem - 1) & 1))) {
                     atomicExch(err, kErrAccum);
                     atomicExch(&abort_flag, 1);
                     break;
                 }
-                const int s = it % kStages;
-                if (!mbar_wait(smem_u32(&full_bar[s]), (it / kStages) & 1)) {
-                    atomicExch(err, kErrFull);
-                    atomicExch(&abort_flag, 1);
-                    break;
-                }
-                if (*(volatile int *)&abort_flag) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t st0 = ring + s * kStageBytes;
-                const uint64_t ahi = smem_desc(st0), alo = smem_desc(st0 + kTileBytes);
-                const uint64_t bhd = smem_desc(st0 + 2 * kTileBytes), bld = smem_desc(st0 + 3 * kTileBytes);
-                const uint32_t acc_hh = tmem + (uint32_t)(slot * kTileN);
+                int slot = 0;
+                for (int it = 0; it < w.nkb; ++it, ++pit) {
+                    const bool first_in_sub = (it % kSub) == 0;
+                    if (first_in_sub) {
+                        slot = (int)(gsub % kSlots);
+                        if (!mbar_wait(smem_u32(&slot_free[slot]), (uint32_t)(((gsub / kSlots) & 1) ^ 1))) {
+                            atomicExch(err, kErrAccum);
+                            atomicExch(&abort_flag, 1);
+                            stop = true;
+                            break;
+                        }
+                    }
+                    const int s = (int)(pit % kStages);
+                    if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((pit / kStages) & 1))) {
+                        atomicExch(err, kErrFull);
+                        atomicExch(&abort_flag, 1);
+                        stop = true;
+                        break;
+                    }
+                    if (*(volatile int *)&abort_flag) {
+                        stop = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t st0 = ring + s * kStageBytes;
+                    const uint64_t ahi = smem_desc(st0), alo = smem_desc(st0 + kTileBytes);
+                    const uint64_t bhd = smem_desc(st0 + 2 * kTileBytes), bld = smem_desc(st0 + 3 * kTileBytes);
+                    const uint32_t acc_hh = tmem + (uint32_t)(slot * kTileN);
 #pragma unroll
-                for (int k = 0; k < kBlockK / 16; ++k) {
-                    // advance 16 BF16 = 32 bytes along K inside the swizzled row
-                    const uint64_t o = (uint64_t)(2 * k);
-                    mma_bf16(acc_hh, ahi + o, bhd + o, (first_in_sub && k == 0) ? 0u : 1u);
-                    mma_bf16(acc_x, ahi + o, bld + o, (it == 0 && k == 0) ? 0u : 1u);
-                    mma_bf16(acc_x, alo + o, bhd + o, 1u);
+                    for (int k = 0; k < kBlockK / 16; ++k) {
+                        // advance 16 BF16 = 32 bytes along K inside the swizzled row
+                        const uint64_t o = (uint64_t)(2 * k);
+                        mma_bf16(acc_hh, ahi + o, bhd + o, (first_in_sub && k == 0) ? 0u : 1u);
+                        mma_bf16(acc_x, ahi + o, bld + o, (it == 0 && k == 0) ? 0u : 1u);
+                        mma_bf16(acc_x, alo + o, bhd + o, 1u);
+                    }
+                    mma_commit(smem_u32(&empty_bar[s]));
+                    if ((it % kSub) == kSub - 1 || it == w.nkb - 1) {
+                        mma_commit(smem_u32(&slot_full[slot]));
+                        ++gsub;
+                    }
                 }
-                mma_commit(smem_u32(&empty_bar[s]));
-                if ((it % kSub) == kSub - 1 || it == nkb - 1) mma_commit(smem_u32(&slot_full[slot]));
+                mma_commit(smem_u32(&accum_bar));
             }
-            mma_commit(smem_u32(&accum_bar));
         }
         __syncwarp();
     } else {
-        // warps 0-3: promote each finished hi.hi slot into FP32 registers
+        // warps 0-3: promote finished hi.hi slots into FP32 registers, then
+        // fold the tile into complex chi and add it in FP64
         const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-        float racc[kTileN];
+        long gsub = 0;
+        int nitem = 0;
+        for (int item = blockIdx.x; item < total; item += gridDim.x, ++nitem) {
+            const Item w = decode(gp, item);
+            const int nsub = (w.nkb + kSub - 1) / kSub;
+            float racc[kTileN];
 #pragma unroll
-        for (int i = 0; i < kTileN; ++i) racc[i] = 0.f;
-        bool ok = true;
-        for (int sub = 0; sub < nsub; ++sub) {
-            const int slot = sub % kSlots;
-            bool got = mbar_wait(smem_u32(&slot_full[slot]), (sub / kSlots) & 1);
-            got = __all_sync(0xffffffffu, got && !*(volatile int *)&abort_flag);
-            if (!got) {
-                if (lane == 0) atomicExch(err, kErrAccum);
-                ok = false;
+            for (int i = 0; i < kTileN; ++i) racc[i] = 0.f;
+            bool ok = true;
+            for (int sub = 0; sub < nsub; ++sub, ++gsub) {
+                const int slot = (int)(gsub % kSlots);
+                bool got = mbar_wait(smem_u32(&slot_full[slot]), (uint32_t)((gsub / kSlots) & 1));
+                got = __all_sync(0xffffffffu, got && !*(volatile int *)&abort_flag);
+                if (!got) {
+                    if (lane == 0) atomicExch(err, kErrAccum);
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int c0 = 0; c0 < kTileN; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(lane_base + (uint32_t)(slot * kTileN + c0), v);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) racc[c0 + i] += __uint_as_float(v[i]);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(smem_u32(&slot_free[slot]));
+            }
+            if (ok) {
+                ok = mbar_wait(smem_u32(&accum_bar), (uint32_t)(nitem & 1));
+                if (!ok && lane == 0) atomicExch(err, kErrAccum);
+                ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);   // warp-uniform
+            }
+            if (!ok) {
+                atomicExch(&abort_flag, 1);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int c0 = 0; c0 < kTileN; c0 += 32) {
                 uint32_t v[32];
-                tmem_ld32(lane_base + (uint32_t)(slot * kTileN + c0), v);
+                tmem_ld32(lane_base + (uint32_t)(kSlots * kTileN + c0), v);   // cross terms
 #pragma unroll
                 for (int i = 0; i < 32; ++i) racc[c0 + i] += __uint_as_float(v[i]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(smem_u32(&slot_free[slot]));
-        }
-        if (ok) {
-            ok = mbar_wait(smem_u32(&accum_bar), 0);
-            if (!ok && lane == 0) atomicExch(err, kErrAccum);
-            ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);   // warp-uniform
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
+            mbar_arrive(smem_u32(&tmem_free));   // the MMAs of the next item may start
+            const int ng = gp.ng[w.q];
+            double2 *acc = gp.acc[w.q];
+            const int a_row = w.ti * kTileM, b_row = w.tj * kTileN;
             const int r = 32 * warp + lane;            // tile row
             const int g = (a_row + r) >> 1;            // complex row
             const bool even = (r & 1) == 0;
 #pragma unroll
             for (int c0 = 0; c0 < kTileN; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(lane_base + (uint32_t)(kSlots * kTileN + c0), v);   // cross terms
-#pragma unroll
-                for (int i = 0; i < 32; ++i) racc[c0 + i] += __uint_as_float(v[i]);
                 float other[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) other[i] = __shfl_xor_sync(0xffffffffu, racc[c0 + i], 1);
@@ -387,9 +459,9 @@ k5_gemm(const __grid_constant__ CUtensorMap xmap, int Kp, int ng, double2 *__res
                         const float d01 = even ? racc[c0 + cc + 1] : other[cc + 1];   // D[2g][2g'+1]
                         const float d10 = even ? other[cc] : racc[c0 + cc];           // D[2g+1][2g']
                         const float d11 = even ? other[cc + 1] : racc[c0 + cc + 1];   // D[2g+1][2g'+1]
-                        const int gp = (b_row + c0 + cc) >> 1;
-                        if ((q < 8) == even && gp < ng) {
-                            double2 *o = acc + ((long)j * ng + g) * ng + gp;
+                        const int gp2 = (b_row + c0 + cc) >> 1;
+                        if ((q < 8) == even && gp2 < ng) {
+                            double2 *o = acc + ((long)w.j * ng + g) * ng + gp2;
                             double2 t = *o;
                             t.x += (double)d00 + (double)d11;
                             t.y += (double)d01 - (double)d10;
@@ -450,28 +522,43 @@ cudaError_t mixed_split(const void *M, int P, int ng, const double *w, int nfreq
     return cudaGetLastError();
 }
 
-cudaError_t mixed_gemm(int P, int ng, int nfreq, void *ws, void *acc, cudaStream_t st, int *err) {
-    if (P == 0) return cudaSuccess;
+int mixed_max_group() { return kMaxGroup; }
+
+cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaStream_t st, int *err) {
+    if (nq < 1 || nq > kMaxGroup) return cudaErrorInvalidValue;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
-    const long R = round_up(2L * ng, kTileM);
-    const long Kp = round_up(P, kBlockK);
-    const int planes = 2 * (1 + nfreq);
-    CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
-    const cuuint32_t box[3] = {kBlockK, kTileM, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult cr = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ws, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    GroupParams gp;
+    memset(&gp, 0, sizeof gp);
+    gp.nq = nq;
+    gp.nfreq = nfreq;
+    int items = 0;
+    for (int i = 0; i < nq; ++i) {
+        gp.first[i] = items;
+        const long R = round_up(2L * qs[i].ng, kTileM);
+        const long Kp = round_up(qs[i].P, kBlockK);
+        const int nt = (int)(R / kTileM);
+        if (qs[i].P > 0) items += nt * (nt + 1) / 2 * nfreq;
+        gp.kp[i] = (int)Kp;
+        gp.ng[i] = qs[i].ng;
+        gp.acc[i] = static_cast<double2 *>(qs[i].acc);
+        const int planes = 2 * (1 + nfreq);
+        const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)planes};
+        const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
+        const cuuint32_t box[3] = {kBlockK, kTileM, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        CUresult cr = g_encode(&gp.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, qs[i].ws, dims, strides,
+                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    gp.first[nq] = items;
+    if (items == 0) return cudaSuccess;
     const int smem = kStages * kStageBytes + 1024;
     e = cudaFuncSetAttribute(k5_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int nt = (int)(R / kTileM);
-    dim3 ggrid((unsigned)(nt * (nt + 1) / 2), (unsigned)nfreq);
-    k5_gemm<<<ggrid, kGemmWarps * 32, smem, st>>>(map, (int)Kp, ng, static_cast<double2 *>(acc), err);
+    const int grid = items < sm_count ? items : sm_count;
+    k5_gemm<<<grid, kGemmWarps * 32, smem, st>>>(gp, err);
     return cudaGetLastError();
 }
 

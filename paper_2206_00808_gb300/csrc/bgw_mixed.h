@@ -15,10 +15,22 @@ size_t mixed_workspace_bytes(long P, int ng, int nfreq);
 cudaError_t mixed_split(const void *M, int P, int ng, const double *w, int nfreq, void *ws,
                         cudaStream_t st);
 
-// acc[j][g][g'] (complex128, lower block triangle) += sum_p w[j][p]
-// conj(M[p][g]) M[p][g'] from the planes in ws, on tcgen05 tensor cores.
-// A device-side wait that gives up writes a non-zero code to the device int
-// *err (the host reports BGW_E_TIMEOUT when it reads it back).
-cudaError_t mixed_gemm(int P, int ng, int nfreq, void *ws, void *acc, cudaStream_t st, int *err);
+// One q-point of a grouped contraction: its split planes (from mixed_split),
+// pair count and accumulator.
+struct MixedQ {
+    void *ws;
+    int P, ng;
+    void *acc;
+};
+
+// Largest number of q-points one grouped launch takes.
+int mixed_max_group();
+
+// For every q of the group, acc[j][g][g'] (complex128, lower block triangle)
+// += sum_p w[j][p] conj(M[p][g]) M[p][g'] from its planes, on tcgen05 tensor
+// cores, in ONE persistent launch of at most sm_count blocks.  A device-side
+// wait that gives up writes a non-zero code to the device int *err (the host
+// reports BGW_E_TIMEOUT when it reads it back).
+cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaStream_t st, int *err);
 
 }  // namespace bgw

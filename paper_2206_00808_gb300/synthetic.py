@@ -36,7 +36,7 @@ import numpy as np
 __all__ = [
     "Problem", "fcc_cell", "rhombohedral_cell", "reciprocal", "kgrid_points",
     "wfn_sphere", "eps_sphere", "spinor_coefficients", "band_energies",
-    "make_problem", "CONFIGS", "spinless_to_spinor", "rotate_spin",
+    "make_problem", "make_batched_problem", "CONFIGS", "spinless_to_spinor", "rotate_spin",
     "plane_wave_bands",
 ]
 
@@ -207,6 +207,26 @@ CONFIGS = {
     "gasb32": dict(config_id=2, a=11.53, box=(32, 32, 32), ecut_wfn=85.0, ng=800,
                    kgrid=(6, 6, 6), nv=18, nc=400, q=(1 / 6, 0, 0), nfreq=16, precision="mixed"),
 }
+
+
+def make_batched_problem(config_id: int = 3, a: float = 11.53, box=(32, 32, 32),
+                         ecut_wfn: float = 85.0, kgrid=(6, 6, 6), nv: int = 18, nq: int = 40,
+                         ng_range=(700, 900), nc_range=(300, 500), nfreq: int = 16,
+                         precision: str = "mixed") -> Problem:
+    """Many q-points of one k-grid with ragged sizes: q = the first nq grid
+    vectors after Gamma in lexicographic order; per q a dielectric sphere of
+    N_G(q) ~ U{ng_range} smallest |q+G|^2 and N_c(q) ~ U{nc_range} conduction
+    bands (seeded).  Bands are generated for the largest N_c."""
+    rng = _rng(config_id, 0, 2)
+    ngs = rng.integers(ng_range[0], ng_range[1] + 1, nq)
+    ncs = rng.integers(nc_range[0], nc_range[1] + 1, nq)
+    nc_max = int(ncs.max())
+    p = _fcc_problem(f"batch{nq}", config_id, a, box, ecut_wfn, int(ngs[0]), kgrid, nv, nc_max,
+                     (0.0, 0.0, 0.0), nfreq, precision)
+    bvec = reciprocal(p.avec)
+    qpts = kgrid_points(kgrid)[1:nq + 1]
+    p.qs = [(q, eps_sphere(bvec, q, int(ng)), int(nc)) for q, ng, nc in zip(qpts, ngs, ncs)]
+    return p
 
 
 def make_problem(name: str, **overrides) -> Problem:
