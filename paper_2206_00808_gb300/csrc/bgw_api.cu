@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <utility>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -382,16 +383,39 @@ size_t mixed_q_bytes(const bgw_ctx_s *c, const QState &s, int nfreq, int kchunk)
     return align256(bgw::mixed_workspace_bytes((long)kchunk * c->nv * s.nc, s.ng, nfreq));
 }
 
+// Consecutive q-points contracted by one grouped launch (mixed path): at
+// most mixed_max_group() of them and, past the first, no more than
+// kGroupBytes of split operands.  FP64: one q per group.
+constexpr size_t kGroupBytes = (size_t)4 << 30;
+
+std::vector<std::pair<size_t, size_t>> form_groups(const bgw_ctx_s *c, const std::vector<QState> &qs,
+                                                   int nfreq, int kchunk) {
+    std::vector<std::pair<size_t, size_t>> groups;
+    const size_t G = c->prec == BGW_FP64 ? 1 : (size_t)bgw::mixed_max_group();
+    size_t b = 0;
+    while (b < qs.size()) {
+        size_t e = b, bytes = 0;
+        while (e < qs.size() && e - b < G) {
+            const size_t qb = c->prec == BGW_FP64 ? 0 : mixed_q_bytes(c, qs[e], nfreq, kchunk);
+            if (e > b && bytes + qb > kGroupBytes) break;
+            bytes += qb;
+            ++e;
+        }
+        groups.emplace_back(b, e);
+        b = e;
+    }
+    return groups;
+}
+
 // Scratch for contraction launches of up to kchunk k-points on every q
 // (mixed: the split operands of a whole group of q-points at once).
 cudaError_t ensure_chunk_scratch(bgw_ctx_s *c, const std::vector<QState> &qs, int nfreq, int kchunk) {
     long Pmax = 0, Mbytes = 0;
     size_t ws = 0;
     cudaError_t e = cudaSuccess;
-    const int G = bgw::mixed_max_group();
-    for (size_t g0 = 0; g0 < qs.size(); g0 += G) {
+    for (auto &gr : form_groups(c, qs, nfreq, kchunk)) {
         size_t sum = 0;
-        for (size_t i = g0; i < qs.size() && i < g0 + G; ++i) {
+        for (size_t i = gr.first; i < gr.second; ++i) {
             const QState &s = qs[i];
             if (c->prec != BGW_FP64)
                 sum += mixed_q_bytes(c, s, nfreq, kchunk);
@@ -488,14 +512,14 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
                       int k_begin, int k_end, int kchunk, int tv, int tc, bool &clean) {
     cudaError_t e = cudaSuccess;
     const double *energy = static_cast<const double *>(c->energy.p);
-    const int G = c->prec == BGW_FP64 ? 1 : bgw::mixed_max_group();
+    const auto groups = form_groups(c, qs, nfreq, kchunk);
     std::vector<bgw::MixedQ> group;
     for (int k0 = k_begin; k0 < k_end; k0 += kchunk) {
         const int kn = std::min(kchunk, k_end - k0);
-        for (size_t g0 = 0; g0 < qs.size(); g0 += G) {
+        for (auto &gr : groups) {
             group.clear();
             size_t off = 0;
-            for (size_t iq = g0; iq < qs.size() && iq < g0 + G; ++iq) {
+            for (size_t iq = gr.first; iq < gr.second; ++iq) {
                 QState &s = qs[iq];
                 const long P = (long)c->nv * s.nc;
                 for (int kl = 0; kl < kn; ++kl) {
