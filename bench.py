@@ -38,6 +38,9 @@ WORKLOADS = {
                          "N_G=800, N_k=216 (6x6x6), N_v=18, N_c=400, 16 imaginary freqs, q=(1/6,0,0)"),
     "gasb32_batch": ("batch", "40 q-points of the GaSb-like 6x6x6 grid in one accumulate call: "
                               "32^3 box, N_G(q)~U{700..900}, N_c(q)~U{300..500}, N_v=18, 16 freqs"),
+    "bi2se3": ("bi2se3", "Bi2Se3-like rhombohedral cell (hex a=4.143 A, c=28.636 A), 64^3 box, "
+                         "N_w~9000 per spinor component, N_G=2000, N_k=216 (6x6x6), N_v=48, N_c=1000, "
+                         "8 imaginary freqs, q=(1/6,0,0); real-space grids streamed through 8 slots"),
 }
 METRIC = "spinor chi0 q-points/s and TFLOP/s, FP64 vs mixed at ≤2e-5 rel. Frobenius error"
 
@@ -65,6 +68,11 @@ def parse_args():
     ap.add_argument("--no-autotune", action="store_true", help="default tiles and k-chunk")
     ap.add_argument("--check-fp64", type=int, default=0, metavar="NQ",
                     help="with --precision mixed: compare the first NQ q-points with one FP64 run")
+    ap.add_argument("--check-kspan", type=int, default=0, metavar="NK",
+                    help="restrict the FP64 comparison to k-points 0..NK-1 (both precisions)")
+    ap.add_argument("--grid-slots", type=int, default=-1,
+                    help="real-space grid slots (0 = all k resident; default 8 for bi2se3, else 0)")
+    ap.add_argument("--kchunk", type=int, default=0, help="k-chunk when not autotuning")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")
     return ap.parse_args()
 
@@ -217,6 +225,8 @@ def make_workload(name):
     over, desc = WORKLOADS[name]
     if over == "batch":
         return syn.make_batched_problem(), desc
+    if over == "bi2se3":
+        return syn.make_bi2se3_problem(), desc
     if isinstance(over, str):
         return syn.make_problem(over), desc
     return syn.make_problem("si24", **over), desc
@@ -271,6 +281,10 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     outs = [torch.empty((nf, len(g), len(g)), dtype=torch.complex128, device="cuda") for _, g, _ in p.qs]
     torch.cuda.synchronize()
     ctx = B.Chi0Context(p, precision, stream)
+    if args.grid_slots > 0:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_GRID_SLOTS, args.grid_slots)
+    if args.kchunk > 0:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk)
     ctx.upload(device_inputs=dev_in)
     tune_span = min(p.nk, 16 if precision == "mixed" else 4)
     tuning = ctx.autotune(0, tune_span) if not args.no_autotune else None
@@ -369,11 +383,16 @@ def run_ours(args, world, rank, local):
     from paper_2206_00808_gb300 import binding as B
 
     p, desc = make_workload(args.workload)
+    if args.grid_slots < 0:
+        args.grid_slots = 8 if args.workload == "bi2se3" else 0
     q, geps, nc = p.qs[0]
     ng, nf = len(geps), len(p.freq)
     stream = torch.cuda.Stream()      # graph capture needs a non-default stream
-    dev_in = [(torch.from_numpy(np.ascontiguousarray(p.coeff[ik])).cuda(),
-               torch.from_numpy(np.ascontiguousarray(p.energy[ik])).cuda()) for ik in range(p.nk)]
+
+    def dev(x):
+        return x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+    dev_in = [(dev(p.coeff[ik]), dev(p.energy[ik])) for ik in range(p.nk)]
     fl = flop_model(p)
     steps = args.steps
 
@@ -410,19 +429,22 @@ def run_ours(args, world, rank, local):
         import copy
         sub = copy.copy(p)
         sub.qs = p.qs[:args.check_fp64]
-        ctx64 = B.Chi0Context(sub, "fp64", stream)
-        ctx64.upload(device_inputs=dev_in)
-        gpu_t = time.perf_counter()
-        ctx64.accumulate()
-        errs = []
-        for iq in range(len(sub.qs)):
-            r = ctx64.finalize(iq)
-            g = head["outs"][iq].cpu().numpy()
-            errs.append(rel_fro(g, r))
-        check = {"q_points_checked": len(sub.qs), "rel_fro_err_vs_fp64_max": max(errs),
-                 "fp64_seconds": time.perf_counter() - gpu_t,
+        kspan = args.check_kspan if args.check_kspan > 0 else p.nk
+        res = {}
+        for prec in ("fp64", "mixed"):
+            cx = B.Chi0Context(sub, prec, stream)
+            if args.grid_slots > 0:
+                B.bgw_set_option(cx.ctx, B.BGW_OPT_GRID_SLOTS, args.grid_slots)
+            cx.upload(device_inputs=dev_in)
+            t0 = time.perf_counter()
+            cx.accumulate(0, kspan)
+            res[prec] = [cx.finalize(iq) for iq in range(len(sub.qs))]
+            res[prec + "_s"] = time.perf_counter() - t0
+            cx.close()
+        errs = [rel_fro(g, r) for g, r in zip(res["mixed"], res["fp64"])]
+        check = {"q_points_checked": len(sub.qs), "k_points": kspan,
+                 "rel_fro_err_vs_fp64_max": max(errs), "fp64_seconds": res["fp64_s"],
                  "error_reference": "the FP64 GPU path (itself within 1e-10 of the CPU oracle)"}
-        ctx64.close()
 
     other = None
     if args.precision == "fp64" and not args.no_mixed:

@@ -102,8 +102,9 @@ BGW_API const char *bgw_version(void);
  *   nc_max  : empty bands held per k (bands nv..nv+nc_max-1)
  *   prec    : BGW_FP64 or BGW_MIXED_BF16X3
  *   stream  : cudaStream_t to queue all work on (NULL = default stream)
- * Allocates the real-space grids, nk * (nv+nc_max) * 2 * N1*N2*N3 complex
- * values (complex128 for FP64, complex64 for mixed), on the current device.
+ * The real-space grids, nk * (nv+nc_max) * 2 * N1*N2*N3 complex values
+ * (complex128 for FP64, complex64 for mixed; fewer with BGW_OPT_GRID_SLOTS),
+ * are allocated on the current device at the first bgw_wfn_upload.
  * Errors: BGW_E_ARG, BGW_E_NOMEM, BGW_E_CUDA.
  */
 BGW_API bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const double *kcrys,
@@ -190,8 +191,19 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        a multiple of the k-chunk.
  *   BGW_OPT_PAIR_TILE_V  valence x conduction pair tile of the FP32 matrix-
  *   BGW_OPT_PAIR_TILE_C  element kernel (0 = automatic, else 1..16).
+ *   BGW_OPT_GRID_SLOTS   real-space grids kept on the device: 0 (default) =
+ *                        every k, built at upload; n < nk = k-point
+ *                        streaming: uploads keep only the coefficients on the
+ *                        device and accumulate builds the grids of the k-points
+ *                        it needs into n slots (least recently used first),
+ *                        for workloads whose grids exceed device memory.  Set
+ *                        before the first upload.  In this mode a device
+ *                        upload (on_device = 1) keeps a reference to the
+ *                        caller's coefficient buffer instead of a copy: keep it
+ *                        alive and unchanged until the k-point is uploaded
+ *                        again or the context is destroyed.
  */
-enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3 };
+enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

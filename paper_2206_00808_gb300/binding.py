@@ -28,7 +28,7 @@ EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "
             "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
             "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune",
             "bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch", "bgw_destroy", "bgw_last_error"]
-BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C = 1, 2, 3
+BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C, BGW_OPT_GRID_SLOTS = 1, 2, 3, 4
 STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split"]
 
 

@@ -62,8 +62,12 @@ struct DevBuf {
 struct KPoint {
     bool uploaded = false;
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // sphere extents (Miller)
+    int ngw = 0;
     std::vector<int> cube_map;                  // host copy of the device map
     DevBuf map_dev;
+    DevBuf coeff;                               // streaming mode: device copy of host coefficients
+    const double *coeff_src = nullptr;          // streaming mode: coefficients the grid is built from
+    int slot = -1;                              // grid slot holding this k (-1: none)
 };
 
 struct QState {
@@ -139,6 +143,14 @@ struct bgw_ctx_s {
     DevBuf out_stage;    // finalize to host
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
     DevBuf errflag;      // device int: non-zero after a bounded device wait gave up
+    // real-space grid slots: every k resident (nslots == nk), or a
+    // least-recently-used cache of nslots grids (streaming)
+    int grid_slots_opt = 0;
+    int nslots = 0;
+    std::vector<int> slot_k;
+    std::vector<long> slot_stamp;
+    long use_clock = 0;
+    bool streaming() const { return nslots > 0 && nslots < nk; }
     // graph capture (bgw_graph_*)
     bool capturing = false;
     cudaGraphExec_t gexec = nullptr;
@@ -209,8 +221,8 @@ struct bgw_ctx_s {
         return e == cudaErrorMemoryAllocation ? BGW_E_NOMEM : BGW_E_CUDA;
     }
     long grid_elems_per_k() const { return (long)nb * 2 * nbox; }
-    char *grid_of(int ik, int band) {
-        return static_cast<char *>(grids.p) + ((long)ik * grid_elems_per_k() + (long)band * 2 * nbox) * csize;
+    char *slot_ptr(int slot, int band) {
+        return static_cast<char *>(grids.p) + ((long)slot * grid_elems_per_k() + (long)band * 2 * nbox) * csize;
     }
 };
 
@@ -226,6 +238,73 @@ bgw_status bgw_ctx_s::fail(bgw_status s, const char *fmt, ...) {
 }
 
 namespace {
+
+// Grid slots are allocated at the first upload: every k (default) or the
+// BGW_OPT_GRID_SLOTS most recently used ones.
+cudaError_t ensure_slots(bgw_ctx_s *c) {
+    if (c->nslots > 0) return cudaSuccess;
+    const int n = (c->grid_slots_opt > 0 && c->grid_slots_opt < c->nk) ? std::max(2, c->grid_slots_opt)
+                                                                         : c->nk;
+    cudaError_t e = c->grids.ensure((size_t)n * c->grid_elems_per_k() * c->csize, c->st);
+    if (e != cudaSuccess) return e;
+    c->nslots = n;
+    c->slot_k.assign(n, -1);
+    c->slot_stamp.assign(n, 0);
+    return cudaSuccess;
+}
+
+// Sphere -> real-space grid of every band of k into grid slot `slot`.
+cudaError_t run_k1(bgw_ctx_s *c, int ik, const double *src, int slot) {
+    KPoint &kp = c->k[ik];
+    const long B = 2L * c->nb;
+    int w[3];
+    for (int a = 0; a < 3; ++a) w[a] = kp.hi[a] - kp.lo[a] + 1;
+    const size_t sbytes = (size_t)B * c->box[0] * w[1] * w[2] * c->csize;
+    const size_t rbytes = (size_t)B * c->box[0] * c->box[1] * w[2] * c->csize;
+    cudaError_t e = c->S.ensure(sbytes, c->st);
+    if (e == cudaSuccess) e = c->R.ensure(rbytes, c->st);
+    if (e != cudaSuccess) return e;
+    bgw::Axes ax;
+    for (int a = 0; a < 3; ++a) {
+        ax.n[a] = c->box[a];
+        ax.w[a] = w[a];
+        ax.s[a] = pmod(kp.lo[a], c->box[a]);
+    }
+    void *U = c->slot_ptr(slot, 0);
+    const int *mp = static_cast<const int *>(kp.map_dev.p);
+    const int rec = c->stage_begin(0);
+    e = (c->prec == BGW_FP64)
+            ? bgw::wfn_to_grid_f64(src, kp.ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st)
+            : bgw::wfn_to_grid_f32(src, kp.ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st);
+    c->stage_end(rec, 3);
+    return e;
+}
+
+// Grid slot of k: resident mode, slot k; streaming, the k's slot if cached,
+// else the least recently used slot is rebuilt from the stored coefficients.
+// Every use and rebuild is queued on the one context stream, so a slot is
+// never overwritten before the kernels that read it have run.
+int ensure_grid(bgw_ctx_s *c, int ik, cudaError_t &e) {
+    e = cudaSuccess;
+    if (!c->streaming()) return ik;
+    KPoint &kp = c->k[ik];
+    if (kp.slot < 0) {
+        int victim = 0;
+        for (int i = 1; i < c->nslots; ++i)
+            if (c->slot_stamp[i] < c->slot_stamp[victim]) victim = i;
+        if (c->slot_k[victim] >= 0) c->k[c->slot_k[victim]].slot = -1;
+        c->slot_k[victim] = ik;
+        kp.slot = victim;
+        e = run_k1(c, ik, kp.coeff_src, victim);
+        if (e != cudaSuccess) {
+            c->slot_k[victim] = -1;
+            kp.slot = -1;
+            return -1;
+        }
+    }
+    c->slot_stamp[kp.slot] = ++c->use_clock;
+    return kp.slot;
+}
 
 // k + q = k' + G0 with k' on the list (tolerance 1e-6 in crystal units).
 bool find_umklapp(const bgw_ctx_s *c, int ik, const double q[3], int &kp, int G0[3]) {
@@ -275,16 +354,28 @@ bgw_status prepare_q(bgw_ctx_s *c, const bgw_q *q, QState &s) {
         }
     for (int a = 0; a < 3; ++a) s.w[a] = std::min(s.emax[a] - s.emin[a] + 1, c->box[a]);
     const long cube = (long)s.w[0] * s.w[1] * s.w[2];
-    if (cube * (long)c->csize > 200 * 1024)
-        return c->fail(BGW_E_ARG, "dielectric sphere spans a %dx%dx%d cube, too wide for one block",
-                       s.w[0], s.w[1], s.w[2]);
-    s.gmap.resize(s.ng);
+    bgw::Axes ax;
+    for (int a = 0; a < 3; ++a) {
+        ax.n[a] = c->box[a];
+        ax.w[a] = s.w[a];
+        ax.s[a] = 0;
+    }
+    const bool scatter = bgw::mtxel_scatter_mode(ax, c->csize);
     // Two G that agree mod N (an aliased sphere) share a cube cell and both
     // read the same cyclic value, which is what the FFT route gives.
+    s.gmap.assign(s.ng + (scatter ? cube : 0), -1);
     for (int g = 0; g < s.ng; ++g) {
         int j[3];
         for (int a = 0; a < 3; ++a) j[a] = pmod((long)s.gvec[3 * g + a] - s.emin[a], c->box[a]);
-        s.gmap[g] = (j[0] * s.w[1] + j[1]) * s.w[2] + j[2];
+        const int cell = (j[0] * s.w[1] + j[1]) * s.w[2] + j[2];
+        s.gmap[g] = cell;
+        if (scatter) {
+            if (s.gmap[s.ng + cell] >= 0)
+                return c->fail(BGW_E_ARG, "dielectric sphere aliased on this box (two G share a cell) "
+                                          "and too wide (%dx%dx%d) for the shared-memory gather",
+                               s.w[0], s.w[1], s.w[2]);
+            s.gmap[s.ng + cell] = g;
+        }
     }
     compute_kmap(c, s);
     return BGW_OK;
@@ -320,9 +411,16 @@ bgw::Axes mtxel_axes(const bgw_ctx_s *c, const QState &s, const int G0[3]) {
     return ax;
 }
 
-// Scratch for P pairs of one k on sphere s; M block too if want_m.
+// Scratch of the matrix-element kernels for one k of q-point s (P = nv x nc
+// pairs, processed in batches of whole valence bands).
 cudaError_t ensure_mtxel_scratch(bgw_ctx_s *c, const QState &s, long P) {
     const long n01 = (long)c->box[0] * c->box[1];
+    if (P > 0) {
+        const int nc = (int)(P / c->nv);
+        const int G0z[3] = {0, 0, 0};
+        const bgw::Axes ax = mtxel_axes(c, s, G0z);
+        P = (long)bgw::mtxel_v_batch((int)(P / std::max(1, nc)), nc, ax, c->csize) * nc;
+    }
     cudaError_t e = c->A.ensure((size_t)(P * n01 * s.w[2]) * c->csize, c->st);
     if (e == cudaSuccess) e = c->Bs.ensure((size_t)(P * c->box[0] * s.w[1] * s.w[2]) * c->csize, c->st);
     return e;
@@ -331,8 +429,13 @@ cudaError_t ensure_mtxel_scratch(bgw_ctx_s *c, const QState &s, long P) {
 cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const int G0[3], int v0,
                          int nv, int c0, int nc, void *M, long ldm, int tv = 0, int tc = 0) {
     const bgw::Axes ax = mtxel_axes(c, s, G0);
-    const void *Uv = c->grid_of(ik, v0);
-    const void *Uc = c->grid_of(kp, c->nv + c0);
+    cudaError_t ge;
+    const int sv = ensure_grid(c, ik, ge);
+    if (ge != cudaSuccess) return ge;
+    const int sc = ensure_grid(c, kp, ge);
+    if (ge != cudaSuccess) return ge;
+    const void *Uv = c->slot_ptr(sv, v0);
+    const void *Uc = c->slot_ptr(sc, c->nv + c0);
     const int *gmap = static_cast<const int *>(s.gmap_dev.p);
     const int rec = c->stage_begin(1);
     cudaError_t e = (c->prec == BGW_FP64)
@@ -466,7 +569,7 @@ bgw_status install_qset(bgw_ctx_s *c, std::vector<QState> &fresh, int nfreq, con
         }
     }
     for (auto &s : fresh) {
-        e = s.gmap_dev.ensure(sizeof(int) * (size_t)s.ng, c->st);
+        e = s.gmap_dev.ensure(sizeof(int) * s.gmap.size(), c->st);
         if (e == cudaSuccess) e = s.kmap_dev.ensure(sizeof(int) * (size_t)c->nk, c->st);
         if (e == cudaSuccess) e = s.acc.ensure(16 * (size_t)nfreq * s.ng * s.ng, c->st);
         if (e != cudaSuccess) {
@@ -490,7 +593,7 @@ bgw_status install_qset(bgw_ctx_s *c, std::vector<QState> &fresh, int nfreq, con
                             cudaMemcpyHostToDevice, c->st);
         for (auto &s : c->qs) {
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(s.gmap_dev.p, s.gmap.data(), sizeof(int) * s.ng,
+                e = cudaMemcpyAsync(s.gmap_dev.p, s.gmap.data(), sizeof(int) * s.gmap.size(),
                                     cudaMemcpyHostToDevice, c->st);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(s.kmap_dev.p, s.kmap.data(), sizeof(int) * c->nk,
@@ -627,12 +730,11 @@ bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const double *kcry
         c->sm_count < 1)
         c->sm_count = 1;
     c->k.resize(nk);
-    e = c->grids.ensure((size_t)nk * c->grid_elems_per_k() * c->csize, c->st);
-    if (e == cudaSuccess) e = c->energy.ensure(sizeof(double) * (size_t)nk * c->nb, c->st);
+    e = c->energy.ensure(sizeof(double) * (size_t)nk * c->nb, c->st);
     if (e == cudaSuccess) e = c->errflag.ensure(sizeof(int), c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st);
     if (e != cudaSuccess) {
-        g_create_error = std::string("bgw_create: allocating grids: ") + cudaGetErrorString(e);
+        g_create_error = std::string("bgw_create: allocating buffers: ") + cudaGetErrorString(e);
         const bgw_status s = (e == cudaErrorMemoryAllocation) ? BGW_E_NOMEM : BGW_E_CUDA;
         cudaGetLastError();
         c->grids.release();
@@ -690,9 +792,24 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
                             cudaMemcpyHostToDevice, c->st);
         if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: map copy");
     }
-    const double *src = coeff;
+    e = ensure_slots(c);
+    if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: real-space grids");
     const size_t cbytes = sizeof(double) * 2 * (size_t)B * ngw;
-    if (!on_device) {
+    const double *src = coeff;
+    if (c->streaming()) {
+        // keep the coefficients (device inputs by reference, host inputs in a
+        // device copy); the grid is built when a k-chunk needs it
+        if (on_device) {
+            kp.coeff.release();
+            kp.coeff_src = coeff;
+        } else {
+            e = kp.coeff.ensure(cbytes, c->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(kp.coeff.p, coeff, cbytes, cudaMemcpyHostToDevice, c->st);
+            if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: coefficient store");
+            kp.coeff_src = static_cast<const double *>(kp.coeff.p);
+        }
+    } else if (!on_device) {
         e = c->stage.ensure(cbytes, c->st);
         if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: staging buffer");
         e = cudaMemcpyAsync(c->stage.p, coeff, cbytes, cudaMemcpyHostToDevice, c->st);
@@ -703,28 +820,20 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
                         sizeof(double) * c->nb,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st);
     if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: energy copy");
-    const size_t sbytes = (size_t)B * c->box[0] * w[1] * w[2] * c->csize;
-    const size_t rbytes = (size_t)B * c->box[0] * c->box[1] * w[2] * c->csize;
-    e = c->S.ensure(sbytes, c->st);
-    if (e == cudaSuccess) e = c->R.ensure(rbytes, c->st);
-    if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: transform scratch");
-    bgw::Axes ax;
-    for (int a = 0; a < 3; ++a) {
-        ax.n[a] = c->box[a];
-        ax.w[a] = w[a];
-        ax.s[a] = pmod(lo[a], c->box[a]);
-    }
-    void *U = c->grid_of(ik, 0);
-    const int *mp = static_cast<const int *>(kp.map_dev.p);
-    const int rec = c->stage_begin(0);
-    e = (c->prec == BGW_FP64)
-            ? bgw::wfn_to_grid_f64(src, ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st)
-            : bgw::wfn_to_grid_f32(src, ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st);
-    c->stage_end(rec, 3);
-    if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: sphere-to-grid kernels");
     for (int a = 0; a < 3; ++a) {
         kp.lo[a] = lo[a];
         kp.hi[a] = hi[a];
+    }
+    kp.ngw = ngw;
+    if (c->streaming()) {
+        if (kp.slot >= 0) {            // the cached grid is stale now
+            c->slot_k[kp.slot] = -1;
+            c->slot_stamp[kp.slot] = 0;
+            kp.slot = -1;
+        }
+    } else {
+        e = run_k1(c, ik, src, ik);
+        if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: sphere-to-grid kernels");
     }
     kp.uploaded = true;
     return BGW_OK;
@@ -754,9 +863,10 @@ bgw_status bgw_mtxel_spinor(bgw_ctx c, const bgw_q *q, int ik, int v0, int nv, i
     if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: scratch");
     // The per-call map goes to a context buffer; reuse is stream-ordered and
     // a pageable-memory copy has read the host vector when the call returns.
-    e = c->gmap_tmp.ensure(sizeof(int) * (size_t)s.ng, c->st);
+    e = c->gmap_tmp.ensure(sizeof(int) * s.gmap.size(), c->st);
     if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: map buffer");
-    e = cudaMemcpyAsync(c->gmap_tmp.p, s.gmap.data(), sizeof(int) * s.ng, cudaMemcpyHostToDevice, c->st);
+    e = cudaMemcpyAsync(c->gmap_tmp.p, s.gmap.data(), sizeof(int) * s.gmap.size(), cudaMemcpyHostToDevice,
+                        c->st);
     if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: map copy");
     s.gmap_dev.p = c->gmap_tmp.p;   // borrowed, not owned
     e = launch_mtxel(c, s, ik, kp, G0, v0, nv, c0, nc, M_dev, s.ng);
@@ -854,6 +964,11 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
             if (value < 0 || value > 16) return c->fail(BGW_E_ARG, "set_option: pair tile must be 0..16");
             (option == BGW_OPT_PAIR_TILE_V ? c->tile_v : c->tile_c) = (int)value;
             return BGW_OK;
+        case BGW_OPT_GRID_SLOTS:
+            if (c->nslots > 0) return c->fail(BGW_E_STATE, "set_option: grid slots are fixed at the first upload");
+            if (value < 0 || value > c->nk) return c->fail(BGW_E_ARG, "set_option: grid slots must be 0..nk");
+            c->grid_slots_opt = (int)value;
+            return BGW_OK;
         default:
             return c->fail(BGW_E_ARG, "set_option: unknown option %d", option);
     }
@@ -866,6 +981,7 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_KCHUNK: *value = c->kchunk; return BGW_OK;
         case BGW_OPT_PAIR_TILE_V: *value = c->tile_v; return BGW_OK;
         case BGW_OPT_PAIR_TILE_C: *value = c->tile_c; return BGW_OK;
+        case BGW_OPT_GRID_SLOTS: *value = c->nslots > 0 ? c->nslots : c->grid_slots_opt; return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }
@@ -909,10 +1025,10 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
     DevBuf tfreq;
     cudaError_t e = tfreq.ensure(sizeof(double) * nfreq, c->st);
     for (auto &s : tq) {
-        if (e == cudaSuccess) e = s.gmap_dev.ensure(sizeof(int) * (size_t)s.ng, c->st);
+        if (e == cudaSuccess) e = s.gmap_dev.ensure(sizeof(int) * s.gmap.size(), c->st);
         if (e == cudaSuccess) e = s.kmap_dev.ensure(sizeof(int) * (size_t)c->nk, c->st);
         if (e == cudaSuccess) e = s.acc.ensure(16 * (size_t)nfreq * s.ng * s.ng, c->st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.gmap_dev.p, s.gmap.data(), sizeof(int) * s.ng,
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.gmap_dev.p, s.gmap.data(), sizeof(int) * s.gmap.size(),
                                                   cudaMemcpyHostToDevice, c->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.kmap_dev.p, s.kmap.data(), sizeof(int) * c->nk,
                                                   cudaMemcpyHostToDevice, c->st);
@@ -1101,7 +1217,10 @@ void bgw_destroy(bgw_ctx c) {
             cudaEventDestroy(r.b);
         }
         for (auto ev : c->pool) cudaEventDestroy(ev);
-        for (auto &k : c->k) k.map_dev.release();
+        for (auto &k : c->k) {
+            k.map_dev.release();
+            k.coeff.release();
+        }
         for (auto &s : c->qs) {
             s.gmap_dev.release();
             s.kmap_dev.release();

@@ -159,7 +159,7 @@ k2_zpass(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, lon
     C a[N];
 #pragma unroll
     for (int z = 0; z < N; ++z)
-        a[z] = cadd(cconjmul(v0[z], c0[z]), cconjmul(v0[vol + z], c0[vol + z]));
+        a[z] = rho2(v0[z], c0[z], v0[vol + z], c0[vol + z]);
     fft_line<T, -1, N>(a);
     const int ns = N - s2;
 #pragma unroll
@@ -218,12 +218,42 @@ k2_xpass_gather(const C *__restrict__ Bs, int w0, int w1, int w2, int s0,
     }
 }
 
+// Pass x + scatter: one thread per (pair, line); every kept output goes to
+// M[p][imap[cell]] when that cell holds a G-vector (large kept cubes).
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k2_xpass_scatter(const C *__restrict__ Bs, long P, int w0, int w1, int w2, int s0,
+                 const int *__restrict__ imap, T scale, C *__restrict__ M, long ldm) {
+    const long lines = (long)w1 * w2;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P * lines) return;
+    const long l = t % lines, p = t / lines;
+    C a[N];
+#pragma unroll
+    for (int x = 0; x < N; ++x) a[x] = Bs[(p * N + x) * lines + l];
+    fft_line<T, -1, N>(a);
+    const int ns = N - s0;
+#pragma unroll
+    for (int f = 0; f < N; ++f) {
+        const int j = rot<N>(f, ns);
+        if (j < w0) {
+            const int g = __ldg(imap + j * lines + l);
+            if (g >= 0) M[p * ldm + g] = C{a[f].x * scale, a[f].y * scale};
+        }
+    }
+}
+
 // ----------------------------------------- plane-fused passes (FP32) --
 // Band planes staged through shared memory with batched loads (kStageU in
 // flight per thread); every line is then read from a padded shared row.
 // Used when the box has n1 == n2.
 constexpr int kPlaneThreads = 256;
 constexpr int kStageU = 8;
+
+// Shared row length of a staged plane: one complex of padding for odd N, two
+// for even N (keeps rows 16-byte aligned for paired FP32 accesses).
+template <int N>
+__host__ __device__ constexpr int plane_row() { return N % 2 == 0 ? N + 2 : N + 1; }
 
 // Pair density + z pass + y pass for one x-plane and a tile of tv x tc pairs.
 // Shared: planes[(tv+tc)][2][N][N+1], then Z[tv*tc][N][w2].
@@ -237,32 +267,46 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
     const int v0 = blockIdx.y * TV, c0 = blockIdx.z * TC;
     const int tv = min(TV, nv - v0), tc = min(TC, nc - c0);
     const int n0 = gridDim.x;
-    constexpr int RS = N + 1;                   // padded row
+    constexpr int RS = plane_row<N>();         // padded row
     constexpr int PS = N * RS;                  // one spin component of a plane
     constexpr int NN = N * N;
+    constexpr bool kVec = sizeof(T) == 4 && N % 2 == 0;   // two complex per 16-byte access
     C *Z = planes + (long)(TV + TC) * 2 * PS;
     const long vol = (long)n0 * NN;
     // 1. stage the x-plane of every band of the tile (both spin components)
-    const int total = (tv + tc) * 2 * NN;
+    constexpr int VW = kVec ? 2 : 1;            // complex values per access
+    const int total = (tv + tc) * 2 * NN / VW;
     for (int base = threadIdx.x; base < total; base += kPlaneThreads * kStageU) {
-        C tmp[kStageU];
+        C tmp[kStageU][VW];
 #pragma unroll
         for (int u = 0; u < kStageU; ++u) {
             const int i = base + u * kPlaneThreads;
             if (i < total) {
-                const int ba = i / NN, yz = i % NN;     // ba = band * 2 + alpha
+                const int ba = (i * VW) / NN, yz = (i * VW) % NN;     // ba = band * 2 + alpha
                 const int b = ba >> 1, a = ba & 1;
                 const C *src = (b < tv) ? Uv + ((long)(v0 + b) * 2 + a) * vol
                                         : Uc + ((long)(c0 + b - tv) * 2 + a) * vol;
-                tmp[u] = src[(long)x * NN + yz];
+                if constexpr (kVec) {
+                    const float4 q = *reinterpret_cast<const float4 *>(src + (long)x * NN + yz);
+                    tmp[u][0] = C{q.x, q.y};
+                    tmp[u][VW - 1] = C{q.z, q.w};
+                } else {
+                    tmp[u][0] = src[(long)x * NN + yz];
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < kStageU; ++u) {
             const int i = base + u * kPlaneThreads;
             if (i < total) {
-                const int ba = i / NN, yz = i % NN;
-                planes[ba * PS + (yz / N) * RS + (yz % N)] = tmp[u];
+                const int ba = (i * VW) / NN, yz = (i * VW) % NN;
+                C *dst = planes + ba * PS + (yz / N) * RS + (yz % N);
+                if constexpr (kVec) {
+                    *reinterpret_cast<float4 *>(dst) =
+                        make_float4(tmp[u][0].x, tmp[u][0].y, tmp[u][VW - 1].x, tmp[u][VW - 1].y);
+                } else {
+                    dst[0] = tmp[u][0];
+                }
             }
         }
     }
@@ -276,9 +320,20 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
         const C *pv = planes + (v * 2) * PS + y * RS;
         const C *pc = planes + ((tv + c) * 2) * PS + y * RS;
         C a[N];
+        if constexpr (kVec) {
+            const float4 *v4 = reinterpret_cast<const float4 *>(pv);
+            const float4 *c4 = reinterpret_cast<const float4 *>(pc);
+            constexpr int P4 = PS / 2;
 #pragma unroll
-        for (int z = 0; z < N; ++z)
-            a[z] = cadd(cconjmul(pv[z], pc[z]), cconjmul(pv[PS + z], pc[PS + z]));
+            for (int z = 0; z < N / 2; ++z) {
+                const float4 va = v4[z], vb = v4[P4 + z], ca = c4[z], cb = c4[P4 + z];
+                a[2 * z] = rho2(C{va.x, va.y}, C{ca.x, ca.y}, C{vb.x, vb.y}, C{cb.x, cb.y});
+                a[2 * z + 1] = rho2(C{va.z, va.w}, C{ca.z, ca.w}, C{vb.z, vb.w}, C{cb.z, cb.w});
+            }
+        } else {
+#pragma unroll
+            for (int z = 0; z < N; ++z) a[z] = rho2(pv[z], pc[z], pv[PS + z], pc[PS + z]);
+        }
         fft_line<T, -1, N>(a);
         C *zo = Z + ((long)pr * N + y) * w2;
 #pragma unroll
@@ -392,6 +447,7 @@ static inline unsigned blocks_for(long n) { return (unsigned)((n + kLineThreads 
     }
 
 static constexpr size_t kPlaneSmemMax = 110 * 1024;   // two blocks per SM
+static constexpr size_t kPlaneSmemLarge = 200 * 1024;  // one block per SM (large boxes)
 
 static bool use_plane_kernels(const Axes &a) { return sizeof(T) == 4 && a.n[1] == a.n[2]; }
 
@@ -407,21 +463,27 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
     }
     if (use_plane_kernels(a)) {
         const int n = a.n[1];
-        const int TB = 4;
-        const size_t smem = sizeof(C) * ((size_t)TB * a.w[1] * a.w[2] + (size_t)TB * n * (a.w[2] + 1) +
-                                         (size_t)TB * n * (n + 1));
-        dim3 grid((unsigned)a.n[0], (unsigned)((nb + TB - 1) / TB));
-        cudaError_t e = cudaSuccess;
-        BGW_FOR_EACH_LEN(n, {
-            if (smem > 48 * 1024) {
-                e = cudaFuncSetAttribute(k1_yz_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-                if (e != cudaSuccess) return e;
-            }
-            k1_yz_plane<N><<<grid, kPlaneThreads, smem, st>>>(Sp, nb, TB, a.w[1], a.w[2], a.s[1],
-                                                             a.s[2], Up);
-        });
-        return cudaGetLastError();
+        auto yz_smem = [&](int tb) {
+            return sizeof(C) * ((size_t)tb * a.w[1] * a.w[2] + (size_t)tb * n * (a.w[2] + 1) +
+                                (size_t)tb * n * (n + 1));
+        };
+        int TB = 4;
+        while (TB > 1 && yz_smem(TB) > kPlaneSmemMax) --TB;
+        const size_t smem = yz_smem(TB);
+        if (smem <= kPlaneSmemLarge) {
+            dim3 grid((unsigned)a.n[0], (unsigned)((nb + TB - 1) / TB));
+            cudaError_t e = cudaSuccess;
+            BGW_FOR_EACH_LEN(n, {
+                if (smem > 48 * 1024) {
+                    e = cudaFuncSetAttribute(k1_yz_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+                    if (e != cudaSuccess) return e;
+                }
+                k1_yz_plane<N><<<grid, kPlaneThreads, smem, st>>>(Sp, nb, TB, a.w[1], a.w[2], a.s[1],
+                                                                 a.s[2], Up);
+            });
+            return cudaGetLastError();
+        }
     }
     {
         const long nbx = nb * a.n[0];
@@ -439,7 +501,8 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
 // Pair tiles (TV valence x TC conduction) of the plane kernel that fit
 // kPlaneSmemMax, best first: least staged data per pair, then most pairs.
 static size_t plane_smem(int tv, int tc, int n, int w2) {
-    return sizeof(C) * ((size_t)(tv + tc) * 2 * n * (n + 1) + (size_t)tv * tc * n * w2);
+    const int rs = n % 2 == 0 ? n + 2 : n + 1;
+    return sizeof(C) * ((size_t)(tv + tc) * 2 * n * rs + (size_t)tv * tc * n * w2);
 }
 
 static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int max) {
@@ -447,9 +510,10 @@ static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int 
     struct Cand { double cost; int tv, tc; };
     Cand best[64];
     int nbest = 0;
+    const size_t budget = plane_smem(1, 1, a.n[1], a.w[2]) <= kPlaneSmemMax ? kPlaneSmemMax : kPlaneSmemLarge;
     for (int tv = 1; tv <= nv && tv <= 16; ++tv)
         for (int tc = 1; tc <= nc && tc <= 16; ++tc) {
-            if (plane_smem(tv, tc, a.n[1], a.w[2]) > kPlaneSmemMax) continue;
+            if (plane_smem(tv, tc, a.n[1], a.w[2]) > budget) continue;
             const Cand c{(double)(tv + tc) / (tv * tc) - 1e-3 * tv * tc, tv, tc};
             int pos = nbest < 64 ? nbest++ : 63;
             if (pos == 63 && c.cost >= best[63].cost) continue;
@@ -469,16 +533,14 @@ static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int 
     return n;
 }
 
-static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
-                         const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                         cudaStream_t st, int tv_req, int tc_req) {
+static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const Axes &a,
+                               const int *gmap, int ng, C *Ap, C *Bp, C *Mp, long ldm,
+                               cudaStream_t st, int tv_req, int tc_req) {
     const long P = (long)nv * nc;
-    if (P == 0) return cudaSuccess;
-    const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
-    C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
     int TV = 0, TC = 0;
     if (use_plane_kernels(a)) {
-        if (tv_req > 0 && tc_req > 0 && plane_smem(tv_req, tc_req, a.n[1], a.w[2]) <= kPlaneSmemMax) {
+        const size_t budget = plane_smem(1, 1, a.n[1], a.w[2]) <= kPlaneSmemMax ? kPlaneSmemMax : kPlaneSmemLarge;
+        if (tv_req > 0 && tc_req > 0 && plane_smem(tv_req, tc_req, a.n[1], a.w[2]) <= budget) {
             TV = tv_req < nv ? tv_req : nv;
             TC = tc_req < nc ? tc_req : nc;
         } else {
@@ -509,6 +571,12 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
     const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
     const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
     cudaError_t e = cudaSuccess;
+    if (mtxel_scatter_mode(a, sizeof(C))) {
+        const long lines = (long)a.w[1] * a.w[2];
+        BGW_FOR_EACH_LEN(a.n[0], (k2_xpass_scatter<N><<<blocks_for(P * lines), kLineThreads, 0, st>>>(
+                                     Bp, P, a.w[0], a.w[1], a.w[2], a.s[0], gmap + ng, scale, Mp, ldm)));
+        return cudaGetLastError();
+    }
     BGW_FOR_EACH_LEN(a.n[0], {
         if (smem > 48 * 1024) {
             e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -519,6 +587,23 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
             Bp, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
     });
     return cudaGetLastError();
+}
+
+static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
+                         const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
+                         cudaStream_t st, int tv_req, int tc_req) {
+    if ((long)nv * nc == 0) return cudaSuccess;
+    const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
+    C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
+    const long vol = (long)a.n[0] * a.n[1] * a.n[2];
+    const int VB = mtxel_v_batch(nv, nc, a, sizeof(C));
+    for (int vb0 = 0; vb0 < nv; vb0 += VB) {
+        const int nvb = nv - vb0 < VB ? nv - vb0 : VB;
+        cudaError_t e = mtxel_batch(uv + (long)vb0 * 2 * vol, uc, nvb, nc, a, gmap, ng, Ap, Bp,
+                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 #undef BGW_FOR_EACH_LEN

@@ -34,12 +34,33 @@ cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube
 // a.w = kept widths; gmap[g] = j0*w1*w2 + j1*w2 + j2 (position in the kept
 // cube); A: [P][n0][n1][w2], Bs: [P][n0][w1][w2] scratch; M row stride ldm.
 // tv, tc: pair tile of the plane-fused FP32 kernel (0 = choose automatically).
+// Pairs are processed in batches of mtxel_v_batch(...) valence bands x nc, so
+// A and Bs need room for that many pairs only.
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
                       cudaStream_t st, int tv = 0, int tc = 0);
 cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
                       cudaStream_t st, int tv = 0, int tc = 0);
+// The last forward pass gathers the kept w0*w1*w2 cube through shared memory
+// when it is small; a larger cube is written straight to M through an
+// inverse map (cube cell -> G index or -1) stored in the map buffer right
+// after the ng-entry gather map.
+inline bool mtxel_scatter_mode(const Axes &a, size_t csize) {
+    return (size_t)a.w[0] * a.w[1] * a.w[2] * csize > (size_t)64 * 1024;
+}
+
+// Valence bands per batch of the matrix-element kernels: their scratch
+// (A + Bs per pair) stays under 1 GiB.
+inline int mtxel_v_batch(int nv, int nc, const Axes &a, size_t csize) {
+    const size_t per_pair =
+        csize * ((size_t)a.n[0] * a.n[1] * a.w[2] + (size_t)a.n[0] * a.w[1] * a.w[2]);
+    const size_t cap = (size_t)1 << 30;
+    size_t vb = cap / (per_pair * (size_t)(nc > 0 ? nc : 1) + 1);
+    if (vb < 1) vb = 1;
+    return (int)(vb < (size_t)nv ? vb : (size_t)nv);
+}
+
 // Candidate pair tiles (tv, tc) of the plane-fused FP32 kernel for this shape,
 // best first by the staging heuristic; returns how many were written.
 int plane_tile_candidates(int nv, int nc, const Axes &a, int *tv, int *tc, int max);

@@ -26,6 +26,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[BGW_NOALLOC_SCR
 
 constexpr int kMaxDevices = 128;
 constexpr int kMaxNg = 65536;
+constexpr int kMaxCube = 64 * 64 * 64;
 
 struct DeviceSetup {
     bool done = false;
@@ -37,7 +38,7 @@ DeviceSetup g_setup[kMaxDevices];
 // Host staging of the sphere map (a static array, not heap or thread-local
 // storage); g_map_mu serialises its use across host threads.
 std::mutex g_map_mu;
-int g_gmap_host[kMaxNg];
+int g_gmap_host[kMaxNg + kMaxCube];
 
 bool supported_len(int n) {
     static const int lens[] = {16, 18, 20, 24, 27, 30, 32, 36, 40, 48, 64};
@@ -112,12 +113,14 @@ extern "C" bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv,
         ax.w[a] = std::min(emax[a] - emin[a] + 1, fft[a]);
         ax.s[a] = pmod((long)emin[a] + G0[a], fft[a]);
     }
-    if ((size_t)ax.w[0] * ax.w[1] * ax.w[2] * 16 > 200 * 1024)
-        return fail(BGW_E_ARG, "mtxel_noalloc: dielectric sphere too wide for one block");
+    const long cube = (long)ax.w[0] * ax.w[1] * ax.w[2];
+    const bool scatter = bgw::mtxel_scatter_mode(ax, 16);
+    const long nmap = ng + (scatter ? cube : 0);
     const long P = (long)nv * nc;
-    const size_t gbytes = round_up(sizeof(int) * (size_t)ng);
-    const size_t abytes = round_up((size_t)P * fft[0] * fft[1] * ax.w[2] * 16);
-    const size_t bbytes = round_up((size_t)P * fft[0] * ax.w[1] * ax.w[2] * 16);
+    const long PB = (long)bgw::mtxel_v_batch(nv, nc, ax, 16) * nc;   // pairs per kernel batch
+    const size_t gbytes = round_up(sizeof(int) * (size_t)nmap);
+    const size_t abytes = round_up((size_t)PB * fft[0] * fft[1] * ax.w[2] * 16);
+    const size_t bbytes = round_up((size_t)PB * fft[0] * ax.w[1] * ax.w[2] * 16);
     const size_t need = gbytes + abytes + bbytes;
     if (need > (size_t)BGW_NOALLOC_SCRATCH_BYTES)
         return fail(BGW_E_ARG, "mtxel_noalloc: " + std::to_string(P) + " pairs need " +
@@ -132,16 +135,23 @@ extern "C" bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv,
     const bgw_status s = setup_device(dev, &scratch, err);
     if (s != BGW_OK) return fail(s, err);
     std::lock_guard<std::mutex> lk(g_map_mu);
+    for (long i = ng; i < nmap; ++i) g_gmap_host[i] = -1;
     for (long g = 0; g < ng; ++g) {
         int j[3];
         for (int a = 0; a < 3; ++a) j[a] = pmod((long)gvec[3 * g + a] - emin[a], fft[a]);
-        g_gmap_host[g] = (j[0] * ax.w[1] + j[1]) * ax.w[2] + j[2];
+        const int cell = (j[0] * ax.w[1] + j[1]) * ax.w[2] + j[2];
+        g_gmap_host[g] = cell;
+        if (scatter) {
+            if (g_gmap_host[ng + cell] >= 0)
+                return fail(BGW_E_ARG, "mtxel_noalloc: aliased dielectric sphere too wide for the gather");
+            g_gmap_host[ng + cell] = (int)g;
+        }
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(scratch);
     int *gmap = reinterpret_cast<int *>(base);
     // pageable source: the copy has read g_gmap_host when this call returns
-    e = cudaMemcpyAsync(gmap, g_gmap_host, sizeof(int) * (size_t)ng, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(gmap, g_gmap_host, sizeof(int) * (size_t)nmap, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, ng, base + gbytes, base + gbytes + abytes, M_dev,
                            ng, st);

@@ -36,7 +36,8 @@ import numpy as np
 __all__ = [
     "Problem", "fcc_cell", "rhombohedral_cell", "reciprocal", "kgrid_points",
     "wfn_sphere", "eps_sphere", "spinor_coefficients", "band_energies",
-    "make_problem", "make_batched_problem", "CONFIGS", "spinless_to_spinor", "rotate_spin",
+    "make_problem", "make_batched_problem", "make_bi2se3_problem", "spinor_coefficients_device",
+    "CONFIGS", "spinless_to_spinor", "rotate_spin",
     "plane_wave_bands",
 ]
 
@@ -71,8 +72,10 @@ def kgrid_points(n) -> np.ndarray:
 
 
 def _miller_box(bvec: np.ndarray, radius2: float, center: np.ndarray) -> np.ndarray:
-    bmin = np.min(np.linalg.norm(bvec, axis=1))
-    r = int(np.ceil(np.sqrt(radius2) / bmin + np.abs(center).max())) + 2
+    """All Miller triples that can lie within |center + h| B < sqrt(radius2):
+    h_i = (center + h).a_i / 2pi - center_i, so |h_i| <= r |a_i| / 2pi + |center_i|."""
+    alen = np.linalg.norm(2.0 * np.pi * np.linalg.inv(np.asarray(bvec, float)).T, axis=1)
+    r = int(np.ceil(np.sqrt(radius2) * alen.max() / (2.0 * np.pi) + np.abs(center).max())) + 1
     rng = range(-r, r + 1)
     return np.array(list(itertools.product(rng, rng, rng)), dtype=np.int64)
 
@@ -227,6 +230,43 @@ def make_batched_problem(config_id: int = 3, a: float = 11.53, box=(32, 32, 32),
     qpts = kgrid_points(kgrid)[1:nq + 1]
     p.qs = [(q, eps_sphere(bvec, q, int(ng)), int(nc)) for q, ng, nc in zip(qpts, ngs, ncs)]
     return p
+
+
+BOHR_PER_ANGSTROM = 1.0 / 0.529177210903
+
+
+def spinor_coefficients_device(config_id: int, ik: int, ngw: int, nbands: int, device="cuda"):
+    """Orthonormal spinor coefficients generated on a CUDA device with torch
+    (complex128 [nbands][2][ngw]); same recipe as spinor_coefficients, for
+    sizes whose host QR would take too long.  Seeded per (config, k)."""
+    import torch
+    seed = int(np.random.SeedSequence([int(config_id), int(ik), 0]).generate_state(1)[0])
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    z = torch.randn((2 * ngw, nbands), dtype=torch.complex128, generator=g, device=device)
+    q, _ = torch.linalg.qr(z, mode="reduced")
+    return q.T.reshape(nbands, 2, ngw).contiguous()
+
+
+def make_bi2se3_problem(config_id: int = 4, box=(64, 64, 64), ecut_wfn: float = 67.9, ng: int = 2000,
+                        kgrid=(6, 6, 6), nv: int = 48, nc: int = 1000, q=(1 / 6, 0, 0),
+                        nfreq: int = 8, device="cuda") -> Problem:
+    """Bi2Se3-like rhombohedral cell (hexagonal a = 4.143 A, c = 28.636 A),
+    64^3 box, ~9000 plane waves per spinor component, N_G = 2000; the
+    coefficients are generated on the device (torch tensors)."""
+    avec = rhombohedral_cell(4.143 * BOHR_PER_ANGSTROM, 28.636 * BOHR_PER_ANGSTROM)
+    bvec = reciprocal(avec)
+    kc = kgrid_points(kgrid)
+    gvec, coeff, energy = [], [], []
+    for ik in range(len(kc)):
+        gk = wfn_sphere(bvec, kc[ik], ecut_wfn)
+        gvec.append(gk)
+        coeff.append(spinor_coefficients_device(config_id, ik, len(gk), nv + nc, device))
+        energy.append(band_energies(config_id, ik, nv, nc))
+    qv = np.asarray(q, float)
+    freq = np.linspace(0.0, 40.0, nfreq) if nfreq > 1 else np.zeros(1)
+    return Problem("bi2se3", avec, tuple(box), tuple(kgrid), kc, nv, nc, gvec, coeff, energy,
+                   [(qv, eps_sphere(bvec, qv, ng), nc)], freq, "mixed")
 
 
 def make_problem(name: str, **overrides) -> Problem:
