@@ -216,4 +216,74 @@ __device__ __forceinline__ void fft_line(cpx<T> (&a)[N]) {
     Fft<T, S, N, N>::run(a);
 }
 
+// ------------------------------------------- four lanes per line (N >= 32) --
+// Lanes t = 0..3 of an aligned group of four transform one line of length
+// N = 4M together (Cooley-Tukey with the stride-4 split):
+//   lane t enters with a[m] = x[4m + t], m < M;
+//   Y_t[k2] = sum_m x[4m + t] w_M^{m k2}           (M-point DFT in registers)
+//   Y_t[k2] *= w_N^{t k2}                          (twiddle)
+//   X[k2 + M k1] = sum_t' Y_t'[k2] w_4^{t' k1}    (4-point DFT across lanes)
+// and leaves with out[k1][j] = X[t Q + j + M k1], Q = M/4, j < Q.
+// Values are picked with selects on t and exchanged with __shfl_xor, so no
+// register array is indexed at run time.
+template <typename T>
+__device__ __forceinline__ cpx<T> sel4(int i, cpx<T> v0, cpx<T> v1, cpx<T> v2, cpx<T> v3) {
+    cpx<T> r = v0;
+    r = (i == 1) ? v1 : r;
+    r = (i == 2) ? v2 : r;
+    r = (i == 3) ? v3 : r;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> shfl_xor_c(cpx<T> v, int d) {
+    return {__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)};
+}
+
+template <typename T, int S, int N>
+__device__ __forceinline__ void fft_line_coop4(cpx<T> (&a)[N / 4], int t, cpx<T> (&out)[4][N / 16]) {
+    static_assert(fft_len_supported(N) && N % 16 == 0, "four-lane FFT needs N a multiple of 16");
+    constexpr int M = N / 4;
+    constexpr int Q = M / 4;
+    Fft<T, S, M, N>::run(a);
+    // twiddle w_N^{t k2}: pick among the warp-uniform roots of exponents k2, 2k2, 3k2
+#pragma unroll
+    for (int k2 = 1; k2 < M; ++k2) {
+        cpx<T> w1 = Tw<T>::at(tw_offset(N) + (k2 % N));
+        cpx<T> w2 = Tw<T>::at(tw_offset(N) + ((2 * k2) % N));
+        cpx<T> w3 = Tw<T>::at(tw_offset(N) + ((3 * k2) % N));
+        if (S > 0) {
+            w1.y = -w1.y;
+            w2.y = -w2.y;
+            w3.y = -w3.y;
+        }
+        const cpx<T> w = sel4<T>(t, cpx<T>{T(1), T(0)}, w1, w2, w3);
+        a[k2] = cmul(a[k2], w);
+    }
+    // lane t gathers Y_t'[t Q + j] from every lane t'
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        cpx<T> y[4];
+        // own value
+        y[0] = sel4<T>(t, a[j], a[Q + j], a[2 * Q + j], a[3 * Q + j]);
+#pragma unroll
+        for (int d = 1; d < 4; ++d) {
+            // send the entry of the partner's block, receive the partner's entry of ours
+            const int pb = t ^ d;
+            const cpx<T> send = sel4<T>(pb, a[j], a[Q + j], a[2 * Q + j], a[3 * Q + j]);
+            y[d] = shfl_xor_c(send, d);
+        }
+        // y[d] came from lane t ^ d: order by source lane
+        cpx<T> z[4];
+#pragma unroll
+        for (int tp = 0; tp < 4; ++tp) {
+            const int d = t ^ tp;
+            z[tp] = sel4<T>(d, y[0], y[1], y[2], y[3]);
+        }
+        dft_small<T, S, 4, N>(z);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) out[k1][j] = z[k1];
+    }
+}
+
 }  // namespace bgw

@@ -243,6 +243,101 @@ k2_xpass_scatter(const C *__restrict__ Bs, long P, int w0, int w1, int w2, int s
     }
 }
 
+// ------------------------------------- four lanes per line (N >= 48) --
+// Long lines do not fit one thread's registers; four lanes share each line
+// (fft_line_coop4).  Whole quads of lanes stay alive through the shuffles:
+// a quad past the end works on line 0 and stores nothing.
+constexpr int kCoopMinN = 48;
+
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k2_zpass_c4(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, long plane, int w2,
+            int s2, C *__restrict__ A) {
+    constexpr int M = N / 4, Q = M / 4;
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (int)(tid & 3);
+    long line = tid >> 2;
+    const bool valid = line < P * plane;
+    if (!valid) line = 0;
+    const long xy = line % plane;
+    const long p = line / plane;
+    const long v = p / nc, c = p % nc;
+    const long vol = plane * N;
+    const C *v0 = Uv + (2 * v) * vol + xy * N;
+    const C *c0 = Uc + (2 * c) * vol + xy * N;
+    C a[M], out[4][Q];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int z = 4 * m + t;
+        a[m] = rho2(v0[z], c0[z], v0[vol + z], c0[vol + z]);
+    }
+    fft_line_coop4<T, -1, N>(a, t, out);
+    if (!valid) return;
+    const int ns = N - s2;
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int jj = rot<N>(t * Q + j + M * k1, ns);
+            if (jj < w2) A[line * w2 + jj] = out[k1][j];
+        }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k2_ypass_c4(const C *__restrict__ A, long npx, int w1, int w2, int s1, C *__restrict__ Bs) {
+    constexpr int M = N / 4, Q = M / 4;
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (int)(tid & 3);
+    long line = tid >> 2;
+    const bool valid = line < npx * w2;
+    if (!valid) line = 0;
+    const long jz = line % w2, px = line / w2;
+    C a[M], out[4][Q];
+#pragma unroll
+    for (int m = 0; m < M; ++m) a[m] = A[(px * N + 4 * m + t) * w2 + jz];
+    fft_line_coop4<T, -1, N>(a, t, out);
+    if (!valid) return;
+    const int ns = N - s1;
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int jj = rot<N>(t * Q + j + M * k1, ns);
+            if (jj < w1) Bs[(px * w1 + jj) * w2 + jz] = out[k1][j];
+        }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kLineThreads)
+k2_xpass_scatter_c4(const C *__restrict__ Bs, long P, int w0, int w1, int w2, int s0,
+                    const int *__restrict__ imap, T scale, C *__restrict__ M, long ldm) {
+    constexpr int MM = N / 4, Q = MM / 4;
+    const long lines = (long)w1 * w2;
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (int)(tid & 3);
+    long line = tid >> 2;
+    const bool valid = line < P * lines;
+    if (!valid) line = 0;
+    const long l = line % lines, p = line / lines;
+    C a[MM], out[4][Q];
+#pragma unroll
+    for (int m = 0; m < MM; ++m) a[m] = Bs[(p * N + 4 * m + t) * lines + l];
+    fft_line_coop4<T, -1, N>(a, t, out);
+    if (!valid) return;
+    const int ns = N - s0;
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int jj = rot<N>(t * Q + j + MM * k1, ns);
+            if (jj < w0) {
+                const int g = __ldg(imap + jj * lines + l);
+                if (g >= 0) M[p * ldm + g] = C{out[k1][j].x * scale, out[k1][j].y * scale};
+            }
+        }
+}
+
 // ----------------------------------------- plane-fused passes (FP32) --
 // Band planes staged through shared memory with batched loads (kStageU in
 // flight per thread); every line is then read from a padded shared row.
@@ -449,7 +544,23 @@ static inline unsigned blocks_for(long n) { return (unsigned)((n + kLineThreads 
 static constexpr size_t kPlaneSmemMax = 110 * 1024;   // two blocks per SM
 static constexpr size_t kPlaneSmemLarge = 200 * 1024;  // one block per SM (large boxes)
 
-static bool use_plane_kernels(const Axes &a) { return sizeof(T) == 4 && a.n[1] == a.n[2]; }
+static bool use_plane_kernels(const Axes &a) {
+    return sizeof(T) == 4 && a.n[1] == a.n[2] && a.n[1] < kCoopMinN;
+}
+
+static bool use_coop(const Axes &a) {
+    return a.n[0] >= kCoopMinN && a.n[1] >= kCoopMinN && a.n[2] >= kCoopMinN && a.n[0] % 16 == 0 &&
+           a.n[1] % 16 == 0 && a.n[2] % 16 == 0;
+}
+
+static inline unsigned quads_for(long lines) { return (unsigned)((4 * lines + kLineThreads - 1) / kLineThreads); }
+
+#define BGW_FOR_EACH_COOP_LEN(n, ...)                                                 \
+    switch (n) {                                                                      \
+        case 48: { constexpr int N = 48; __VA_ARGS__; } break;                        \
+        case 64: { constexpr int N = 64; __VA_ARGS__; } break;                        \
+        default: return cudaErrorInvalidValue;                                        \
+    }
 
 static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *cube_map,
                                const Axes &a, void *S, void *R, void *U, cudaStream_t st) {
@@ -548,6 +659,19 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         }
     }
     const size_t psmem = TV > 0 ? plane_smem(TV, TC, a.n[1], a.w[2]) : 0;
+    if (use_coop(a)) {
+        const long plane = (long)a.n[0] * a.n[1];
+        BGW_FOR_EACH_COOP_LEN(a.n[2], (k2_zpass_c4<N><<<quads_for(P * plane), kLineThreads, 0, st>>>(
+                                          uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
+        const long npx = P * a.n[0];
+        BGW_FOR_EACH_COOP_LEN(a.n[1], (k2_ypass_c4<N><<<quads_for(npx * a.w[2]), kLineThreads, 0, st>>>(
+                                          Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
+        const long lines = (long)a.w[1] * a.w[2];
+        const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
+        BGW_FOR_EACH_COOP_LEN(a.n[0], (k2_xpass_scatter_c4<N><<<quads_for(P * lines), kLineThreads, 0, st>>>(
+                                          Bp, P, a.w[0], a.w[1], a.w[2], a.s[0], gmap + ng, scale, Mp, ldm)));
+        return cudaGetLastError();
+    }
     if (TV > 0) {
         dim3 grid((unsigned)a.n[0], (unsigned)((nv + TV - 1) / TV), (unsigned)((nc + TC - 1) / TC));
         cudaError_t e = cudaSuccess;
@@ -607,6 +731,7 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
 }
 
 #undef BGW_FOR_EACH_LEN
+#undef BGW_FOR_EACH_COOP_LEN
 
 }  // namespace BGW_SUFFIX
 }  // namespace bgw

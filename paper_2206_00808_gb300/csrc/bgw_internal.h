@@ -47,7 +47,9 @@ cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes
 // inverse map (cube cell -> G index or -1) stored in the map buffer right
 // after the ng-entry gather map.
 inline bool mtxel_scatter_mode(const Axes &a, size_t csize) {
-    return (size_t)a.w[0] * a.w[1] * a.w[2] * csize > (size_t)64 * 1024;
+    const bool long_lines = a.n[0] >= 48 && a.n[1] >= 48 && a.n[2] >= 48 && a.n[0] % 16 == 0 &&
+                            a.n[1] % 16 == 0 && a.n[2] % 16 == 0;   // four-lane FFT kernels
+    return long_lines || (size_t)a.w[0] * a.w[1] * a.w[2] * csize > (size_t)64 * 1024;
 }
 
 // Valence bands per batch of the matrix-element kernels: their scratch
