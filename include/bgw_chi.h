@@ -49,6 +49,8 @@
 #ifndef BGW_CHI_H
 #define BGW_CHI_H
 
+#include <stddef.h>
+
 #if defined(__GNUC__)
 #define BGW_API __attribute__((visibility("default")))
 #else
@@ -165,6 +167,43 @@ BGW_API bgw_status bgw_chi0_accumulate(bgw_ctx ctx, int nq, const bgw_q *qs, int
 BGW_API bgw_status bgw_chi0_finalize(bgw_ctx ctx, int iq, void *chi0, int on_device);
 
 /*
+ * Progress, checkpoint and resume of a running sum.  The k sum of the
+ * polarizability (the 1/N_k sum over k of Sec. II's P formula) is linear, so
+ * the state between two k-blocks is the FP64 accumulators alone; the paper
+ * has no counterpart of these calls (they serve long runs that must survive
+ * a restart).
+ *
+ * bgw_chi0_progress: k_counts[nk] (host, caller-owned) receives, for every
+ *   k, how many accumulate calls since the q-set was installed (first
+ *   accumulate after a reset, or a resume) summed that k.  Calls captured in
+ *   a graph count once, at capture; replays are not counted.
+ *   BGW_E_STATE without a running sum.
+ * bgw_chi0_checkpoint_bytes: *bytes = size of a checkpoint of the running
+ *   sum (56-byte header, 4 bytes per k padded to 16, then per q-point 16 + 16 N_w N_G^2).
+ * bgw_chi0_checkpoint: writes the running sum into the host buffer buf
+ *   (caller-owned, `bytes` long): header (format tag, version, precision, a
+ *   64-bit FNV-1a hash of the box, k list, band layout, precision, q-set and
+ *   frequencies), the k counts, then each q-point's FP64 accumulators as
+ *   complex128 [N_w][N_G][N_G] (lower block triangle meaningful).  Waits for
+ *   the context stream.  BGW_E_TIMEOUT if a device-side wait of the mixed
+ *   contraction gave up (the sum is invalid); BGW_E_STATE during graph
+ *   capture or without a running sum; BGW_E_ARG if buf is too small.
+ * bgw_chi0_resume: starts a running sum from a checkpoint: the q-set and
+ *   frequencies (as for accumulate) must be those the checkpoint was taken
+ *   with, on a context created with the same box, k list, bands and
+ *   precision (BGW_E_STATE otherwise).  Replaces any running sum; the k
+ *   counts are restored; later accumulate calls add to it.  Returns when the
+ *   buffer has been read.  Resuming and accumulating the remaining k-blocks
+ *   with the same k-chunk gives bitwise the same chi0 as one uninterrupted
+ *   run over the same blocks.
+ */
+BGW_API bgw_status bgw_chi0_progress(bgw_ctx ctx, int *k_counts);
+BGW_API bgw_status bgw_chi0_checkpoint_bytes(bgw_ctx ctx, size_t *bytes);
+BGW_API bgw_status bgw_chi0_checkpoint(bgw_ctx ctx, void *buf, size_t bytes);
+BGW_API bgw_status bgw_chi0_resume(bgw_ctx ctx, int nq, const bgw_q *qs, int nfreq, const double *freq_eV,
+                                   const void *buf, size_t bytes);
+
+/*
  * CUDA-graph capture of a sequence of calls on this context (for repeated
  * identical steps, e.g. serving the same workload).  bgw_graph_begin starts
  * capturing the context stream (which must not be the legacy default
@@ -202,8 +241,21 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        caller's coefficient buffer instead of a copy: keep it
  *                        alive and unchanged until the k-point is uploaded
  *                        again or the context is destroyed.
+ *   BGW_OPT_TEST_FAIL_ALLOC for failure-handling tests only: when n > 0, the
+ *                        n-th device allocation made by the library from now on
+ *                        (by any context of the process) fails as if the device
+ *                        were out of memory, so the call needing it returns
+ *                        BGW_E_NOMEM; 0 switches it off.  The environment
+ *                        variable BGW_FAULT=oom@n, read by bgw_create, does the
+ *                        same.
+ *   BGW_OPT_TEST_DROP_LOAD  for failure-handling tests only: the next mixed
+ *                        contractions lose one operand load on purpose, so the
+ *                        kernel's bounded waits (about 2 s) expire, it frees its
+ *                        resources and records an error that a host finalize
+ *                        reports as BGW_E_TIMEOUT.  No fault, trap or hang.
  */
-enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4 };
+enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
+       BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

@@ -27,8 +27,11 @@ PRECISIONS = {"fp64": BGW_FP64, "mixed": BGW_MIXED_BF16X3}
 EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
             "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
             "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune",
-            "bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch", "bgw_destroy", "bgw_last_error"]
+            "bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch", "bgw_chi0_progress",
+            "bgw_chi0_checkpoint_bytes", "bgw_chi0_checkpoint", "bgw_chi0_resume", "bgw_destroy",
+            "bgw_last_error"]
 BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C, BGW_OPT_GRID_SLOTS = 1, 2, 3, 4
+BGW_OPT_TEST_DROP_LOAD, BGW_OPT_TEST_FAIL_ALLOC = 5, 6
 STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split"]
 
 
@@ -55,11 +58,16 @@ _lib.bgw_autotune.argtypes = [_P, _I, ctypes.POINTER(bgw_q), _I, _P, _I, _I, cty
 for _f in ["bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch"]:
     getattr(_lib, _f).argtypes = [_P]
     getattr(_lib, _f).restype = ctypes.c_int
+_lib.bgw_chi0_progress.argtypes = [_P, _P]
+_lib.bgw_chi0_checkpoint_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+_lib.bgw_chi0_checkpoint.argtypes = [_P, _P, ctypes.c_size_t]
+_lib.bgw_chi0_resume.argtypes = [_P, _I, ctypes.POINTER(bgw_q), _I, _P, _P, ctypes.c_size_t]
 _lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
 _lib.bgw_last_error.argtypes, _lib.bgw_last_error.restype = [_P], ctypes.c_char_p
 for _f in ["bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
            "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
-           "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune"]:
+           "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune",
+           "bgw_chi0_progress", "bgw_chi0_checkpoint_bytes", "bgw_chi0_checkpoint", "bgw_chi0_resume"]:
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -170,6 +178,36 @@ def bgw_chi0_finalize(ctx, iq: int, out) -> int:
     return _check(_lib.bgw_chi0_finalize(ctx, iq, p, d), ctx)
 
 
+def bgw_chi0_progress(ctx, nk: int) -> np.ndarray:
+    """Per-k count of accumulate calls in the running sum."""
+    out = np.zeros(nk, dtype=np.int32)
+    _check(_lib.bgw_chi0_progress(ctx, _host_ptr(out)), ctx)
+    return out
+
+
+def bgw_chi0_checkpoint(ctx) -> bytes:
+    """The running sum as a checkpoint (bytes)."""
+    n = ctypes.c_size_t(0)
+    _check(_lib.bgw_chi0_checkpoint_bytes(ctx, ctypes.byref(n)), ctx)
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(_lib.bgw_chi0_checkpoint(ctx, _host_ptr(buf), n.value), ctx)
+    return buf.tobytes()
+
+
+def bgw_chi0_resume(ctx, qs, freq, data: bytes) -> int:
+    """Start the running sum from a checkpoint of the same problem and q-set."""
+    structs, keep = [], []
+    for q, g, nc in qs:
+        s, a = make_q(q, g, nc)
+        structs.append(s)
+        keep.append(a)
+    arr = (bgw_q * len(structs))(*structs)
+    f = np.ascontiguousarray(freq, dtype=np.float64)
+    b = np.frombuffer(data, dtype=np.uint8)
+    return _check(_lib.bgw_chi0_resume(ctx, len(structs), arr, len(f), _host_ptr(f), _host_ptr(b),
+                                       len(b)), ctx)
+
+
 def bgw_profile(ctx, enable: bool) -> int:
     return _check(_lib.bgw_profile(ctx, int(bool(enable))), ctx)
 
@@ -245,6 +283,7 @@ class Chi0Context:
 
     def __init__(self, problem, precision=None, stream=None):
         self.p = problem
+        self.stream = stream
         self.precision = precision or problem.precision
         self.ctx = bgw_create(problem.box, problem.kcrys, problem.nv, problem.nc, self.precision,
                               stream)

@@ -11,7 +11,10 @@
 //   acc[nfreq][ng][ng] (lower block triangle filled; finalize mirrors it).
 // Scratch buffers grow on demand and are reused.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 #include <utility>
 #include <cstring>
@@ -26,6 +29,19 @@
 namespace {
 
 thread_local std::string g_create_error;
+
+// Allocation-failure injection for tests: when positive, the n-th device
+// allocation from now on fails as if the device were out of memory (set by
+// BGW_OPT_TEST_FAIL_ALLOC or the environment variable BGW_FAULT=oom@n).
+std::atomic<long> g_fail_alloc{0};
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    long n = g_fail_alloc.load();
+    while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
 
 struct DevBuf {
     void *p = nullptr;
@@ -44,7 +60,7 @@ struct DevBuf {
             p = nullptr;
             cap = 0;
         }
-        cudaError_t e = cudaMalloc(&p, bytes);
+        cudaError_t e = dev_alloc(&p, bytes);
         if (e != cudaSuccess) {
             p = nullptr;
             return e;
@@ -158,6 +174,10 @@ struct bgw_ctx_s {
     int kchunk = 1;      // k-points per contraction launch
     int sm_count = 0;
     int tile_v = 0, tile_c = 0;   // pair tile of the FP32 plane kernel (0 = automatic)
+    int test_drop_load = 0;       // BGW_OPT_TEST_DROP_LOAD
+    // k-points summed into the running sum (accumulate calls made since the
+    // q-set was installed; replays of a captured graph are not counted)
+    std::vector<int> kcount;
     // stage timing (bgw_profile)
     static constexpr int kStages = 6;
     bool prof = false;
@@ -588,6 +608,7 @@ bgw_status install_qset(bgw_ctx_s *c, std::vector<QState> &fresh, int nfreq, con
     c->freq.assign(freq, freq + nfreq);
     c->nfreq = nfreq;
     c->have_qset = true;
+    c->kcount.assign(c->nk, 0);
     if (!same_content) {
         e = cudaMemcpyAsync(c->freq_dev.p, c->freq.data(), sizeof(double) * nfreq,
                             cudaMemcpyHostToDevice, c->st);
@@ -662,7 +683,7 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
             if (c->prec != BGW_FP64) {
                 const int rec = c->stage_begin(3);
                 e = bgw::mixed_gemm(group.data(), (int)group.size(), nfreq, c->sm_count, c->st,
-                                    static_cast<int *>(c->errflag.p));
+                                    static_cast<int *>(c->errflag.p), c->test_drop_load);
                 c->stage_end(rec, 1);
                 if (e != cudaSuccess) return e;
             }
@@ -670,6 +691,65 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
     }
     return e;
 }
+}  // namespace
+
+// ---- checkpoint / resume ----------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'B', 'G', 'W', 'C', 'H', 'I', '0', 'K'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t precision;
+    uint64_t hash;        // FNV-1a of the problem the sum belongs to
+    int32_t nq, nfreq, nk, box0;
+    int32_t box1, box2, nv, nc_max;
+};
+static_assert(sizeof(CkptHeader) == 56, "checkpoint header layout");
+
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    }
+    template <class T> void add(const T &v) { add(&v, sizeof(T)); }
+};
+
+// The problem a running sum belongs to: box, k list, band layout, precision,
+// q-set (q, sphere, Nc) and frequencies.
+uint64_t problem_hash(const bgw_ctx_s *c, const std::vector<QState> &qs, const std::vector<double> &freq) {
+    Fnv f;
+    f.add(c->box, sizeof(c->box));
+    f.add(c->nk);
+    f.add(c->kcrys.data(), sizeof(double) * c->kcrys.size());
+    f.add(c->nv);
+    f.add(c->nc_max);
+    f.add((int)c->prec);
+    f.add((int)qs.size());
+    for (const QState &s : qs) {
+        f.add(s.q, sizeof(s.q));
+        f.add(s.ng);
+        f.add(s.nc);
+        f.add(s.gvec.data(), sizeof(int) * s.gvec.size());
+    }
+    f.add((int)freq.size());
+    f.add(freq.data(), sizeof(double) * freq.size());
+    return f.h;
+}
+
+size_t ckpt_bytes(const bgw_ctx_s *c, const std::vector<QState> &qs, int nfreq) {
+    size_t b = sizeof(CkptHeader) + sizeof(int32_t) * (size_t)c->nk;
+    b = (b + 15) & ~(size_t)15;
+    for (const QState &s : qs) b += 16 + 16 * (size_t)nfreq * s.ng * s.ng;
+    return b;
+}
+
 }  // namespace
 
 extern "C" {
@@ -707,6 +787,10 @@ bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const double *kcry
             g_create_error = "bgw_create: non-finite k coordinate";
             return BGW_E_ARG;
         }
+    if (const char *f = std::getenv("BGW_FAULT")) {   // BGW_FAULT=oom@n: see g_fail_alloc
+        long n = 0;
+        if (std::sscanf(f, "oom@%ld", &n) == 1 && n > 0) g_fail_alloc.store(n);
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = ensure_tables(dev);
@@ -912,6 +996,7 @@ bgw_status bgw_chi0_accumulate(bgw_ctx c, int nq, const bgw_q *qs, int nfreq,
     e = run_range(c, c->qs, nfreq, static_cast<const double *>(c->freq_dev.p), k_begin, k_end, kchunk,
                   c->tile_v, c->tile_c, clean);
     if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: kernels");
+    for (int k = k_begin; k < k_end; ++k) ++c->kcount[k];
     return clean ? BGW_OK : BGW_W_ALIAS;
 }
 
@@ -951,6 +1036,112 @@ bgw_status bgw_chi0_finalize(bgw_ctx c, int iq, void *chi0, int on_device) {
     return BGW_OK;
 }
 
+// ---- checkpoint / resume (format and problem hash defined before extern "C") ----
+
+bgw_status bgw_chi0_progress(bgw_ctx c, int *k_counts) {
+    if (!c) return BGW_E_ARG;
+    c->err.clear();
+    if (!k_counts) return c->fail(BGW_E_ARG, "progress: null output");
+    if (!c->have_qset) return c->fail(BGW_E_STATE, "progress: no running sum");
+    std::copy(c->kcount.begin(), c->kcount.end(), k_counts);
+    return BGW_OK;
+}
+
+bgw_status bgw_chi0_checkpoint_bytes(bgw_ctx c, size_t *bytes) {
+    if (!c) return BGW_E_ARG;
+    c->err.clear();
+    if (!bytes) return c->fail(BGW_E_ARG, "checkpoint_bytes: null output");
+    if (!c->have_qset) return c->fail(BGW_E_STATE, "checkpoint_bytes: no running sum");
+    *bytes = ckpt_bytes(c, c->qs, c->nfreq);
+    return BGW_OK;
+}
+
+bgw_status bgw_chi0_checkpoint(bgw_ctx c, void *buf, size_t bytes) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (!buf) return c->fail(BGW_E_ARG, "checkpoint: null buffer");
+    if (!c->have_qset) return c->fail(BGW_E_STATE, "checkpoint: no running sum");
+    if (c->capturing) return c->fail(BGW_E_STATE, "checkpoint: not allowed during graph capture");
+    const size_t need = ckpt_bytes(c, c->qs, c->nfreq);
+    if (bytes < need) return c->fail(BGW_E_ARG, "checkpoint: buffer of %zu bytes, %zu needed", bytes, need);
+    char *o = static_cast<char *>(buf);
+    CkptHeader h;
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = kCkptVersion;
+    h.precision = (uint32_t)c->prec;
+    h.hash = problem_hash(c, c->qs, c->freq);
+    h.nq = (int32_t)c->qs.size();
+    h.nfreq = c->nfreq;
+    h.nk = c->nk;
+    h.box0 = c->box[0];
+    h.box1 = c->box[1];
+    h.box2 = c->box[2];
+    h.nv = c->nv;
+    h.nc_max = c->nc_max;
+    std::memcpy(o, &h, sizeof(h));
+    std::memcpy(o + sizeof(h), c->kcount.data(), sizeof(int32_t) * (size_t)c->nk);
+    size_t off = (sizeof(h) + sizeof(int32_t) * (size_t)c->nk + 15) & ~(size_t)15;
+    cudaError_t e = cudaSuccess;
+    for (const QState &s : c->qs) {
+        const int32_t hdr[4] = {s.ng, s.nc, 0, 0};
+        std::memcpy(o + off, hdr, sizeof(hdr));
+        off += 16;
+        const size_t ab = 16 * (size_t)c->nfreq * s.ng * s.ng;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(o + off, s.acc.p, ab, cudaMemcpyDeviceToHost, c->st);
+        off += ab;
+    }
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "checkpoint: copy to host");
+    if (flag != 0)
+        return c->fail(BGW_E_TIMEOUT, "checkpoint: a device-side wait gave up (code %d); the sum is invalid", flag);
+    return BGW_OK;
+}
+
+bgw_status bgw_chi0_resume(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const double *freq_eV,
+                           const void *buf, size_t bytes) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (!buf) return c->fail(BGW_E_ARG, "resume: null buffer");
+    if (c->capturing) return c->fail(BGW_E_STATE, "resume: not allowed during graph capture");
+    std::vector<QState> fresh;
+    bgw_status vst = validate_qset(c, "resume", nq, qs, nfreq, freq_eV, 0, 0, fresh);
+    if (vst != BGW_OK) return vst;
+    const size_t need = ckpt_bytes(c, fresh, nfreq);
+    const char *in = static_cast<const char *>(buf);
+    CkptHeader h;
+    if (bytes < sizeof(h)) return c->fail(BGW_E_ARG, "resume: buffer too small for a checkpoint");
+    std::memcpy(&h, in, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion)
+        return c->fail(BGW_E_ARG, "resume: not a checkpoint of this format");
+    std::vector<double> fv(freq_eV, freq_eV + nfreq);
+    if (h.hash != problem_hash(c, fresh, fv) || h.nq != nq || h.nfreq != nfreq || h.nk != c->nk)
+        return c->fail(BGW_E_STATE, "resume: the checkpoint belongs to another problem or q-set");
+    if (bytes < need) return c->fail(BGW_E_ARG, "resume: buffer of %zu bytes, %zu needed", bytes, need);
+    c->have_qset = false;
+    bgw_status st = install_qset(c, fresh, nfreq, freq_eV);   // zeroes the accumulators on the stream
+    if (st != BGW_OK) return st;
+    std::memcpy(c->kcount.data(), in + sizeof(h), sizeof(int32_t) * (size_t)c->nk);
+    size_t off = (sizeof(h) + sizeof(int32_t) * (size_t)c->nk + 15) & ~(size_t)15;
+    cudaError_t e = cudaSuccess;
+    for (QState &s : c->qs) {
+        off += 16;
+        const size_t ab = 16 * (size_t)nfreq * s.ng * s.ng;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.acc.p, in + off, ab, cudaMemcpyHostToDevice, c->st);
+        off += ab;
+    }
+    // pageable source: wait so the caller may free or reuse the buffer at once
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        c->have_qset = false;
+        return c->cuda_fail(e, "resume: copy to device");
+    }
+    return BGW_OK;
+}
+
 bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
     if (!c) return BGW_E_ARG;
     c->err.clear();
@@ -963,6 +1154,13 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
         case BGW_OPT_PAIR_TILE_C:
             if (value < 0 || value > 16) return c->fail(BGW_E_ARG, "set_option: pair tile must be 0..16");
             (option == BGW_OPT_PAIR_TILE_V ? c->tile_v : c->tile_c) = (int)value;
+            return BGW_OK;
+        case BGW_OPT_TEST_DROP_LOAD:
+            c->test_drop_load = value != 0;
+            return BGW_OK;
+        case BGW_OPT_TEST_FAIL_ALLOC:
+            if (value < 0) return c->fail(BGW_E_ARG, "set_option: allocation count must be >= 0");
+            g_fail_alloc.store(value);
             return BGW_OK;
         case BGW_OPT_GRID_SLOTS:
             if (c->nslots > 0) return c->fail(BGW_E_STATE, "set_option: grid slots are fixed at the first upload");
@@ -982,6 +1180,8 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_PAIR_TILE_V: *value = c->tile_v; return BGW_OK;
         case BGW_OPT_PAIR_TILE_C: *value = c->tile_c; return BGW_OK;
         case BGW_OPT_GRID_SLOTS: *value = c->nslots > 0 ? c->nslots : c->grid_slots_opt; return BGW_OK;
+        case BGW_OPT_TEST_DROP_LOAD: *value = c->test_drop_load; return BGW_OK;
+        case BGW_OPT_TEST_FAIL_ALLOC: *value = g_fail_alloc.load(); return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }

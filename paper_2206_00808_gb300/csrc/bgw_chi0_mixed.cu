@@ -48,7 +48,8 @@ constexpr int kTileBytes = kTileM * kBlockK * 2;                 // 16 KB per op
 constexpr int kStageBytes = 4 * kTileBytes;                      // A_hi, A_lo, B_hi, B_lo
 constexpr int kAccCols = 4 * kTileN;                             // 3 hi.hi + 1 cross accumulator
 constexpr int kMaxGroup = 48;                                    // q-points per grouped launch
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kSpinLimit = 1u << 26;          // backstop; the time limit ends waits first
+constexpr uint64_t kWaitNs = 2000000000ull;          // a device-side wait gives up after ~2 s
 constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
 
 // ------------------------------------------------------------ split kernel --
@@ -59,19 +60,21 @@ __global__ void __launch_bounds__(256)
 k5_split(const float2 *__restrict__ M, int P, int ng, const double *__restrict__ w, int R, int Kp,
          __nv_bfloat16 *__restrict__ X) {
     __shared__ float2 tile[kSplitTile][kSplitTile + 1];   // [p][g]
+    __shared__ float wt[kSplitTile];                     // this block's pair weights in FP32
     const int g0 = blockIdx.x * kSplitTile;   // complex column block (rows 2g, 2g+1)
     const int p0 = blockIdx.y * kSplitTile;
     const int plane = blockIdx.z;             // 0 = A, 1 + j = B_j
     const int tx = threadIdx.x % kSplitTile, ty = threadIdx.x / kSplitTile;   // 32 x 8
+    // one FP64 -> FP32 conversion per pair (the FP64 unit is slow on this part)
+    if (threadIdx.x < kSplitTile)
+        wt[tx] = (plane > 0 && p0 + tx < P) ? (float)w[(long)(plane - 1) * P + p0 + tx] : 1.0f;
+    __syncthreads();
     for (int i = ty; i < kSplitTile; i += 8) {
         const int p = p0 + i, g = g0 + tx;
         float2 v = make_float2(0.f, 0.f);
         if (p < P && g < ng) v = M[(long)p * ng + g];
-        if (plane > 0 && p < P) {
-            const float s = (float)w[(long)(plane - 1) * P + p];
-            v.x *= s;
-            v.y *= s;
-        }
+        v.x *= wt[i];
+        v.y *= wt[i];
         tile[i][tx] = v;
     }
     __syncthreads();
@@ -123,11 +126,20 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false after kSpinLimit polls.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false once ~kWaitNs of wall time (or kSpinLimit polls) pass.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; i < kSpinLimit; ++i) {
         if (mbar_try(bar, parity)) return true;
         if (i > 32) __nanosleep(64);
+        if ((i & 255) == 0 && global_ns() - t0 > kWaitNs) return false;
     }
     return false;
 }
@@ -219,6 +231,7 @@ struct GroupParams {
     int ng[kMaxGroup];
     int first[kMaxGroup + 1];     // first work item of each q-point
     int nq, nfreq;
+    int drop_first_load;          // test hook: block 0 never issues its first stage
 };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -289,7 +302,7 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
     if (warp == 4) {
         if (lane == 0) {
             // TMA producer; planes: 0 A_hi, 1 A_lo, 2 + 2j B_j hi, 3 + 2j B_j lo
-            long pit = 0, issued_from = 0;
+            long pit = 0, issued_from = 0, dropped = -1;
             for (int item = blockIdx.x; item < total; item += gridDim.x) {
                 const Item w = decode(gp, item);
                 const CUtensorMap *map = &gp.map[w.q];
@@ -304,6 +317,10 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
                         break;
                     }
                     if (*(volatile int *)&abort_flag) break;
+                    if (gp.drop_first_load && blockIdx.x == 0 && pit == 0) {   // test hook
+                        dropped = pit;
+                        continue;
+                    }
                     const uint32_t st0 = ring + s * kStageBytes;
                     const uint32_t fb = smem_u32(&full_bar[s]);
                     const int x = it * kBlockK;
@@ -318,6 +335,7 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
             // every issued load must land before the CTA can exit
             issued_from = pit > kStages ? pit - kStages : 0;
             for (long q = issued_from; q < pit; ++q) {
+                if (q == dropped) continue;
                 if (!mbar_wait(smem_u32(&full_bar[q % kStages]), (uint32_t)((q / kStages) & 1))) {
                     atomicExch(err, kErrDrain);
                     break;
@@ -524,7 +542,8 @@ cudaError_t mixed_split(const void *M, int P, int ng, const double *w, int nfreq
 
 int mixed_max_group() { return kMaxGroup; }
 
-cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaStream_t st, int *err) {
+cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaStream_t st, int *err,
+                       int drop_first_load) {
     if (nq < 1 || nq > kMaxGroup) return cudaErrorInvalidValue;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
@@ -532,6 +551,7 @@ cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaSt
     memset(&gp, 0, sizeof gp);
     gp.nq = nq;
     gp.nfreq = nfreq;
+    gp.drop_first_load = drop_first_load;
     int items = 0;
     for (int i = 0; i < nq; ++i) {
         gp.first[i] = items;

@@ -31,6 +31,9 @@ int mixed_max_group();
 // cores, in ONE persistent launch of at most sm_count blocks.  A device-side
 // wait that gives up writes a non-zero code to the device int *err (the host
 // reports BGW_E_TIMEOUT when it reads it back).
-cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaStream_t st, int *err);
+// drop_first_load (tests only): block 0 skips its first TMA stage so the
+// consumers' bounded waits expire and the error path runs.
+cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaStream_t st, int *err,
+                       int drop_first_load = 0);
 
 }  // namespace bgw
