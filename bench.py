@@ -49,6 +49,10 @@ METRIC = "spinor chi0 q-points/s and TFLOP/s, FP64 vs mixed at ≤2e-5 rel. Frob
 # i.e. 2 DFMA per clock per SM.  Peak = 152 * 2 * 2 * 2.07e9.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
+# cuBLAS DGEMM 8192^3 through torch.matmul on this GPU type
+# (profiles/alu_peaks_gb300.md; `bench.py --alu-peaks` measures it again).
+MEASURED_DGEMM_TFLOPS = 1.101
+
 # DRAM bytes per launch of the FP64 contraction kernel from one ncu capture
 # (profiles/k4_herk_f64_si24.txt); valid for the kernel source it was taken on.
 TRAFFIC = {}
@@ -73,8 +77,41 @@ def parse_args():
     ap.add_argument("--grid-slots", type=int, default=-1,
                     help="real-space grid slots (0 = all k resident; default 8 for bi2se3, else 0)")
     ap.add_argument("--kchunk", type=int, default=0, help="k-chunk when not autotuning")
+    ap.add_argument("--k1-path", type=int, default=0, choices=[0, 1, 2],
+                    help="sphere -> grid kernels: 0 automatic, 1 per axis, 2 one kernel per band component")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")
+    ap.add_argument("--alu-peaks", action="store_true",
+                    help="only time cuBLAS FP64 and FP32 (no TF32) GEMMs of 8192^3 through torch.matmul "
+                         "and print them (the measured ALU ceilings for the roofline)")
     return ap.parse_args()
+
+
+def alu_peaks():
+    """Library GEMM rates that bound hand-written FP64 / FP32 arithmetic on
+    this GPU: torch.matmul (cuBLAS) on 8192^3, FP64 and FP32 with TF32 off,
+    CUDA events, 2 warm-ups, median of 5."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {}
+    n = 8192
+    for name, dt in (("fp64_gemm_tflops", torch.float64), ("fp32_gemm_tflops", torch.float32)):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        c = torch.empty(n, n, dtype=dt, device="cuda")
+        ts = []
+        for i in range(7):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(e0.elapsed_time(e1))
+        out[name] = 2 * n ** 3 / (statistics.median(ts) * 1e-3) / 1e12
+        del a, b, c
+    out["gpu"] = torch.cuda.get_device_name()
+    return out
 
 
 # ----------------------------------------------------------- distributed --
@@ -285,6 +322,8 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_GRID_SLOTS, args.grid_slots)
     if args.kchunk > 0:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk)
+    if args.k1_path > 0:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_K1_PATH, args.k1_path)
     ctx.upload(device_inputs=dev_in)
     tune_span = min(p.nk, 16 if precision == "mixed" else 4)
     tuning = ctx.autotune(0, tune_span) if not args.no_autotune else None
@@ -417,7 +456,9 @@ def run_ours(args, world, rank, local):
                     "executed_over_algorithmic_ops": ops_ratio,
                     "traffic": TRAFFIC.get("k4_herk_f64"),
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
-                                   "(nominal FP64 1.25 TFLOP/s)"}
+                                   "(nominal FP64 1.25 TFLOP/s)",
+                    "measured_dgemm_tflops": MEASURED_DGEMM_TFLOPS,
+                    "executed_frac_of_dgemm": executed / MEASURED_DGEMM_TFLOPS}
     else:
         roofline = {"bound": "tensor", "kernel": "k5_gemm", "achieved": achieved,
                     "peak": sustained / 3, "unit": "TFLOP/s", "frac": achieved / (sustained / 3),
@@ -512,6 +553,9 @@ def run_ours(args, world, rank, local):
 
 
 def main():
+    if "--alu-peaks" in sys.argv:
+        print(json.dumps({"alu_peaks": alu_peaks()}))
+        return 0
     args = parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -241,6 +241,11 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        caller's coefficient buffer instead of a copy: keep it
  *                        alive and unchanged until the k-point is uploaded
  *                        again or the context is destroyed.
+ *   BGW_OPT_K1_PATH      kernels of the sphere -> real-space transform of
+ *                        bgw_wfn_upload: 0 automatic (default), 1 one kernel
+ *                        per axis, 2 one kernel for the whole transform of a
+ *                        band component where the box fits in shared memory
+ *                        (else as 1).  All give the same grids up to rounding.
  *   BGW_OPT_TEST_FAIL_ALLOC for failure-handling tests only: when n > 0, the
  *                        n-th device allocation made by the library from now on
  *                        (by any context of the process) fails as if the device
@@ -255,7 +260,7 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        reports as BGW_E_TIMEOUT.  No fault, trap or hang.
  */
 enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
-       BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6 };
+       BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

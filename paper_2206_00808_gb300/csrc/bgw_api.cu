@@ -79,7 +79,8 @@ struct KPoint {
     bool uploaded = false;
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // sphere extents (Miller)
     int ngw = 0;
-    std::vector<int> cube_map;                  // host copy of the device map
+    std::vector<int> cube_map;                  // host copy of the device map: cube cell ->
+                                                // coefficient (or -1), then coefficient -> cell
     DevBuf map_dev;
     DevBuf coeff;                               // streaming mode: device copy of host coefficients
     const double *coeff_src = nullptr;          // streaming mode: coefficients the grid is built from
@@ -175,6 +176,7 @@ struct bgw_ctx_s {
     int sm_count = 0;
     int tile_v = 0, tile_c = 0;   // pair tile of the FP32 plane kernel (0 = automatic)
     int test_drop_load = 0;       // BGW_OPT_TEST_DROP_LOAD
+    int k1_path = 0;              // BGW_OPT_K1_PATH
     // k-points summed into the running sum (accumulate calls made since the
     // q-set was installed; replays of a captured graph are not counted)
     std::vector<int> kcount;
@@ -294,8 +296,8 @@ cudaError_t run_k1(bgw_ctx_s *c, int ik, const double *src, int slot) {
     const int *mp = static_cast<const int *>(kp.map_dev.p);
     const int rec = c->stage_begin(0);
     e = (c->prec == BGW_FP64)
-            ? bgw::wfn_to_grid_f64(src, kp.ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st)
-            : bgw::wfn_to_grid_f32(src, kp.ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st);
+            ? bgw::wfn_to_grid_f64(src, kp.ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st, c->k1_path)
+            : bgw::wfn_to_grid_f32(src, kp.ngw, (int)B, mp, ax, c->S.p, c->R.p, U, c->st, c->k1_path);
     c->stage_end(rec, 3);
     return e;
 }
@@ -863,6 +865,11 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
                            gvec[3 * i], gvec[3 * i + 1], gvec[3 * i + 2], ik);
         map[idx] = (int)i;
     }
+    // inverse map (coefficient -> cube cell) after the cube map
+    const size_t ncube = map.size();
+    map.resize(ncube + ngw);
+    for (size_t cell = 0; cell < ncube; ++cell)
+        if (map[cell] >= 0) map[ncube + map[cell]] = (int)cell;
     const long B = 2L * c->nb;
     cudaError_t e;
     KPoint &kp = c->k[ik];
@@ -1158,6 +1165,10 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
         case BGW_OPT_TEST_DROP_LOAD:
             c->test_drop_load = value != 0;
             return BGW_OK;
+        case BGW_OPT_K1_PATH:
+            if (value < 0 || value > 2) return c->fail(BGW_E_ARG, "set_option: K1 path must be 0..2");
+            c->k1_path = (int)value;
+            return BGW_OK;
         case BGW_OPT_TEST_FAIL_ALLOC:
             if (value < 0) return c->fail(BGW_E_ARG, "set_option: allocation count must be >= 0");
             g_fail_alloc.store(value);
@@ -1182,6 +1193,7 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_GRID_SLOTS: *value = c->nslots > 0 ? c->nslots : c->grid_slots_opt; return BGW_OK;
         case BGW_OPT_TEST_DROP_LOAD: *value = c->test_drop_load; return BGW_OK;
         case BGW_OPT_TEST_FAIL_ALLOC: *value = g_fail_alloc.load(); return BGW_OK;
+        case BGW_OPT_K1_PATH: *value = c->k1_path; return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }

@@ -54,51 +54,79 @@ constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
 
 // ------------------------------------------------------------ split kernel --
 // plane 0: A = X; plane 1 + j: B_j = w_j X.  Output [plane][hi|lo][R][Kp].
-constexpr int kSplitTile = 32;
+// One CTA per (32 complex G = 64 real rows) x (64 pairs) block writes every
+// plane of that block: M is read once, the weights are converted to FP32
+// once per pair, and each thread stores 16 consecutive pairs of one row
+// (two 16-byte stores per plane and half).  Rows 2*ng..R-1 and pairs
+// P..Kp-1 are written as zeros.
+constexpr int kSplitG = 32;
+constexpr int kSplitP = 64;
+constexpr int kSplitRow = kSplitG + 1;                  // padded shared row (floats)
+
+__host__ __device__ constexpr size_t split_smem_floats(int nfreq) {
+    return (size_t)2 * kSplitP * kSplitRow + 16 + (size_t)nfreq * kSplitP;
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) {
+    return *reinterpret_cast<uint32_t *>(&v);
+}
 
 __global__ void __launch_bounds__(256)
-k5_split(const float2 *__restrict__ M, int P, int ng, const double *__restrict__ w, int R, int Kp,
-         __nv_bfloat16 *__restrict__ X) {
-    __shared__ float2 tile[kSplitTile][kSplitTile + 1];   // [p][g]
-    __shared__ float wt[kSplitTile];                     // this block's pair weights in FP32
-    const int g0 = blockIdx.x * kSplitTile;   // complex column block (rows 2g, 2g+1)
-    const int p0 = blockIdx.y * kSplitTile;
-    const int plane = blockIdx.z;             // 0 = A, 1 + j = B_j
-    const int tx = threadIdx.x % kSplitTile, ty = threadIdx.x / kSplitTile;   // 32 x 8
-    // one FP64 -> FP32 conversion per pair (the FP64 unit is slow on this part)
-    if (threadIdx.x < kSplitTile)
-        wt[tx] = (plane > 0 && p0 + tx < P) ? (float)w[(long)(plane - 1) * P + p0 + tx] : 1.0f;
-    __syncthreads();
-    for (int i = ty; i < kSplitTile; i += 8) {
+k5_split(const float2 *__restrict__ M, int P, int ng, const double *__restrict__ w, int nfreq, int R,
+         int Kp, __nv_bfloat16 *__restrict__ X) {
+    extern __shared__ float split_sm[];
+    float *re = split_sm;                                // [kSplitP][kSplitRow]
+    float *im = re + kSplitP * kSplitRow + 16;           // offset by 16 banks from re
+    float *wt = im + kSplitP * kSplitRow;                // [nfreq][kSplitP]
+    // blockIdx.x runs along the pairs, so CTAs resident together write
+    // neighbouring 128-byte pieces of the same rows (whole DRAM pages)
+    const int p0 = blockIdx.x * kSplitP, g0 = blockIdx.y * kSplitG;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    // one FP64 -> FP32 conversion per pair and frequency (the FP64 unit is slow on this part)
+    for (int i = threadIdx.x; i < nfreq * kSplitP; i += 256) {
+        const int j = i / kSplitP, p = p0 + i % kSplitP;
+        wt[i] = p < P ? (float)w[(long)j * P + p] : 0.f;
+    }
+    for (int i = ty; i < kSplitP; i += 8) {
         const int p = p0 + i, g = g0 + tx;
         float2 v = make_float2(0.f, 0.f);
         if (p < P && g < ng) v = M[(long)p * ng + g];
-        v.x *= wt[i];
-        v.y *= wt[i];
-        tile[i][tx] = v;
+        re[i * kSplitRow + tx] = v.x;
+        im[i * kSplitRow + tx] = v.y;
     }
     __syncthreads();
+    const int r = threadIdx.x % 64;                      // local real row: G = g0 + r/2, Re/Im = r&1
+    const int pq = (threadIdx.x / 64) * 16;              // first of this thread's 16 pairs
+    const int row = 2 * g0 + r;
+    const float *src = ((r & 1) ? im : re) + (r >> 1);
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = src[(pq + i) * kSplitRow];
     const long planeElems = (long)R * Kp;
-    __nv_bfloat16 *hi = X + (long)plane * 2 * planeElems;
-    __nv_bfloat16 *lo = hi + planeElems;
-    // each thread writes pair p0+tx for rows 2g, 2g+1 of eight g
-    for (int i = ty; i < kSplitTile; i += 8) {
-        const int g = g0 + i, p = p0 + tx;
-        if (2 * g >= R || p >= Kp) continue;
-        const float2 v = tile[tx][i];
-        const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hm = __float2bfloat16_rn(v.y);
-        const __nv_bfloat16 lr = __float2bfloat16_rn(v.x - __bfloat162float(hr));
-        const __nv_bfloat16 lm = __float2bfloat16_rn(v.y - __bfloat162float(hm));
-        hi[(long)(2 * g) * Kp + p] = hr;
-        hi[(long)(2 * g + 1) * Kp + p] = hm;
-        lo[(long)(2 * g) * Kp + p] = lr;
-        lo[(long)(2 * g + 1) * Kp + p] = lm;
+    __nv_bfloat16 *base = X + (long)row * Kp + p0 + pq;
+    for (int plane = 0; plane <= nfreq; ++plane) {
+        const float *wp = wt + (plane - 1) * kSplitP + pq;
+        uint32_t h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+            float a = x[i], b = x[i + 1];
+            if (plane > 0) {
+                a *= wp[i];
+                b *= wp[i + 1];
+            }
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(a, b);
+            const float2 hf = __bfloat1622float2(hh);
+            h[i / 2] = bf2_bits(hh);
+            l[i / 2] = bf2_bits(__floats2bfloat162_rn(a - hf.x, b - hf.y));
+        }
+        uint4 *ho = reinterpret_cast<uint4 *>(base + (long)plane * 2 * planeElems);
+        uint4 *lo = reinterpret_cast<uint4 *>(base + ((long)plane * 2 + 1) * planeElems);
+        ho[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        ho[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        lo[0] = make_uint4(l[0], l[1], l[2], l[3]);
+        lo[1] = make_uint4(l[4], l[5], l[6], l[7]);
     }
 }
-
-// Rows beyond 2*ng and pairs beyond P are zero: the padding rows are written
-// by the block that owns them only when 2g < R; rows 2*ng..R-1 of the last
-// block get zeros above, pairs P..Kp-1 get zeros from the guarded loads.
 
 // --------------------------------------------------------- PTX helpers --
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -533,10 +561,15 @@ cudaError_t mixed_split(const void *M, int P, int ng, const double *w, int nfreq
     if (P == 0) return cudaSuccess;
     const long R = round_up(2L * ng, kTileM);
     const long Kp = round_up(P, kBlockK);
-    dim3 sgrid((unsigned)((R / 2 + kSplitTile - 1) / kSplitTile),
-               (unsigned)((Kp + kSplitTile - 1) / kSplitTile), (unsigned)(1 + nfreq));
-    k5_split<<<sgrid, 256, 0, st>>>(static_cast<const float2 *>(M), P, ng, w, (int)R, (int)Kp,
-                                    static_cast<__nv_bfloat16 *>(ws));
+    // R is a multiple of 128 (64 real rows per block) and Kp of 64
+    dim3 sgrid((unsigned)(Kp / kSplitP), (unsigned)(R / (2 * kSplitG)));
+    const size_t smem = sizeof(float) * split_smem_floats(nfreq);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k5_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k5_split<<<sgrid, 256, smem, st>>>(static_cast<const float2 *>(M), P, ng, w, nfreq, (int)R, (int)Kp,
+                                       static_cast<__nv_bfloat16 *>(ws));
     return cudaGetLastError();
 }
 

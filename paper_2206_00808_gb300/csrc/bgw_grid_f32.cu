@@ -7,8 +7,8 @@
 namespace bgw {
 cudaError_t grid_tables_init_f32() { return f32::upload_tables(); }
 cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube_map,
-                            const Axes &a, void *S, void *R, void *U, cudaStream_t st) {
-    return f32::wfn_to_grid(coeff, ngw, B, cube_map, a, S, R, U, st);
+                            const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path) {
+    return f32::wfn_to_grid(coeff, ngw, B, cube_map, a, S, R, U, st, path);
 }
 cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,

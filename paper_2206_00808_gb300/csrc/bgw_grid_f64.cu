@@ -6,8 +6,8 @@
 namespace bgw {
 cudaError_t grid_tables_init_f64() { return f64::upload_tables(); }
 cudaError_t wfn_to_grid_f64(const double *coeff, int ngw, int B, const int *cube_map,
-                            const Axes &a, void *S, void *R, void *U, cudaStream_t st) {
-    return f64::wfn_to_grid(coeff, ngw, B, cube_map, a, S, R, U, st);
+                            const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path) {
+    return f64::wfn_to_grid(coeff, ngw, B, cube_map, a, S, R, U, st, path);
 }
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,

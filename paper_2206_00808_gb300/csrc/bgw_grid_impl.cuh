@@ -12,11 +12,11 @@
 //   pair density -> M (forward, e^{-2 pi i f.r/N}): z first on all n0*n1
 //     lines, keeping the w2 needed outputs, then y keeping w1, then x keeping
 //     w0, then a gather of the dielectric sphere from the kept cube.
-// A cube that starts at index s (not 0) is handled by a phase: an input
-// placed at s + j picks up e^{+2 pi i s x/N} after the inverse transform; the
-// outputs s + j of a forward transform are the outputs j of the input
-// multiplied by e^{-2 pi i s z/N}.  The phases come from the twiddle table
-// with a warp-uniform index, so no register array is indexed at run time.
+// A cube that starts at box index s (not 0) is placed by rotating memory
+// indices, not by phase factors: cube entry j sits at box position
+// (s + j) mod N, so the inverse transform loads register f from cube slot
+// (f - s) mod N and the forward transform stores output f to slot
+// (f - s) mod N (see rot<N>).  Register indices stay compile-time.
 #pragma once
 #include <cmath>
 
@@ -338,6 +338,113 @@ k2_xpass_scatter_c4(const C *__restrict__ Bs, long P, int w0, int w1, int w2, in
         }
 }
 
+// ------------------------------------------ sphere -> grid, one kernel --
+// Whole inverse transform of one band component per CTA, for boxes whose
+// x-transformed cube fits in shared memory.  The band's coefficients are read
+// once, coalesced, and scattered into the sphere's bounding cube in shared
+// memory (inv[i] = cube cell of coefficient i); x lines of the cube go to
+// X[N][w1][w2]; then, KP x-planes at a time, y lines go to Y[KP][N][w2p]
+// (over the dead cube) and z lines are written to the grid.  No
+// intermediate array leaves the SM.
+constexpr int kFusedThreads = 256;
+
+template <int N>
+__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
+k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv, int w0, int w1,
+         int w2, int s0, int s1, int s2, int KP, C *__restrict__ U) {
+    extern __shared__ unsigned char smem_raw[];
+    C *X = reinterpret_cast<C *>(smem_raw);
+    const int yzs = w1 * w2;
+    const int w2p = w2 | 1;                    // odd row stride: conflict-free z-line reads
+    C *cube = X + (long)N * yzs;               // [w0][w1][w2], later Y[KP][N][w2p]
+    C *Y = cube;
+    const long b = blockIdx.x;
+    const double2 *cb = coeff + b * ngw;
+    const int ncube = w0 * yzs;
+    for (int i = threadIdx.x; i < ncube; i += kFusedThreads) cube[i] = C{T(0), T(0)};
+    __syncthreads();
+    for (int i = threadIdx.x; i < ngw; i += kFusedThreads) {
+        const double2 c = __ldg(cb + i);
+        cube[__ldg(inv + i)] = C{(T)c.x, (T)c.y};
+    }
+    __syncthreads();
+    const int ns0 = N - s0, ns1 = N - s1, ns2 = N - s2;
+    for (int l = threadIdx.x; l < yzs; l += kFusedThreads) {
+        C a[N];
+#pragma unroll
+        for (int f = 0; f < N; ++f) {
+            const int j = rot<N>(f, ns0);
+            a[f] = (j < w0) ? cube[j * yzs + l] : C{T(0), T(0)};
+        }
+        fft_line<T, +1, N>(a);
+#pragma unroll
+        for (int x = 0; x < N; ++x) X[x * yzs + l] = a[x];
+    }
+    __syncthreads();
+    C *out = U + b * (long)N * N * N;
+    for (int x0 = 0; x0 < N; x0 += KP) {
+        const int kp = min(KP, N - x0);
+        for (int l = threadIdx.x; l < kp * w2; l += kFusedThreads) {
+            const int xl = l / w2, z = l % w2;
+            const C *xi = X + (x0 + xl) * yzs + z;
+            C a[N];
+#pragma unroll
+            for (int f = 0; f < N; ++f) {
+                const int j = rot<N>(f, ns1);
+                a[f] = (j < w1) ? xi[j * w2] : C{T(0), T(0)};
+            }
+            fft_line<T, +1, N>(a);
+            C *yo = Y + xl * N * w2p + z;
+#pragma unroll
+            for (int y = 0; y < N; ++y) yo[y * w2p] = a[y];
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < kp * N; l += kFusedThreads) {
+            const int xl = l / N, y = l % N;
+            const C *yi = Y + (xl * N + y) * w2p;
+            C a[N];
+#pragma unroll
+            for (int f = 0; f < N; ++f) {
+                const int j = rot<N>(f, ns2);
+                a[f] = (j < w2) ? yi[j] : C{T(0), T(0)};
+            }
+            fft_line<T, +1, N>(a);
+            C *o = out + ((long)(x0 + xl) * N + y) * N;
+            if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+#pragma unroll
+                for (int z = 0; z < N; z += 2)
+                    *reinterpret_cast<float4 *>(o + z) = make_float4(a[z].x, a[z].y, a[z + 1].x, a[z + 1].y);
+            } else {
+#pragma unroll
+                for (int z = 0; z < N; ++z) o[z] = a[z];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Shared bytes of k1_fused with KP planes per chunk (Y reuses the cube).
+static size_t fused_smem(const Axes &a, int KP) {
+    const size_t cube = (size_t)a.w[0] * a.w[1] * a.w[2];
+    const size_t y = (size_t)KP * a.n[1] * (a.w[2] | 1);
+    return sizeof(C) * ((size_t)a.n[0] * a.w[1] * a.w[2] + (cube > y ? cube : y));
+}
+// Automatic choice: two CTAs per SM; on request (path 2) up to one per SM.
+static constexpr size_t kFusedSmemAuto = 110 * 1024;
+static constexpr size_t kFusedSmemMax = 200 * 1024;
+
+// Planes per chunk for k1_fused: the fewest chunks of equal size that fit
+// in `limit` bytes (0: the box does not fit; use the pass kernels).
+static int fused_planes(const Axes &a, size_t limit) {
+    if (a.n[0] != a.n[1] || a.n[1] != a.n[2] || a.n[0] >= kCoopMinN) return 0;
+    const int n = a.n[0];
+    for (int chunks = 1; chunks <= n; ++chunks) {
+        const int KP = (n + chunks - 1) / chunks;
+        if (fused_smem(a, KP) <= limit) return KP;
+    }
+    return 0;
+}
+
 // ----------------------------------------- plane-fused passes (FP32) --
 // Band planes staged through shared memory with batched loads (kStageU in
 // flight per thread); every line is then read from a padded shared row.
@@ -352,8 +459,8 @@ __host__ __device__ constexpr int plane_row() { return N % 2 == 0 ? N + 2 : N + 
 
 // Pair density + z pass + y pass for one x-plane and a tile of tv x tc pairs.
 // Shared: planes[(tv+tc)][2][N][N+1], then Z[tv*tc][N][w2].
-template <int N>
-__global__ void __launch_bounds__(kPlaneThreads, 2)
+template <int N, int MINB>
+__global__ void __launch_bounds__(kPlaneThreads, MINB)
 k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int TV, int TC,
             int w1, int w2, int s1, int s2, C *__restrict__ Bs) {
     extern __shared__ unsigned char smem_raw[];
@@ -563,10 +670,27 @@ static inline unsigned quads_for(long lines) { return (unsigned)((4 * lines + kL
     }
 
 static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *cube_map,
-                               const Axes &a, void *S, void *R, void *U, cudaStream_t st) {
+                               const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path) {
     const long nb = B;
     C *Sp = static_cast<C *>(S), *Rp = static_cast<C *>(R), *Up = static_cast<C *>(U);
     const double2 *cf = reinterpret_cast<const double2 *>(coeff);
+    const int *inv = cube_map + (long)a.w[0] * a.w[1] * a.w[2];
+    if (const int KP = path == 1 ? 0 : fused_planes(a, path == 2 ? kFusedSmemMax : kFusedSmemAuto)) {
+        const size_t smem = fused_smem(a, KP);
+        cudaError_t e = cudaSuccess;
+        BGW_FOR_EACH_LEN(a.n[0], {
+            if constexpr (N < kCoopMinN) {
+                if (smem > 48 * 1024) {
+                    e = cudaFuncSetAttribute(k1_fused<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+                    if (e != cudaSuccess) return e;
+                }
+                k1_fused<N><<<(unsigned)nb, kFusedThreads, smem, st>>>(
+                    cf, ngw, inv, a.w[0], a.w[1], a.w[2], a.s[0], a.s[1], a.s[2], KP, Up);
+            }
+        });
+        return cudaGetLastError();
+    }
     {
         const long lines = nb * a.w[1] * a.w[2];
         BGW_FOR_EACH_LEN(a.n[0], (k1_xpass<N><<<blocks_for(lines), kLineThreads, 0, st>>>(
@@ -578,7 +702,9 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
             return sizeof(C) * ((size_t)tb * a.w[1] * a.w[2] + (size_t)tb * n * (a.w[2] + 1) +
                                 (size_t)tb * n * (n + 1));
         };
-        int TB = 4;
+        // band components per CTA: as many as fit two CTAs per SM (fills the
+        // 256 threads with w2 y lines and N z lines per component)
+        int TB = 16;
         while (TB > 1 && yz_smem(TB) > kPlaneSmemMax) --TB;
         const size_t smem = yz_smem(TB);
         if (smem <= kPlaneSmemLarge) {
@@ -616,31 +742,44 @@ static size_t plane_smem(int tv, int tc, int n, int w2) {
     return sizeof(C) * ((size_t)(tv + tc) * 2 * n * rs + (size_t)tv * tc * n * w2);
 }
 
+// Three CTAs per SM (80 registers per thread, no spills up to N = 30) for
+// tiles whose shared memory allows it.
+static constexpr size_t kPlaneSmem3 = 72 * 1024;
+static bool plane_three_per_sm(const Axes &a, size_t smem) { return a.n[1] <= 30 && smem <= kPlaneSmem3; }
+
 static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int max) {
     if (!use_plane_kernels(a)) return 0;
     struct Cand { double cost; int tv, tc; };
-    Cand best[64];
-    int nbest = 0;
+    // two ranked lists: tiles for two CTAs per SM (the default first), and
+    // smaller tiles that allow three
+    Cand best[2][64];
+    int nbest[2] = {0, 0};
     const size_t budget = plane_smem(1, 1, a.n[1], a.w[2]) <= kPlaneSmemMax ? kPlaneSmemMax : kPlaneSmemLarge;
     for (int tv = 1; tv <= nv && tv <= 16; ++tv)
         for (int tc = 1; tc <= nc && tc <= 16; ++tc) {
-            if (plane_smem(tv, tc, a.n[1], a.w[2]) > budget) continue;
+            const size_t sm = plane_smem(tv, tc, a.n[1], a.w[2]);
+            if (sm > budget) continue;
+            const int cls = plane_three_per_sm(a, sm) ? 1 : 0;
+            Cand *b = best[cls];
             const Cand c{(double)(tv + tc) / (tv * tc) - 1e-3 * tv * tc, tv, tc};
-            int pos = nbest < 64 ? nbest++ : 63;
-            if (pos == 63 && c.cost >= best[63].cost) continue;
-            best[pos] = c;
-            while (pos > 0 && best[pos].cost < best[pos - 1].cost) {
-                const Cand t = best[pos];
-                best[pos] = best[pos - 1];
-                best[pos - 1] = t;
+            int pos = nbest[cls] < 64 ? nbest[cls]++ : 63;
+            if (pos == 63 && c.cost >= b[63].cost) continue;
+            b[pos] = c;
+            while (pos > 0 && b[pos].cost < b[pos - 1].cost) {
+                const Cand t = b[pos];
+                b[pos] = b[pos - 1];
+                b[pos - 1] = t;
                 --pos;
             }
         }
-    const int n = nbest < max ? nbest : max;
-    for (int i = 0; i < n; ++i) {
-        TV[i] = best[i].tv;
-        TC[i] = best[i].tc;
-    }
+    int n = 0;
+    for (int i = 0; n < max && (i < nbest[0] || i < nbest[1]); ++i)
+        for (int cls = 0; cls < 2 && n < max; ++cls)
+            if (i < nbest[cls]) {
+                TV[n] = best[cls][i].tv;
+                TC[n] = best[cls][i].tc;
+                ++n;
+            }
     return n;
 }
 
@@ -675,14 +814,17 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
     if (TV > 0) {
         dim3 grid((unsigned)a.n[0], (unsigned)((nv + TV - 1) / TV), (unsigned)((nc + TC - 1) / TC));
         cudaError_t e = cudaSuccess;
+        const bool three = plane_three_per_sm(a, psmem);
         BGW_FOR_EACH_LEN(a.n[1], {
+            auto kern = k2_zy_plane<N, 2>;
+            if constexpr (N <= 30)
+                if (three) kern = k2_zy_plane<N, 3>;
             if (psmem > 48 * 1024) {
-                e = cudaFuncSetAttribute(k2_zy_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)psmem);
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
                 if (e != cudaSuccess) return e;
             }
-            k2_zy_plane<N><<<grid, kPlaneThreads, psmem, st>>>(uv, uc, nv, nc, TV, TC, a.w[1], a.w[2],
-                                                              a.s[1], a.s[2], Bp);
+            kern<<<grid, kPlaneThreads, psmem, st>>>(uv, uc, nv, nc, TV, TC, a.w[1], a.w[2], a.s[1], a.s[2],
+                                                     Bp);
         });
     } else {
         const long plane = (long)a.n[0] * a.n[1];

@@ -20,12 +20,14 @@ cudaError_t grid_tables_init_f32();
 // Sphere -> real space for B = 2*nb band components of one k:
 //   u_b(r) = sum_{h in sphere} c_b(h) e^{+2 pi i h.r / N}
 // coeff: complex128 [B][ngw]; cube_map: [w0][w1][w2] -> coefficient index or
-// -1 (cube origin at Miller index s, i.e. a.s = sphere minimum); S: [B][n0][w1][w2],
-// R: [B][n0][n1][w2] scratch of T-complex; U: [B][n0][n1][n2] T-complex.
+// -1 (cube origin at Miller index s, i.e. a.s = sphere minimum), followed by
+// the inverse map [ngw] -> cube cell; S: [B][n0][w1][w2], R: [B][n0][n1][w2]
+// scratch of T-complex; U: [B][n0][n1][n2] T-complex.  path: 0 automatic,
+// 1 the per-axis pass kernels, 2 the one-kernel transform where it fits.
 cudaError_t wfn_to_grid_f64(const double *coeff, int ngw, int B, const int *cube_map,
-                            const Axes &a, void *S, void *R, void *U, cudaStream_t st);
+                            const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path = 0);
 cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube_map,
-                            const Axes &a, void *S, void *R, void *U, cudaStream_t st);
+                            const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path = 0);
 
 // Pair density, pruned forward FFT and gather for P = nv*nc pairs of one k:
 //   M[v*nc+c][g] = N^-3 sum_r sum_alpha conj(u_v,alpha(r)) u_c,alpha(r) e^{-2 pi i f_g.r/N}

@@ -56,7 +56,7 @@ def test_resume_refuses_other_problem_and_cut_buffer(gpu_lib):
     ctx = B.Chi0Context(p, "fp64")
     ctx.upload()
     ctx.accumulate(0, 2)
-    ck = B.bgw_chi0_checkpoint(ctx)
+    ck = B.bgw_chi0_checkpoint(ctx.ctx)
     with pytest.raises(B.BgwError) as e:
         B.bgw_chi0_resume(ctx.ctx, ctx.qlist(), p.freq + 1.0, ck)      # other frequencies
     assert e.value.status == B.BGW_E_STATE
