@@ -53,9 +53,19 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # (profiles/alu_peaks_gb300.md; `bench.py --alu-peaks` measures it again).
 MEASURED_DGEMM_TFLOPS = 1.101
 
-# DRAM bytes per launch of the FP64 contraction kernel from one ncu capture
-# (profiles/k4_herk_f64_si24.txt); valid for the kernel source it was taken on.
-TRAFFIC = {}
+# FP32 FFMA peak from unit counts and clocks: 152 SMs x 128 lanes x 2 flop x
+# 2.07 GHz (cuBLAS SGEMM measures 69.7 TFLOP/s on this GPU type).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM bytes (read + write) of one launch, from one ncu capture of the
+# full-size workload with that k-chunk (profiles/traffic_si24.md); valid for
+# the kernel sources they were taken on.  Keyed by (workload, kernel, k-chunk).
+TRAFFIC = {("si24", "k4_herk_f64", 16): 145.66e6 + 67.13e6,
+           ("si24", "k5_gemm", 16): 477.86e6 + 3.16e6}
+
+
+def traffic(workload, kernel, kchunk):
+    return TRAFFIC.get((workload, kernel, kchunk))
 
 
 def parse_args():
@@ -375,6 +385,21 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
                          "launch_groups": calls, "kernels": kern}
                      for s, (sms, calls, kern) in prof.items() if calls}
     res["gpu_launches"] = sum(v["kernels"] for v in res["stages"].values())
+    # achieved algorithmic rate and roofline fraction of each stage with a FLOP model
+    fl = flop_model(p)
+    burst, sustained, _ = bf16_peaks()
+    peaks = ({"wfn_to_grid": (FP64_PEAK_TFLOPS, "FP64 ALU (derived)"),
+              "mtxel": (FP64_PEAK_TFLOPS, "FP64 ALU (derived)"),
+              "contraction": (FP64_PEAK_TFLOPS, "FP64 ALU (derived)")}
+             if precision == "fp64" else
+             {"wfn_to_grid": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
+              "mtxel": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
+              "contraction": (sustained / 3, "BF16 sustained / 3 products")})
+    for name, st in res["stages"].items():
+        if name in peaks and st["ms_per_step"] > 0:
+            tf = fl[name] / (st["ms_per_step"] * 1e-3) / 1e12
+            st.update({"tflops": tf, "peak_tflops": peaks[name][0], "roofline_frac": tf / peaks[name][0],
+                       "peak": peaks[name][1]})
     return res
 
 
@@ -443,6 +468,7 @@ def run_ours(args, world, rank, local):
     # algorithmic contraction FLOPs of the profiled steps over the kernel's summed device time
     achieved = fl["contraction"] * steps / (con_ms * 1e-3) / 1e12
     burst, sustained, src = bf16_peaks()
+    head_kchunk = head["tuning"]["kchunk"] if head["tuning"] else max(1, args.kchunk)
     if args.precision == "fp64":
         # The kernel forms conj(M_g) M_g' once per pair (4 FP64 operations) and
         # weights it per frequency (2 FMAs each): (4 + 2 N_w) operations per
@@ -454,7 +480,7 @@ def run_ours(args, world, rank, local):
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "executed_fp64_tflops": executed, "executed_frac": executed / FP64_PEAK_TFLOPS,
                     "executed_over_algorithmic_ops": ops_ratio,
-                    "traffic": TRAFFIC.get("k4_herk_f64"),
+                    "traffic": traffic(args.workload, "k4_herk_f64", head_kchunk),
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                                    "(nominal FP64 1.25 TFLOP/s)",
                     "measured_dgemm_tflops": MEASURED_DGEMM_TFLOPS,
@@ -462,7 +488,7 @@ def run_ours(args, world, rank, local):
     else:
         roofline = {"bound": "tensor", "kernel": "k5_gemm", "achieved": achieved,
                     "peak": sustained / 3, "unit": "TFLOP/s", "frac": achieved / (sustained / 3),
-                    "traffic": TRAFFIC.get("k5_gemm"),
+                    "traffic": traffic(args.workload, "k5_gemm", head_kchunk),
                     "peak_source": f"{src} BF16 sustained {sustained} / 3 products"}
     e2e = None if args.no_e2e else e2e_measure(B, torch, p, head, args, dist, stream)
     check = None
@@ -519,7 +545,7 @@ def run_ours(args, world, rank, local):
                               "frac": gm_ach / (sustained / 3),
                               "executed_bf16_tflops": executed / (gm_ms * 1e-3) / 1e12,
                               "executed_frac_of_bf16": executed / (gm_ms * 1e-3) / 1e12 / sustained,
-                              "traffic": TRAFFIC.get("k5_gemm"),
+                              "traffic": traffic(args.workload, "k5_gemm", kc),
                               "peak_source": f"{src} BF16 sustained {sustained} TFLOP/s / 3 products"}}
         mix["ctx"].close()
 
