@@ -12,7 +12,10 @@ What the functions follow (arXiv:2206.00808, Sec. II):
   * `chi0`       -- the P formula: (1/N_k) sum_k sum_v sum_c w conj(M) M,
                     no spin-degeneracy factor;
   * `umklapp`    -- k + q = k' + G0 with k' on the grid (Bloch periodicity;
-                    the paper is silent on it).
+                    the paper is silent on it);
+  * `coulomb`    -- v(q+G) = 4 pi e^2 / (Omega |q+G|^2) in eV;
+  * `epsinv`     -- eps = delta - v(q+G) P and W = eps^-1 v(q+G') (the two
+                    equations before the P formula), eps^-1 by a plain LU.
 All are pinned by tests/test_oracle_pins.py; none is "parity unpinned".
 """
 from __future__ import annotations
@@ -60,6 +63,10 @@ def _load():
             lib.oracle_chi0_accumulate.restype = None
             lib.oracle_scale.argtypes = [ctypes.c_long, ctypes.c_double, P]
             lib.oracle_scale.restype = None
+            lib.oracle_coulomb.argtypes = [P, P, ctypes.c_int, P, P]
+            lib.oracle_coulomb.restype = None
+            lib.oracle_epsinv.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P]
+            lib.oracle_epsinv.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -145,3 +152,29 @@ def chi0(problem, iq: int = 0, k_indices=None, nc=None) -> np.ndarray:
     flat = chi.reshape(-1).view(np.float64)
     lib.oracle_scale(flat.size, 1.0 / problem.nk, _ptr(flat))
     return chi
+
+
+def coulomb(avec, q, gvec) -> np.ndarray:
+    """v(q+G) = 4 pi e^2 / (Omega |q+G|^2) in eV for Miller vectors gvec
+    (ng, 3), cell rows avec (bohr); 0 where q + G = 0."""
+    lib = _load()
+    a, qq, g = _f64(np.asarray(avec).reshape(9)), _f64(q), _i32(gvec)
+    v = np.zeros(len(g), dtype=np.float64)
+    lib.oracle_coulomb(_ptr(a), _ptr(qq), len(g), _ptr(g), _ptr(v))
+    return v
+
+
+def epsinv(chi, v) -> tuple[np.ndarray, np.ndarray]:
+    """(eps^-1, W) per frequency for chi [nfreq][ng][ng] (eV^-1) and v [ng] (eV):
+    eps = delta - v(q+G) chi, W = eps^-1 v(q+G')."""
+    lib = _load()
+    chi = _c128(chi)
+    if chi.ndim == 2:
+        chi = chi[None]
+    nf, ng, _ = chi.shape
+    vv = _f64(v)
+    e = np.zeros_like(chi)
+    w = np.zeros_like(chi)
+    if lib.oracle_epsinv(ng, nf, _ptr(chi), _ptr(vv), _ptr(e), _ptr(w)) != 0:
+        raise ArithmeticError("oracle_epsinv: singular matrix or allocation failure")
+    return e, w

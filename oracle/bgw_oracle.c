@@ -33,6 +33,11 @@
  * parallel loops split only independent output entries, so the result does
  * not depend on the thread count.
  *
+ *  Dielectric matrix and screened interaction (Sec. II, the two equations
+ *  before the P formula): eps = delta - v(q+G) P, W = eps^-1 v(q+G'), with
+ *  eps^-1 by a plain LU (oracle_coulomb, oracle_epsinv at the end of this
+ *  file).
+ *
  * Parity status: every function here is pinned by the CPU tests (brute-force
  * real-space sums, numpy.fft, closed forms and invariants); none is unpinned.
  */
@@ -165,4 +170,188 @@ void oracle_chi0_accumulate(int nv, int nc, int ng, const double *M,
 void oracle_scale(long n, double s, double *x)
 {
     for (long i = 0; i < n; ++i) x[i] *= s;
+}
+
+/*
+ * ---------------------------------------------------------------------------
+ * Dielectric matrix, its inverse and the screened interaction (Sec. II, the
+ * two equations before the P formula):
+ *      eps_GG'(q, w) = delta_GG' - v(q+G) P_GG'(q, w)
+ *      W_GG'(q, w)   = eps^-1_GG'(q, w) v(q+G')
+ * with the bare Coulomb interaction v(q+G) = 4 pi e^2 / (Omega |q+G|^2).
+ * The P formula as printed has no 1/Omega; it is carried here by v, so that
+ * with chi0 in eV^-1 and e^2 = 1 Hartree bohr = 27.211386245988 eV bohr the
+ * product v chi0 is dimensionless and W is in eV.  v = 0 where q + G = 0 (the
+ * head at q = 0 is not defined by these equations; eps is then the identity
+ * in that row).
+ * ---------------------------------------------------------------------------
+ */
+#define ORACLE_E2_EV_BOHR 27.211386245988
+#define ORACLE_PI 3.14159265358979323846
+
+/*
+ * v[g] = 4 pi e^2 / (Omega |(q + h_g) B|^2) in eV for the Miller vectors
+ * gvec[g] = h_g, with avec the rows a_1, a_2, a_3 (bohr), B = 2 pi A^-T and
+ * Omega = |det A|.
+ */
+void oracle_coulomb(const double *avec, const double *q, int ng, const int *gvec, double *v)
+{
+    const double *a0 = avec, *a1 = avec + 3, *a2 = avec + 6;
+    /* b_i = 2 pi (a_j x a_k) / (a_0 . (a_1 x a_2)) */
+    double c12[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
+    double c20[3] = {a2[1] * a0[2] - a2[2] * a0[1], a2[2] * a0[0] - a2[0] * a0[2], a2[0] * a0[1] - a2[1] * a0[0]};
+    double c01[3] = {a0[1] * a1[2] - a0[2] * a1[1], a0[2] * a1[0] - a0[0] * a1[2], a0[0] * a1[1] - a0[1] * a1[0]};
+    double det = a0[0] * c12[0] + a0[1] * c12[1] + a0[2] * c12[2];
+    double omega = det < 0 ? -det : det;
+    double b[3][3];
+    for (int x = 0; x < 3; ++x) {
+        b[0][x] = 2.0 * ORACLE_PI * c12[x] / det;
+        b[1][x] = 2.0 * ORACLE_PI * c20[x] / det;
+        b[2][x] = 2.0 * ORACLE_PI * c01[x] / det;
+    }
+    for (int g = 0; g < ng; ++g) {
+        double k[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i) {
+            double c = q[i] + gvec[3 * g + i];
+            for (int x = 0; x < 3; ++x) k[x] += c * b[i][x];
+        }
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        v[g] = k2 > 1e-24 ? 4.0 * ORACLE_PI * ORACLE_E2_EV_BOHR / (omega * k2) : 0.0;
+    }
+}
+
+/*
+ * For each frequency j: eps = I - diag(v) chi[j] (as printed), eps^-1 by LU
+ * with partial pivoting (Doolittle, column by column of the identity), and
+ * W = eps^-1 diag(v).  chi, epsinv, W: complex128 [nfreq][ng][ng] row-major
+ * (G row, G' column).  Returns -1 on a zero pivot or allocation failure.
+ */
+int oracle_epsinv(int ng, int nfreq, const double *chi, const double *v, double *epsinv, double *W)
+{
+    long n = ng;
+    double *a = (double *)malloc(sizeof(double) * 2 * n * n);
+    int *piv = (int *)malloc(sizeof(int) * n);
+    if (!a || !piv) {
+        free(a);
+        free(piv);
+        return -1;
+    }
+    int failed = 0;
+    for (int j = 0; j < nfreq && !failed; ++j) {
+        const double *cj = chi + 2 * (long)j * n * n;
+        double *ej = epsinv + 2 * (long)j * n * n;
+        double *wj = W + 2 * (long)j * n * n;
+        /* eps = delta - v(q+G) P */
+        for (long r = 0; r < n; ++r)
+            for (long c = 0; c < n; ++c) {
+                a[2 * (r * n + c)] = (r == c ? 1.0 : 0.0) - v[r] * cj[2 * (r * n + c)];
+                a[2 * (r * n + c) + 1] = -v[r] * cj[2 * (r * n + c) + 1];
+            }
+        /* LU with partial pivoting: P a = L U, L unit lower, stored in place */
+        for (long k = 0; k < n; ++k) {
+            long p = k;
+            double best = -1.0;
+            for (long r = k; r < n; ++r) {
+                double m = a[2 * (r * n + k)] * a[2 * (r * n + k)] + a[2 * (r * n + k) + 1] * a[2 * (r * n + k) + 1];
+                if (m > best) {
+                    best = m;
+                    p = r;
+                }
+            }
+            piv[k] = (int)p;
+            if (best <= 0.0) {
+                failed = 1;
+                break;
+            }
+            if (p != k)
+                for (long c = 0; c < 2 * n; ++c) {
+                    double t = a[2 * k * n + c];
+                    a[2 * k * n + c] = a[2 * p * n + c];
+                    a[2 * p * n + c] = t;
+                }
+            double pr = a[2 * (k * n + k)], pi = a[2 * (k * n + k) + 1];
+            double den = pr * pr + pi * pi;
+            for (long r = k + 1; r < n; ++r) {
+                double xr = a[2 * (r * n + k)], xi = a[2 * (r * n + k) + 1];
+                double lr = (xr * pr + xi * pi) / den, li = (xi * pr - xr * pi) / den;   /* x / pivot */
+                a[2 * (r * n + k)] = lr;
+                a[2 * (r * n + k) + 1] = li;
+                for (long c = k + 1; c < n; ++c) {
+                    double ur = a[2 * (k * n + c)], ui = a[2 * (k * n + c) + 1];
+                    a[2 * (r * n + c)] -= lr * ur - li * ui;
+                    a[2 * (r * n + c) + 1] -= lr * ui + li * ur;
+                }
+            }
+        }
+        if (failed) break;
+        /* columns of eps^-1: solve L U x = P e_c */
+#pragma omp parallel for schedule(static)
+        for (long c = 0; c < n; ++c) {
+            double *x = (double *)malloc(sizeof(double) * 2 * n);
+            if (!x) {
+#pragma omp atomic write
+                failed = 1;
+                continue;
+            }
+            for (long r = 0; r < n; ++r) x[2 * r] = x[2 * r + 1] = 0.0;
+            /* permuted unit vector: apply the row swaps in order */
+            double *e = (double *)calloc(2 * n, sizeof(double));
+            if (!e) {
+                free(x);
+#pragma omp atomic write
+                failed = 1;
+                continue;
+            }
+            e[2 * c] = 1.0;
+            for (long k = 0; k < n; ++k) {
+                long p = piv[k];
+                if (p != k) {
+                    double t0 = e[2 * k], t1 = e[2 * k + 1];
+                    e[2 * k] = e[2 * p];
+                    e[2 * k + 1] = e[2 * p + 1];
+                    e[2 * p] = t0;
+                    e[2 * p + 1] = t1;
+                }
+            }
+            /* forward: L y = e */
+            for (long r = 0; r < n; ++r) {
+                double sr = e[2 * r], si = e[2 * r + 1];
+                for (long k = 0; k < r; ++k) {
+                    double lr = a[2 * (r * n + k)], li = a[2 * (r * n + k) + 1];
+                    sr -= lr * x[2 * k] - li * x[2 * k + 1];
+                    si -= lr * x[2 * k + 1] + li * x[2 * k];
+                }
+                x[2 * r] = sr;
+                x[2 * r + 1] = si;
+            }
+            /* backward: U x = y */
+            for (long r = n - 1; r >= 0; --r) {
+                double sr = x[2 * r], si = x[2 * r + 1];
+                for (long k = r + 1; k < n; ++k) {
+                    double ur = a[2 * (r * n + k)], ui = a[2 * (r * n + k) + 1];
+                    sr -= ur * x[2 * k] - ui * x[2 * k + 1];
+                    si -= ur * x[2 * k + 1] + ui * x[2 * k];
+                }
+                double pr = a[2 * (r * n + r)], pi = a[2 * (r * n + r) + 1];
+                double den = pr * pr + pi * pi;
+                x[2 * r] = (sr * pr + si * pi) / den;
+                x[2 * r + 1] = (si * pr - sr * pi) / den;
+            }
+            for (long r = 0; r < n; ++r) {
+                ej[2 * (r * n + c)] = x[2 * r];
+                ej[2 * (r * n + c) + 1] = x[2 * r + 1];
+            }
+            free(e);
+            free(x);
+        }
+        /* W = eps^-1 v(q+G') */
+        for (long r = 0; r < n; ++r)
+            for (long c = 0; c < n; ++c) {
+                wj[2 * (r * n + c)] = ej[2 * (r * n + c)] * v[c];
+                wj[2 * (r * n + c) + 1] = ej[2 * (r * n + c) + 1] * v[c];
+            }
+    }
+    free(a);
+    free(piv);
+    return failed ? -1 : 0;
 }

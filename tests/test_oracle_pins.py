@@ -355,3 +355,93 @@ def test_q0_head_vanishes():
     i0 = int(np.where((geps == 0).all(1))[0][0])
     assert abs(chi[0, i0, i0]) < 1e-14 * np.abs(chi).max()
     assert abs(chi[0, i0]).max() < 1e-14 * np.abs(chi).max()
+
+
+# ---------------------------------------------------------------------------
+# Dielectric matrix, eps^-1 and W (Sec. II: eps = delta - v(q+G) P,
+# W = eps^-1 v(q+G')), v(q+G) = 4 pi e^2 / (Omega |q+G|^2) in eV.
+E2 = 27.211386245988   # e^2 in eV bohr
+
+
+def test_coulomb_simple_cubic_closed_form():
+    a = 2.0                                   # bohr; B = (2 pi / a) I = pi I, Omega = 8
+    q = [0.5, 0.0, 0.0]
+    g = np.array([[0, 0, 0], [1, 0, 0], [-1, 2, 0], [0, 0, 3]])
+    k2 = np.pi ** 2 * np.array([0.25, 2.25, 0.25 + 4.0, 0.25 + 9.0])
+    want = 4 * np.pi * E2 / (8.0 * k2)
+    assert np.allclose(oracle.coulomb(a * np.eye(3), q, g), want, rtol=1e-14)
+
+
+def test_coulomb_fcc_against_independent_reciprocal_and_head():
+    from paper_2206_00808_gb300 import synthetic as syn
+    a = 10.26
+    avec = syn.fcc_cell(a)
+    omega = a ** 3 / 4                        # FCC primitive cell volume
+    B = 2 * np.pi * np.linalg.inv(np.asarray(avec)).T
+    rng = np.random.default_rng(3)
+    g = rng.integers(-4, 5, (40, 3))
+    q = np.array([0.25, -0.125, 0.0])
+    k = (q + g) @ B
+    want = 4 * np.pi * E2 / (omega * (k * k).sum(1))
+    assert np.allclose(oracle.coulomb(avec, q, g), want, rtol=1e-13)
+    # q + G = 0: v is defined as 0 there
+    assert oracle.coulomb(avec, [0, 0, 0], [[0, 0, 0], [1, 0, 0]])[0] == 0.0
+
+
+def _nsd_chi(rng, n, nf, rank=None):
+    chis = []
+    for _ in range(nf):
+        X = rng.normal(size=(n, rank or n)) + 1j * rng.normal(size=(n, rank or n))
+        chis.append(-(X @ X.conj().T) * 0.05)
+    return np.array(chis)
+
+
+def test_epsinv_is_the_inverse_of_eps_and_w_is_hermitian():
+    rng = np.random.default_rng(5)
+    n = 23
+    chi = _nsd_chi(rng, n, 3)
+    v = rng.uniform(0.2, 3.0, n)
+    e, w = oracle.epsinv(chi, v)
+    for j in range(3):
+        eps = np.eye(n) - v[:, None] * chi[j]
+        assert np.abs(e[j] @ eps - np.eye(n)).max() < 1e-12
+        assert np.abs(eps @ e[j] - np.eye(n)).max() < 1e-12
+        assert np.abs(w[j] - w[j].conj().T).max() < 1e-12 * np.abs(w[j]).max()
+        # eps is similar to I + (PSD), so its eigenvalues are real and >= 1
+        ev = np.linalg.eigvals(eps)
+        assert np.abs(ev.imag).max() < 1e-10 and ev.real.min() > 1 - 1e-12
+
+
+def test_epsinv_diagonal_closed_form():
+    n = 6
+    d = -np.linspace(0.1, 2.0, n)
+    v = np.linspace(0.5, 1.5, n)
+    e, w = oracle.epsinv(np.diag(d).astype(complex)[None], v)
+    assert np.allclose(np.diag(e[0]), 1 / (1 - v * d), rtol=1e-15)
+    assert np.allclose(np.diag(w[0]), v / (1 - v * d), rtol=1e-15)
+    assert np.abs(e[0] - np.diag(np.diag(e[0]))).max() == 0.0
+
+
+def test_w_rank_one_sherman_morrison():
+    """chi = -u u^H: eps = I + diag(v) u u^H, so
+    W = eps^-1 V = V - (V u)(V u)^H / (1 + u^H V u)."""
+    rng = np.random.default_rng(11)
+    n = 9
+    u = rng.normal(size=n) + 1j * rng.normal(size=n)
+    v = rng.uniform(0.1, 2.0, n)
+    chi = -np.outer(u, u.conj())[None]
+    _, w = oracle.epsinv(chi, v)
+    vu = v * u
+    want = np.diag(v) - np.outer(vu, vu.conj()) / (1 + (u.conj() * v * u).sum().real)
+    assert np.abs(w[0] - want).max() < 1e-13 * np.abs(want).max()
+
+
+def test_epsinv_head_row_is_identity_when_v_is_zero():
+    rng = np.random.default_rng(2)
+    n = 5
+    chi = _nsd_chi(rng, n, 1)
+    v = rng.uniform(0.5, 1.0, n)
+    v[0] = 0.0
+    e, w = oracle.epsinv(chi, v)
+    assert np.allclose(e[0][0], np.eye(n)[0], atol=1e-15)
+    assert np.abs(w[0][:, 0]).max() == 0.0
