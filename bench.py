@@ -403,6 +403,33 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     return res
 
 
+def epsinv_measure(B, torch, p, res, stream, reps=3):
+    """The step after chi0: W = eps^-1 v of every frequency of the first
+    q-point from the device chi0 of the last timed step (bgw_epsinv, FP64),
+    timed with CUDA events on the bench stream; FLOPs = 8 N_G^3 per matrix
+    (complex Gauss-Jordan inversion)."""
+    q, geps, _ = p.qs[0]
+    s = B.bgw_coulomb_sqrt(p.avec, q, geps)
+    chi = res["outs"][0]
+    nf, ng = chi.shape[0], chi.shape[1]
+    ws = torch.empty(B.bgw_epsinv_workspace_bytes(ng, nf), dtype=torch.uint8, device="cuda")
+    times = []
+    for _ in range(reps + 1):
+        t = chi.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.bgw_epsinv(t, s, "W", work=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times[1:])
+    tf = 8.0 * ng ** 3 * nf / (ms * 1e-3) / 1e12
+    return {"what": "W = eps^-1 v(q+G') for every frequency of one q (FP64, blocked Gauss-Jordan on "
+                    "the symmetrised eps)", "n_g": ng, "n_freq": nf, "ms_per_q": ms, "tflops": tf,
+            "peak_tflops": FP64_PEAK_TFLOPS, "roofline_frac": tf / FP64_PEAK_TFLOPS}
+
+
 def e2e_measure(B, torch, p, res, args, dist, stream):
     """Same step from pinned host buffers, chi0 read back to host."""
     ctx = res["ctx"]
@@ -490,6 +517,7 @@ def run_ours(args, world, rank, local):
                     "peak": sustained / 3, "unit": "TFLOP/s", "frac": achieved / (sustained / 3),
                     "traffic": traffic(args.workload, "k5_gemm", head_kchunk),
                     "peak_source": f"{src} BF16 sustained {sustained} / 3 products"}
+    epsinv = epsinv_measure(B, torch, p, head, stream) if args.precision == "fp64" else None
     e2e = None if args.no_e2e else e2e_measure(B, torch, p, head, args, dist, stream)
     check = None
     if args.precision == "mixed" and args.check_fp64 > 0:
@@ -568,7 +596,7 @@ def run_ours(args, world, rank, local):
                 "tflops": fl["total"] / (ms * 1e-3) / 1e12,
                 "pairs_per_s": value / nq * sum(p.pairs(i) for i in range(nq)),
                 "stages": head["stages"],
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "epsinv": epsinv,
                 "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
                 "tuning": head["tuning"], "fp64_check": check,
                 "mixed": other}

@@ -204,6 +204,41 @@ BGW_API bgw_status bgw_chi0_resume(bgw_ctx ctx, int nq, const bgw_q *qs, int nfr
                                    const void *buf, size_t bytes);
 
 /*
+ * Dielectric matrix inverse and screened interaction (the step after chi0:
+ * Sec. II, the two equations before the P formula,
+ *     eps_GG' = delta_GG' - v(q+G) P_GG',    W_GG' = eps^-1_GG' v(q+G')).
+ * The P formula prints no 1/Omega; here it is carried by the bare Coulomb
+ * interaction v(q+G) = 4 pi e^2 / (Omega |q+G|^2) (e^2 = 27.211386245988
+ * eV bohr), so that with chi0 from bgw_chi0_finalize (eV^-1) v chi0 is
+ * dimensionless and W is in eV.
+ *
+ * bgw_coulomb_sqrt: s[g] = sqrt(v(q + G_g)) in eV^1/2 for the Miller vectors
+ *   gvec[g][3] of the sphere, cell rows avec[3][3] (bohr, row i = a_i), q in
+ *   crystal coordinates; s = 0 where q + G = 0.  Host computation.
+ *   BGW_E_ARG for null pointers, ng < 1 or a singular cell.
+ * bgw_epsinv_workspace_bytes: device workspace bgw_epsinv needs.
+ * bgw_epsinv: for each of the nfreq matrices chi[j] (device, complex128
+ *   [nfreq][ng][ng], row G, column G'; overwritten) forms the Hermitian
+ *   eps~ = I - S chi S (S = diag(s), s on the host) and inverts it in FP64 on
+ *   the GPU (blocked Gauss-Jordan without pivoting: eps~ is positive definite
+ *   when chi is Hermitian negative semidefinite, as chi0 on the imaginary axis
+ *   is).  Output per mode: 0 eps~^-1; 1 W = S eps~^-1 S (eV); 2 the paper's
+ *   eps^-1 = S eps~^-1 S^-1 (needs every s > 0).  work: device workspace of
+ *   work_bytes >= bgw_epsinv_workspace_bytes(ng, nfreq) bytes, or NULL (the
+ *   call then allocates and frees it).  Runs on `stream` and waits for it.
+ *   BGW_E_ARG for bad sizes, s < 0 or non-finite, or when a pivot is not
+ *   positive (the input is not negative semidefinite; the output is then
+ *   invalid); BGW_E_NOMEM / BGW_E_CUDA on allocation or CUDA failure.
+ *   Errors are reported by bgw_last_error(NULL).  The paper has no
+ *   counterpart of the symmetrised form; it is the standard way to make the
+ *   inversion Hermitian positive definite.
+ */
+BGW_API bgw_status bgw_coulomb_sqrt(const double *avec, const double *q, int ng, const int *gvec, double *s);
+BGW_API size_t bgw_epsinv_workspace_bytes(int ng, int nfreq);
+BGW_API bgw_status bgw_epsinv(int ng, int nfreq, const double *s, void *chi, int mode, void *work,
+                              size_t work_bytes, void *stream);
+
+/*
  * CUDA-graph capture of a sequence of calls on this context (for repeated
  * identical steps, e.g. serving the same workload).  bgw_graph_begin starts
  * capturing the context stream (which must not be the legacy default

@@ -28,8 +28,8 @@ EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "
             "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",
             "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune",
             "bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch", "bgw_chi0_progress",
-            "bgw_chi0_checkpoint_bytes", "bgw_chi0_checkpoint", "bgw_chi0_resume", "bgw_destroy",
-            "bgw_last_error"]
+            "bgw_chi0_checkpoint_bytes", "bgw_chi0_checkpoint", "bgw_chi0_resume", "bgw_coulomb_sqrt",
+            "bgw_epsinv_workspace_bytes", "bgw_epsinv", "bgw_destroy", "bgw_last_error"]
 BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C, BGW_OPT_GRID_SLOTS = 1, 2, 3, 4
 BGW_OPT_TEST_DROP_LOAD, BGW_OPT_TEST_FAIL_ALLOC, BGW_OPT_K1_PATH = 5, 6, 7
 STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split"]
@@ -62,6 +62,11 @@ _lib.bgw_chi0_progress.argtypes = [_P, _P]
 _lib.bgw_chi0_checkpoint_bytes.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
 _lib.bgw_chi0_checkpoint.argtypes = [_P, _P, ctypes.c_size_t]
 _lib.bgw_chi0_resume.argtypes = [_P, _I, ctypes.POINTER(bgw_q), _I, _P, _P, ctypes.c_size_t]
+_lib.bgw_coulomb_sqrt.argtypes, _lib.bgw_coulomb_sqrt.restype = [_P, _P, _I, _P, _P], ctypes.c_int
+_lib.bgw_epsinv_workspace_bytes.argtypes = [_I, _I]
+_lib.bgw_epsinv_workspace_bytes.restype = ctypes.c_size_t
+_lib.bgw_epsinv.argtypes = [_I, _I, _P, _P, _I, _P, ctypes.c_size_t, _P]
+_lib.bgw_epsinv.restype = ctypes.c_int
 _lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
 _lib.bgw_last_error.argtypes, _lib.bgw_last_error.restype = [_P], ctypes.c_char_p
 for _f in ["bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
@@ -206,6 +211,33 @@ def bgw_chi0_resume(ctx, qs, freq, data: bytes) -> int:
     b = np.frombuffer(data, dtype=np.uint8)
     return _check(_lib.bgw_chi0_resume(ctx, len(structs), arr, len(f), _host_ptr(f), _host_ptr(b),
                                        len(b)), ctx)
+
+
+EPSINV_MODES = {"epsinv_sym": 0, "W": 1, "epsinv": 2}
+
+
+def bgw_coulomb_sqrt(avec, q, gvec) -> np.ndarray:
+    """sqrt(v(q+G)) in eV^1/2 for the sphere gvec (ng, 3), cell rows avec (bohr)."""
+    a = np.ascontiguousarray(np.asarray(avec, dtype=np.float64).reshape(9))
+    qq = np.ascontiguousarray(q, dtype=np.float64)
+    g = np.ascontiguousarray(gvec, dtype=np.int32)
+    s = np.zeros(len(g), dtype=np.float64)
+    _check(_lib.bgw_coulomb_sqrt(_host_ptr(a), _host_ptr(qq), len(g), _host_ptr(g), _host_ptr(s)), None)
+    return s
+
+
+def bgw_epsinv_workspace_bytes(ng: int, nfreq: int) -> int:
+    return int(_lib.bgw_epsinv_workspace_bytes(ng, nfreq))
+
+
+def bgw_epsinv(chi_dev, s, mode="W", work=None, stream=None) -> int:
+    """In place on the device tensor chi_dev (complex128 [nfreq][ng][ng]):
+    eps~^-1 ("epsinv_sym"), W ("W") or the paper's eps^-1 ("epsinv")."""
+    nf, ng = int(chi_dev.shape[0]), int(chi_dev.shape[1])
+    sv = np.ascontiguousarray(s, dtype=np.float64)
+    pw, wb = (None, 0) if work is None else (work.data_ptr(), work.numel() * work.element_size())
+    return _check(_lib.bgw_epsinv(ng, nf, _host_ptr(sv), ctypes.c_void_p(chi_dev.data_ptr()),
+                                  EPSINV_MODES[mode], ctypes.c_void_p(pw), wb, _stream_handle(stream)), None)
 
 
 def bgw_profile(ctx, enable: bool) -> int:

@@ -437,13 +437,14 @@ bgw::Axes mtxel_axes(const bgw_ctx_s *c, const QState &s, const int G0[3]) {
 // pairs, processed in batches of whole valence bands).
 cudaError_t ensure_mtxel_scratch(bgw_ctx_s *c, const QState &s, long P) {
     const long n01 = (long)c->box[0] * c->box[1];
+    const int G0z[3] = {0, 0, 0};
+    const bgw::Axes ax = mtxel_axes(c, s, G0z);
     if (P > 0) {
         const int nc = (int)(P / c->nv);
-        const int G0z[3] = {0, 0, 0};
-        const bgw::Axes ax = mtxel_axes(c, s, G0z);
         P = (long)bgw::mtxel_v_batch((int)(P / std::max(1, nc)), nc, ax, c->csize) * nc;
     }
-    cudaError_t e = c->A.ensure((size_t)(P * n01 * s.w[2]) * c->csize, c->st);
+    const long PA = bgw::mtxel_uses_a(ax) ? P : 0;
+    cudaError_t e = c->A.ensure((size_t)(PA * n01 * s.w[2]) * c->csize, c->st);
     if (e == cudaSuccess) e = c->Bs.ensure((size_t)(P * c->box[0] * s.w[1] * s.w[2]) * c->csize, c->st);
     return e;
 }

@@ -283,6 +283,81 @@ k2_zpass_c4(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, 
         }
 }
 
+// Pair density + z and y forward passes of one (pair, x-plane) per CTA for
+// the four-lane lengths: 64 quads of lanes; quad y forms the pair density of
+// z line y from the grids (both spin components) and transforms it, the kept
+// w2 outputs go to shared Zs[N][w2p]; then quad jz transforms y line jz of Zs
+// and writes the kept w1 outputs to Bs[p][x][w1][w2].  The z-pass output
+// never leaves the SM.  A warp whose four quads all lie past the last line
+// skips the iteration (lanes of a quad exchange values by warp shuffles, so
+// whole warps stay together).  grid (P, n0); N <= 64 lines per pass.
+constexpr int kZyC4Threads = 256;
+
+template <int N>
+__global__ void __launch_bounds__(kZyC4Threads, 2)
+k2_zy_c4(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, int w1, int w2, int s1, int s2,
+         C *__restrict__ Bs) {
+    static_assert(N <= 64, "one z line per quad");
+    extern __shared__ unsigned char zy_sm[];
+    C *Zs = reinterpret_cast<C *>(zy_sm);
+    constexpr int M = N / 4, Q = M / 4;
+    const int w2p = w2 | 1;
+    const long p = blockIdx.x;
+    const int x = blockIdx.y, n0 = gridDim.y;
+    const long v = p / nc, c = p % nc;
+    const long plane = (long)N * N, vol = (long)n0 * plane;
+    const int quad = threadIdx.x >> 2, t = threadIdx.x & 3;
+    const int warp_first_quad = (threadIdx.x >> 5) * 8;
+    {
+        const C *pv = Uv + (2 * v) * vol + x * plane;
+        const C *pc = Uc + (2 * c) * vol + x * plane;
+        if (warp_first_quad < N) {                     // warp-uniform
+            const int y = quad;
+            const bool valid = y < N;
+            const int yy = valid ? y : 0;
+            C a[M], out[4][Q];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const long o = (long)yy * N + 4 * m + t;
+                a[m] = rho2(pv[o], pc[o], pv[vol + o], pc[vol + o]);
+            }
+            fft_line_coop4<T, -1, N>(a, t, out);
+            if (valid) {
+                const int ns = N - s2;
+#pragma unroll
+                for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+                    for (int j = 0; j < Q; ++j) {
+                        const int jj = rot<N>(t * Q + j + M * k1, ns);
+                        if (jj < w2) Zs[y * w2p + jj] = out[k1][j];
+                    }
+            }
+        }
+    }
+    __syncthreads();
+    for (int base = 0; base < w2; base += kZyC4Threads / 4) {
+        if (base + warp_first_quad >= w2) break;       // warp-uniform
+        const int jz = base + quad;
+        const bool valid = jz < w2;
+        const int jc = valid ? jz : 0;
+        C a[M], out[4][Q];
+#pragma unroll
+        for (int m = 0; m < M; ++m) a[m] = Zs[(4 * m + t) * w2p + jc];
+        fft_line_coop4<T, -1, N>(a, t, out);
+        if (valid) {
+            const int ns = N - s1;
+            C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    const int jj = rot<N>(t * Q + j + M * k1, ns);
+                    if (jj < w1) bo[jj * w2] = out[k1][j];
+                }
+        }
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(kLineThreads)
 k2_ypass_c4(const C *__restrict__ A, long npx, int w1, int w2, int s1, C *__restrict__ Bs) {
@@ -660,6 +735,9 @@ static bool use_coop(const Axes &a) {
            a.n[1] % 16 == 0 && a.n[2] % 16 == 0;
 }
 
+// The fused z+y four-lane kernel: cubic box (one z line per quad), N <= 64.
+static bool use_zy_c4(const Axes &a) { return a.n[0] == a.n[1] && a.n[1] == a.n[2] && a.n[0] <= 64; }
+
 static inline unsigned quads_for(long lines) { return (unsigned)((4 * lines + kLineThreads - 1) / kLineThreads); }
 
 #define BGW_FOR_EACH_COOP_LEN(n, ...)                                                 \
@@ -799,12 +877,18 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
     }
     const size_t psmem = TV > 0 ? plane_smem(TV, TC, a.n[1], a.w[2]) : 0;
     if (use_coop(a)) {
-        const long plane = (long)a.n[0] * a.n[1];
-        BGW_FOR_EACH_COOP_LEN(a.n[2], (k2_zpass_c4<N><<<quads_for(P * plane), kLineThreads, 0, st>>>(
-                                          uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
-        const long npx = P * a.n[0];
-        BGW_FOR_EACH_COOP_LEN(a.n[1], (k2_ypass_c4<N><<<quads_for(npx * a.w[2]), kLineThreads, 0, st>>>(
-                                          Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
+        if (use_zy_c4(a)) {
+            const size_t zs = sizeof(C) * (size_t)a.n[1] * (a.w[2] | 1);
+            BGW_FOR_EACH_COOP_LEN(a.n[2], (k2_zy_c4<N><<<dim3((unsigned)P, (unsigned)a.n[0]), kZyC4Threads, zs,
+                                                         st>>>(uv, uc, nc, a.w[1], a.w[2], a.s[1], a.s[2], Bp)));
+        } else {
+            const long plane = (long)a.n[0] * a.n[1];
+            BGW_FOR_EACH_COOP_LEN(a.n[2], (k2_zpass_c4<N><<<quads_for(P * plane), kLineThreads, 0, st>>>(
+                                              uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
+            const long npx = P * a.n[0];
+            BGW_FOR_EACH_COOP_LEN(a.n[1], (k2_ypass_c4<N><<<quads_for(npx * a.w[2]), kLineThreads, 0, st>>>(
+                                              Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
+        }
         const long lines = (long)a.w[1] * a.w[2];
         const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
         BGW_FOR_EACH_COOP_LEN(a.n[0], (k2_xpass_scatter_c4<N><<<quads_for(P * lines), kLineThreads, 0, st>>>(

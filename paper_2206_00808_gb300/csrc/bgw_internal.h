@@ -54,11 +54,21 @@ inline bool mtxel_scatter_mode(const Axes &a, size_t csize) {
     return long_lines || (size_t)a.w[0] * a.w[1] * a.w[2] * csize > (size_t)64 * 1024;
 }
 
+// Whether the matrix-element kernels keep the z-pass output in the global
+// scratch A: every path but the fused z+y four-lane kernel (cubic boxes of
+// N = 48 or 64), which keeps it in shared memory.
+inline bool mtxel_uses_a(const Axes &a) {
+    const bool four_lane = a.n[0] >= 48 && a.n[1] >= 48 && a.n[2] >= 48 && a.n[0] % 16 == 0 &&
+                           a.n[1] % 16 == 0 && a.n[2] % 16 == 0;
+    const bool cubic = a.n[0] == a.n[1] && a.n[1] == a.n[2];
+    return !(four_lane && cubic && a.n[0] <= 64);
+}
+
 // Valence bands per batch of the matrix-element kernels: their scratch
-// (A + Bs per pair) stays under 1 GiB.
+// (A, where used, + Bs per pair) stays under 1 GiB.
 inline int mtxel_v_batch(int nv, int nc, const Axes &a, size_t csize) {
     const size_t per_pair =
-        csize * ((size_t)a.n[0] * a.n[1] * a.w[2] + (size_t)a.n[0] * a.w[1] * a.w[2]);
+        csize * ((mtxel_uses_a(a) ? (size_t)a.n[0] * a.n[1] * a.w[2] : 0) + (size_t)a.n[0] * a.w[1] * a.w[2]);
     const size_t cap = (size_t)1 << 30;
     size_t vb = cap / (per_pair * (size_t)(nc > 0 ? nc : 1) + 1);
     if (vb < 1) vb = 1;

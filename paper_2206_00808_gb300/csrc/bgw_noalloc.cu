@@ -119,7 +119,7 @@ extern "C" bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv,
     const long P = (long)nv * nc;
     const long PB = (long)bgw::mtxel_v_batch(nv, nc, ax, 16) * nc;   // pairs per kernel batch
     const size_t gbytes = round_up(sizeof(int) * (size_t)nmap);
-    const size_t abytes = round_up((size_t)PB * fft[0] * fft[1] * ax.w[2] * 16);
+    const size_t abytes = bgw::mtxel_uses_a(ax) ? round_up((size_t)PB * fft[0] * fft[1] * ax.w[2] * 16) : 0;
     const size_t bbytes = round_up((size_t)PB * fft[0] * ax.w[1] * ax.w[2] * 16);
     const size_t need = gbytes + abytes + bbytes;
     if (need > (size_t)BGW_NOALLOC_SCRATCH_BYTES)

@@ -71,3 +71,25 @@ def test_null_context_calls_are_rejected(lib):
     assert so.bgw_chi0_reset(None) == lib.BGW_E_ARG
     assert so.bgw_chi0_finalize(None, 0, None, 0) == lib.BGW_E_ARG
     so.bgw_destroy(None)
+
+
+def test_coulomb_sqrt_host_matches_oracle():
+    """bgw_coulomb_sqrt is a host computation: checked here without a GPU."""
+    import oracle
+    from paper_2206_00808_gb300 import binding as B
+    from paper_2206_00808_gb300 import synthetic as syn
+    p = syn.make_problem("si18_qx")
+    q, geps, _ = p.qs[0]
+    s = B.bgw_coulomb_sqrt(p.avec, q, geps)
+    v = oracle.coulomb(p.avec, q, geps)
+    assert np.allclose(s ** 2, v, rtol=1e-13, atol=0)
+
+
+def test_epsinv_argument_errors_without_gpu():
+    from paper_2206_00808_gb300 import binding as B
+    rc = B._lib.bgw_epsinv(0, 1, None, None, 1, None, 0, None)
+    assert rc == B.BGW_E_ARG
+    s = np.array([-1.0])
+    rc = B._lib.bgw_epsinv(1, 1, B._host_ptr(s), B.ctypes.c_void_p(16), 1, None, 0, None)
+    assert rc == B.BGW_E_ARG
+    assert b"finite" in B._lib.bgw_last_error(None)
