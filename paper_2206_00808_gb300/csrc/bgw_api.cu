@@ -282,16 +282,17 @@ cudaError_t run_k1(bgw_ctx_s *c, int ik, const double *src, int slot) {
     int w[3];
     for (int a = 0; a < 3; ++a) w[a] = kp.hi[a] - kp.lo[a] + 1;
     const size_t sbytes = (size_t)B * c->box[0] * w[1] * w[2] * c->csize;
-    const size_t rbytes = (size_t)B * c->box[0] * c->box[1] * w[2] * c->csize;
-    cudaError_t e = c->S.ensure(sbytes, c->st);
-    if (e == cudaSuccess) e = c->R.ensure(rbytes, c->st);
-    if (e != cudaSuccess) return e;
     bgw::Axes ax;
     for (int a = 0; a < 3; ++a) {
         ax.n[a] = c->box[a];
         ax.w[a] = w[a];
         ax.s[a] = pmod(kp.lo[a], c->box[a]);
     }
+    const size_t rbytes =
+        bgw::wfn_uses_r(ax, c->csize) ? (size_t)B * c->box[0] * c->box[1] * w[2] * c->csize : 0;
+    cudaError_t e = c->S.ensure(sbytes, c->st);
+    if (e == cudaSuccess) e = c->R.ensure(rbytes, c->st);
+    if (e != cudaSuccess) return e;
     void *U = c->slot_ptr(slot, 0);
     const int *mp = static_cast<const int *>(kp.map_dev.p);
     const int rec = c->stage_begin(0);

@@ -17,7 +17,7 @@
 // has been taken the array holds the inverse.  Each step is four launches:
 // k6_diag (one CTA per matrix inverts the kb x kb block in shared memory),
 // k6_panels (P A_KR and A_RK P into a workspace), k6_update (the rank-kb
-// update of all (r, c) outside K, tiled 64 x 64 in shared memory: this is
+// update of all (r, c) outside K, tiled 32 x 32 in shared memory: this is
 // where the 8 n^3 flops per matrix go, on the FP64 pipe), k6_writeback.
 // All matrices of a call (one per frequency) go through each launch together.
 #include <cuda_runtime.h>
@@ -30,7 +30,7 @@
 namespace {
 
 constexpr int kB = 32;           // Gauss-Jordan block
-constexpr int kTile = 64;        // update tile (rows and columns)
+constexpr int kTile = 32;        // update tile (rows and columns): many CTAs per panel step
 constexpr int kErrPivot = 1;
 
 struct Z {
@@ -111,11 +111,16 @@ __global__ void __launch_bounds__(256) k6_diag(double2 *__restrict__ A, int n, i
 
 // T[j][i][c] = sum_k P[i][k] A[k0+k][c]   (row panel, every column c)
 // U[j][r][i] = sum_k A[r][k0+k] P[k][i]   (column panel, every row r)
-// with P = A_KK already inverted in place.  grid (ceil(n/128), 2, nf).
+// with P = A_KK already inverted in place.  Each thread computes kPanelI
+// consecutive i for one column (or row) x.  grid (ceil(n/128), kB/kPanelI,
+// 2 nf): z even for T, odd for U.
+constexpr int kPanelI = 8;
+
 __global__ void __launch_bounds__(128) k6_panels(const double2 *__restrict__ A, int n, int k0, int kb,
                                                  double2 *__restrict__ T, double2 *__restrict__ U) {
     __shared__ Z P[kB][kB + 1];
-    const long j = blockIdx.z;
+    const long j = blockIdx.z >> 1;
+    const bool row_panel = (blockIdx.z & 1) == 0;
     const double2 *M = A + j * (long)n * n;
     for (int i = threadIdx.x; i < kb * kb; i += blockDim.x) {
         const double2 v = M[(long)(k0 + i / kb) * n + k0 + i % kb];
@@ -123,42 +128,44 @@ __global__ void __launch_bounds__(128) k6_panels(const double2 *__restrict__ A, 
     }
     __syncthreads();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= n) return;
-    Z acc[kB];
+    const int i0 = blockIdx.y * kPanelI;
+    if (x >= n || i0 >= kb) return;
+    Z acc[kPanelI];
 #pragma unroll
-    for (int i = 0; i < kB; ++i) acc[i] = {0.0, 0.0};
-    if (blockIdx.y == 0) {                                // column c = x of P A_K.
+    for (int i = 0; i < kPanelI; ++i) acc[i] = {0.0, 0.0};
+    if (row_panel) {                                      // column c = x of P A_K.
         for (int k = 0; k < kb; ++k) {
             const double2 v = M[(long)(k0 + k) * n + x];
             const Z b = {v.x, v.y};
 #pragma unroll
-            for (int i = 0; i < kB; ++i)
-                if (i < kb) acc[i] = zfma(P[i][k], b, acc[i]);
+            for (int i = 0; i < kPanelI; ++i)
+                if (i0 + i < kb) acc[i] = zfma(P[i0 + i][k], b, acc[i]);
         }
         double2 *t = T + j * (long)kB * n + x;
 #pragma unroll
-        for (int i = 0; i < kB; ++i)
-            if (i < kb) t[(long)i * n] = make_double2(acc[i].x, acc[i].y);
+        for (int i = 0; i < kPanelI; ++i)
+            if (i0 + i < kb) t[(long)(i0 + i) * n] = make_double2(acc[i].x, acc[i].y);
     } else {                                              // row r = x of A_.K P
         const double2 *row = M + (long)x * n + k0;
         for (int k = 0; k < kb; ++k) {
             const double2 v = row[k];
             const Z a = {v.x, v.y};
 #pragma unroll
-            for (int i = 0; i < kB; ++i)
-                if (i < kb) acc[i] = zfma(a, P[k][i], acc[i]);
+            for (int i = 0; i < kPanelI; ++i)
+                if (i0 + i < kb) acc[i] = zfma(a, P[k][i0 + i], acc[i]);
         }
-        double2 *u = U + (j * (long)n + x) * kB;
+        double2 *u = U + (j * (long)n + x) * kB + i0;
 #pragma unroll
-        for (int i = 0; i < kB; ++i)
-            if (i < kb) u[i] = make_double2(acc[i].x, acc[i].y);
+        for (int i = 0; i < kPanelI; ++i)
+            if (i0 + i < kb) u[i] = make_double2(acc[i].x, acc[i].y);
     }
 }
 
 // A[r][c] -= sum_k A[r][k0+k] T[k][c] for r, c outside [k0, k0+kb).
-// One CTA per 64 x 64 tile (rows r0.., columns c0..) of one matrix; 256
-// threads, each a 4 x 4 block of complex outputs; outputs in the K rows or
-// K columns are computed and dropped.
+// One CTA per 32 x 32 tile (rows r0.., columns c0..) of one matrix; 256
+// threads, each a 2 x 2 block of complex outputs (small tiles keep every SM
+// busy at N_G of a few hundred); outputs in the K rows or K columns are
+// computed and dropped.
 constexpr int kLRow = kB + 1, kRRow = kTile + 1;
 constexpr size_t kUpdateSmem = sizeof(Z) * ((size_t)kTile * kLRow + (size_t)kB * kRRow);
 
@@ -190,29 +197,30 @@ __global__ void __launch_bounds__(256) k6_update(double2 *__restrict__ A, int n,
         R[k][c] = v;
     }
     __syncthreads();
+    constexpr int RA = kTile / 16;                              // outputs per thread per axis
     const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;   // rows tr + 16a, columns tc + 16b
-    Z acc[4][4];
+    Z acc[RA][RA];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = {0.0, 0.0};
+        for (int b = 0; b < RA; ++b) acc[a][b] = {0.0, 0.0};
     for (int k = 0; k < kb; ++k) {
-        Z l[4], r[4];
+        Z l[RA], r[RA];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) l[a] = L[tr + 16 * a][k];
+        for (int a = 0; a < RA; ++a) l[a] = L[tr + 16 * a][k];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) r[b] = R[k][tc + 16 * b];
+        for (int b = 0; b < RA; ++b) r[b] = R[k][tc + 16 * b];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < RA; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = zfma(l[a], r[b], acc[a][b]);
+            for (int b = 0; b < RA; ++b) acc[a][b] = zfma(l[a], r[b], acc[a][b]);
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < RA; ++a) {
         const int r = r0 + tr + 16 * a;
         if (r >= n || (r >= k0 && r < k0 + kb)) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < RA; ++b) {
             const int c = c0 + tc + 16 * b;
             if (c >= n || (c >= k0 && c < k0 + kb)) continue;
             double2 *o = M + (long)r * n + c;
@@ -308,7 +316,7 @@ extern "C" bgw_status bgw_epsinv(int ng, int nfreq, const double *s, void *chi, 
     };
     if (ng < 1 || nfreq < 1 || !s || !chi) return fail(BGW_E_ARG, "epsinv: ng, nfreq >= 1 and s, chi required");
     if (mode < 0 || mode > 2) return fail(BGW_E_ARG, "epsinv: mode must be 0 (eps~^-1), 1 (W) or 2 (eps^-1)");
-    if (nfreq > 65535 || ng > 65535) return fail(BGW_E_ARG, "epsinv: ng and nfreq must be <= 65535");
+    if (nfreq > 32767 || ng > 65535) return fail(BGW_E_ARG, "epsinv: ng <= 65535 and nfreq <= 32767 required");
     for (int g = 0; g < ng; ++g) {
         if (!(s[g] >= 0.0) || !std::isfinite(s[g])) return fail(BGW_E_ARG, "epsinv: s must be finite and >= 0");
         if (mode == 2 && s[g] == 0.0) return fail(BGW_E_ARG, "epsinv: mode 2 needs s > 0 (q + G = 0 in the sphere)");
@@ -345,7 +353,7 @@ extern "C" bgw_status bgw_epsinv(int ng, int nfreq, const double *s, void *chi, 
     for (int k0 = 0; k0 < ng && e == cudaSuccess; k0 += kB) {
         const int kb = ng - k0 < kB ? ng - k0 : kB;
         k6_diag<<<nfreq, 256, 0, st>>>(A, ng, k0, kb, err);
-        k6_panels<<<dim3((ng + 127) / 128, 2, nfreq), 128, 0, st>>>(A, ng, k0, kb, T, U);
+        k6_panels<<<dim3((ng + 127) / 128, kB / kPanelI, 2 * nfreq), 128, 0, st>>>(A, ng, k0, kb, T, U);
         k6_update<<<dim3(tiles, tiles, nfreq), 256, kUpdateSmem, st>>>(A, ng, k0, kb, T);
         k6_writeback<<<dim3((ng + 127) / 128, 1, nfreq), 128, 0, st>>>(A, ng, k0, kb, T, U);
         e = cudaGetLastError();

@@ -286,4 +286,48 @@ __device__ __forceinline__ void fft_line_coop4(cpx<T> (&a)[N / 4], int t, cpx<T>
     }
 }
 
+// ---------------------------------------------- eight lanes per line (N = 8M) --
+// Lanes t = 0..7 of an aligned group of eight transform one line of length
+// N = 8M (M = 6 or 8) together, exchanging through shared memory:
+//   lane t enters with a[m] = x[8m + t], m < M;
+//   Y_t[k2] = sum_m x[8m + t] w_M^{m k2}            (M-point DFT in registers)
+//   Y_t[k2] *= w_N^{t k2}                           (lane twiddles, tw[k2])
+//   ex[k2][t] = Y_t[k2]                             (8 x 9 padded shared block)
+//   lane k2 < M: X[k2 + M k1] = sum_t Y_t[k2] w_8^{t k1}   (8-point DFT)
+// and leaves with out[k1] = X[t + M k1] (meaningful for t < M).  The row pad
+// of 9 keeps both the column writes and the row reads free of bank conflicts
+// for two groups per half-warp when groups sit 72 entries apart.  Every lane
+// of the warp must call this together (it synchronises the warp).
+constexpr int kOctRow = 9;
+constexpr int kOctBlock = 8 * kOctRow;
+
+// tw[k2] = w_N^{S t k2} for this lane (computed once per kernel).
+template <typename T, int S, int N>
+__device__ __forceinline__ void oct_twiddles(int t, cpx<T> (&tw)[N / 8]) {
+#pragma unroll
+    for (int k2 = 0; k2 < N / 8; ++k2) {
+        cpx<T> w = Tw<T>::at(tw_offset(N) + (t * k2) % N);
+        if (S > 0) w.y = -w.y;
+        tw[k2] = w;
+    }
+}
+
+template <typename T, int S, int N>
+__device__ __forceinline__ void fft_line_oct(cpx<T> (&a)[N / 8], int t, cpx<T> *ex,
+                                             const cpx<T> (&tw)[N / 8], cpx<T> (&out)[8]) {
+    static_assert(fft_len_supported(N) && N % 8 == 0 && N / 8 <= 8, "eight-lane FFT: N = 8M, M <= 8");
+    constexpr int M = N / 8;
+    Fft<T, S, M, N>::run(a);
+#pragma unroll
+    for (int k2 = 1; k2 < M; ++k2) a[k2] = cmul(a[k2], tw[k2]);
+#pragma unroll
+    for (int k2 = 0; k2 < M; ++k2) ex[k2 * kOctRow + t] = a[k2];
+    __syncwarp();
+    const int r = t < M ? t : 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) out[i] = ex[r * kOctRow + i];
+    __syncwarp();
+    Fft<T, S, 8, N>::run(out);
+}
+
 }  // namespace bgw

@@ -283,77 +283,205 @@ k2_zpass_c4(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, 
         }
 }
 
-// Pair density + z and y forward passes of one (pair, x-plane) per CTA for
-// the four-lane lengths: 64 quads of lanes; quad y forms the pair density of
-// z line y from the grids (both spin components) and transforms it, the kept
-// w2 outputs go to shared Zs[N][w2p]; then quad jz transforms y line jz of Zs
-// and writes the kept w1 outputs to Bs[p][x][w1][w2].  The z-pass output
-// never leaves the SM.  A warp whose four quads all lie past the last line
-// skips the iteration (lanes of a quad exchange values by warp shuffles, so
-// whole warps stay together).  grid (P, n0); N <= 64 lines per pass.
-constexpr int kZyC4Threads = 256;
+// Threads of the eight-lane kernels below: 32 groups of eight lanes.
+constexpr int kOctThreads = 256;
 
+// Pair density + z and y forward passes of one (pair, x-plane) per CTA for
+// the eight-lane lengths (48, 64): group y of eight lanes forms the pair
+// density of z line y from the grids (both spin components) and transforms
+// it (fft_line_oct); the kept w2 outputs go to shared Zs[N][w2p]; then group
+// jz transforms y line jz of Zs and writes the kept w1 outputs to
+// Bs[p][x][w1][w2].  The z-pass output never leaves the SM.  Each group has
+// its own 8 x 9 exchange block after Zs.  Lane t handles z = 8m + t on the
+// way in and the outputs f = t + (N/8) k1 on the way out.  A warp whose four
+// groups all lie past the last line skips the iteration (the lanes of a warp
+// synchronise inside the transform).  grid (P, n0).
 template <int N>
-__global__ void __launch_bounds__(kZyC4Threads, 2)
-k2_zy_c4(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, int w1, int w2, int s1, int s2,
-         C *__restrict__ Bs) {
-    static_assert(N <= 64, "one z line per quad");
+__global__ void __launch_bounds__(kOctThreads, 2)
+k2_zy_oct(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, int w1, int w2, int s1, int s2,
+          C *__restrict__ Bs) {
     extern __shared__ unsigned char zy_sm[];
-    C *Zs = reinterpret_cast<C *>(zy_sm);
-    constexpr int M = N / 4, Q = M / 4;
+    constexpr int M = N / 8, G = kOctThreads / 8;      // groups per CTA
     const int w2p = w2 | 1;
+    C *Zs = reinterpret_cast<C *>(zy_sm);
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7;
+    C *ex = Zs + ((N * w2p + 1) & ~1) + grp * kOctBlock;
+    const int warp_first_grp = (threadIdx.x >> 5) * 4;
+    C tw[M];
+    oct_twiddles<T, -1, N>(t, tw);
     const long p = blockIdx.x;
     const int x = blockIdx.y, n0 = gridDim.y;
     const long v = p / nc, c = p % nc;
     const long plane = (long)N * N, vol = (long)n0 * plane;
-    const int quad = threadIdx.x >> 2, t = threadIdx.x & 3;
-    const int warp_first_quad = (threadIdx.x >> 5) * 8;
-    {
-        const C *pv = Uv + (2 * v) * vol + x * plane;
-        const C *pc = Uc + (2 * c) * vol + x * plane;
-        if (warp_first_quad < N) {                     // warp-uniform
-            const int y = quad;
-            const bool valid = y < N;
-            const int yy = valid ? y : 0;
-            C a[M], out[4][Q];
+    const C *pv = Uv + (2 * v) * vol + x * plane;
+    const C *pc = Uc + (2 * c) * vol + x * plane;
+    const int ns2 = N - s2, ns1 = N - s1;
+    for (int y0 = 0; y0 < N; y0 += G) {
+        if (y0 + warp_first_grp >= N) break;            // warp-uniform
+        const int y = y0 + grp;
+        const bool valid = y < N;
+        const long row = (long)(valid ? y : 0) * N;
+        C a[M], out[8];
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const long o = (long)yy * N + 4 * m + t;
-                a[m] = rho2(pv[o], pc[o], pv[vol + o], pc[vol + o]);
-            }
-            fft_line_coop4<T, -1, N>(a, t, out);
-            if (valid) {
-                const int ns = N - s2;
+        for (int m = 0; m < M; ++m) {
+            const long o = row + 8 * m + t;
+            a[m] = rho2(pv[o], pc[o], pv[vol + o], pc[vol + o]);
+        }
+        fft_line_oct<T, -1, N>(a, t, ex, tw, out);
+        if (valid && t < M) {
 #pragma unroll
-                for (int k1 = 0; k1 < 4; ++k1)
-#pragma unroll
-                    for (int j = 0; j < Q; ++j) {
-                        const int jj = rot<N>(t * Q + j + M * k1, ns);
-                        if (jj < w2) Zs[y * w2p + jj] = out[k1][j];
-                    }
+            for (int k1 = 0; k1 < 8; ++k1) {
+                const int jj = rot<N>(t + M * k1, ns2);
+                if (jj < w2) Zs[y * w2p + jj] = out[k1];
             }
         }
     }
     __syncthreads();
-    for (int base = 0; base < w2; base += kZyC4Threads / 4) {
-        if (base + warp_first_quad >= w2) break;       // warp-uniform
-        const int jz = base + quad;
+    for (int base = 0; base < w2; base += G) {
+        if (base + warp_first_grp >= w2) break;          // warp-uniform
+        const int jz = base + grp;
         const bool valid = jz < w2;
         const int jc = valid ? jz : 0;
-        C a[M], out[4][Q];
+        C a[M], out[8];
 #pragma unroll
-        for (int m = 0; m < M; ++m) a[m] = Zs[(4 * m + t) * w2p + jc];
-        fft_line_coop4<T, -1, N>(a, t, out);
-        if (valid) {
-            const int ns = N - s1;
+        for (int m = 0; m < M; ++m) a[m] = Zs[(8 * m + t) * w2p + jc];
+        fft_line_oct<T, -1, N>(a, t, ex, tw, out);
+        if (valid && t < M) {
             C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
 #pragma unroll
-            for (int k1 = 0; k1 < 4; ++k1)
+            for (int k1 = 0; k1 < 8; ++k1) {
+                const int jj = rot<N>(t + M * k1, ns1);
+                if (jj < w1) bo[jj * w2] = out[k1];
+            }
+        }
+    }
+}
+
+// Last forward pass with eight lanes per line: Bs[p][x][w1][w2] -> M through
+// the inverse map (cube cell -> G index or -1).  One group per (pair, y'z'
+// line); 32 groups per CTA.
+template <int N>
+__global__ void __launch_bounds__(kOctThreads)
+k2_xpass_scatter_oct(const C *__restrict__ Bs, long P, int w0, int w1, int w2, int s0,
+                     const int *__restrict__ imap, T scale, C *__restrict__ Mo, long ldm) {
+    __shared__ C exs[(kOctThreads / 8) * kOctBlock];
+    constexpr int M = N / 8;
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7;
+    C *ex = exs + grp * kOctBlock;
+    C tw[M];
+    oct_twiddles<T, -1, N>(t, tw);
+    const long lines = (long)w1 * w2;
+    long line = (long)blockIdx.x * (kOctThreads / 8) + grp;
+    const bool valid = line < P * lines;
+    if (!valid) line = 0;
+    const long l = line % lines, p = line / lines;
+    C a[M], out[8];
 #pragma unroll
-                for (int j = 0; j < Q; ++j) {
-                    const int jj = rot<N>(t * Q + j + M * k1, ns);
-                    if (jj < w1) bo[jj * w2] = out[k1][j];
-                }
+    for (int m = 0; m < M; ++m) a[m] = Bs[(p * N + 8 * m + t) * lines + l];
+    fft_line_oct<T, -1, N>(a, t, ex, tw, out);
+    if (!valid || t >= M) return;
+    const int ns = N - s0;
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        const int jj = rot<N>(t + M * k1, ns);
+        if (jj < w0) {
+            const int g = __ldg(imap + jj * lines + l);
+            if (g >= 0) Mo[p * ldm + g] = C{out[k1].x * scale, out[k1].y * scale};
+        }
+    }
+}
+
+// Sphere -> grid for the eight-lane lengths (48, 64): x lines of the cube
+// (gathered through the cube map) into S[b][n0][w1][w2], then one CTA per
+// (band component, x-plane) for the y lines (into shared Ys[N][w2p]) and the
+// z lines (written to the grid).  grid of k1_xpass_oct: groups of eight.
+template <int N>
+__global__ void __launch_bounds__(kOctThreads)
+k1_xpass_oct(const double2 *__restrict__ coeff, int ngw, long B, const int *__restrict__ cube_map, int w0,
+             int w1, int w2, int s0, C *__restrict__ S) {
+    __shared__ C exs[(kOctThreads / 8) * kOctBlock];
+    constexpr int M = N / 8;
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7;
+    C *ex = exs + grp * kOctBlock;
+    C tw[M];
+    oct_twiddles<T, +1, N>(t, tw);
+    const long yzs = (long)w1 * w2;
+    long line = (long)blockIdx.x * (kOctThreads / 8) + grp;
+    const bool valid = line < B * yzs;
+    if (!valid) line = 0;
+    const long yz = line % yzs, b = line / yzs;
+    const int ns = N - s0;
+    C a[M], out[8];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int j = rot<N>(8 * m + t, ns);
+        C v = {T(0), T(0)};
+        if (j < w0) {
+            const int idx = __ldg(cube_map + j * yzs + yz);
+            if (idx >= 0) {
+                const double2 c = __ldg(coeff + b * ngw + idx);
+                v = {(T)c.x, (T)c.y};
+            }
+        }
+        a[m] = v;
+    }
+    fft_line_oct<T, +1, N>(a, t, ex, tw, out);
+    if (!valid || t >= M) return;
+    C *o = S + b * N * yzs + yz;
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) o[(t + M * k1) * yzs] = out[k1];
+}
+
+template <int N>
+__global__ void __launch_bounds__(kOctThreads, 2)
+k1_yz_oct(const C *__restrict__ S, int w1, int w2, int s1, int s2, C *__restrict__ U) {
+    extern __shared__ unsigned char yz_sm[];
+    constexpr int M = N / 8, G = kOctThreads / 8;
+    const int w2p = w2 | 1;
+    C *Ys = reinterpret_cast<C *>(yz_sm);
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7;
+    C *ex = Ys + ((N * w2p + 1) & ~1) + grp * kOctBlock;
+    const int warp_first_grp = (threadIdx.x >> 5) * 4;
+    C tw[M];
+    oct_twiddles<T, +1, N>(t, tw);
+    const long b = blockIdx.x;
+    const int x = blockIdx.y, n0 = gridDim.y;
+    const C *si = S + ((b * n0 + x) * w1) * (long)w2;
+    const int ns1 = N - s1, ns2 = N - s2;
+    for (int base = 0; base < w2; base += G) {
+        if (base + warp_first_grp >= w2) break;          // warp-uniform
+        const int jz = base + grp;
+        const bool valid = jz < w2;
+        const int jc = valid ? jz : 0;
+        C a[M], out[8];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int j = rot<N>(8 * m + t, ns1);
+            a[m] = (j < w1) ? si[j * w2 + jc] : C{T(0), T(0)};
+        }
+        fft_line_oct<T, +1, N>(a, t, ex, tw, out);
+        if (valid && t < M) {
+#pragma unroll
+            for (int k1 = 0; k1 < 8; ++k1) Ys[(t + M * k1) * w2p + jz] = out[k1];
+        }
+    }
+    __syncthreads();
+    C *uo = U + (b * n0 + x) * (long)N * N;
+    for (int y0 = 0; y0 < N; y0 += G) {
+        if (y0 + warp_first_grp >= N) break;             // warp-uniform
+        const int y = y0 + grp;
+        const bool valid = y < N;
+        const int yc = valid ? y : 0;
+        C a[M], out[8];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int j = rot<N>(8 * m + t, ns2);
+            a[m] = (j < w2) ? Ys[yc * w2p + j] : C{T(0), T(0)};
+        }
+        fft_line_oct<T, +1, N>(a, t, ex, tw, out);
+        if (valid && t < M) {
+#pragma unroll
+            for (int k1 = 0; k1 < 8; ++k1) uo[(long)y * N + t + M * k1] = out[k1];
         }
     }
 }
@@ -735,8 +863,8 @@ static bool use_coop(const Axes &a) {
            a.n[1] % 16 == 0 && a.n[2] % 16 == 0;
 }
 
-// The fused z+y four-lane kernel: cubic box (one z line per quad), N <= 64.
-static bool use_zy_c4(const Axes &a) { return a.n[0] == a.n[1] && a.n[1] == a.n[2] && a.n[0] <= 64; }
+// The eight-lane kernels: cubic boxes of the four-lane lengths (48, 64).
+static bool use_oct(const Axes &a) { return a.n[0] == a.n[1] && a.n[1] == a.n[2] && a.n[0] <= 64; }
 
 static inline unsigned quads_for(long lines) { return (unsigned)((4 * lines + kLineThreads - 1) / kLineThreads); }
 
@@ -773,6 +901,23 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
         const long lines = nb * a.w[1] * a.w[2];
         BGW_FOR_EACH_LEN(a.n[0], (k1_xpass<N><<<blocks_for(lines), kLineThreads, 0, st>>>(
                                      cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
+    }
+    if (use_coop(a) && use_oct(a)) {
+        const long groups = nb * a.w[1] * a.w[2];
+        BGW_FOR_EACH_COOP_LEN(a.n[0], (k1_xpass_oct<N><<<(unsigned)((groups + 31) / 32), kOctThreads, 0, st>>>(
+                                          cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
+        const size_t ys = sizeof(C) * ((((size_t)a.n[1] * (a.w[2] | 1)) + 1) / 2 * 2 +
+                                       (size_t)(kOctThreads / 8) * kOctBlock);
+        cudaError_t e = cudaSuccess;
+        BGW_FOR_EACH_COOP_LEN(a.n[1], {
+            if (ys > 48 * 1024) {
+                e = cudaFuncSetAttribute(k1_yz_oct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys);
+                if (e != cudaSuccess) return e;
+            }
+            k1_yz_oct<N><<<dim3((unsigned)nb, (unsigned)a.n[0]), kOctThreads, ys, st>>>(Sp, a.w[1], a.w[2], a.s[1],
+                                                                                          a.s[2], Up);
+        });
+        return cudaGetLastError();
     }
     if (use_plane_kernels(a)) {
         const int n = a.n[1];
@@ -877,10 +1022,25 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
     }
     const size_t psmem = TV > 0 ? plane_smem(TV, TC, a.n[1], a.w[2]) : 0;
     if (use_coop(a)) {
-        if (use_zy_c4(a)) {
-            const size_t zs = sizeof(C) * (size_t)a.n[1] * (a.w[2] | 1);
-            BGW_FOR_EACH_COOP_LEN(a.n[2], (k2_zy_c4<N><<<dim3((unsigned)P, (unsigned)a.n[0]), kZyC4Threads, zs,
-                                                         st>>>(uv, uc, nc, a.w[1], a.w[2], a.s[1], a.s[2], Bp)));
+        if (use_oct(a)) {
+            const size_t zs = sizeof(C) * ((((size_t)a.n[1] * (a.w[2] | 1)) + 1) / 2 * 2 +
+                                           (size_t)(kOctThreads / 8) * kOctBlock);
+            cudaError_t e = cudaSuccess;
+            BGW_FOR_EACH_COOP_LEN(a.n[2], {
+                if (zs > 48 * 1024) {
+                    e = cudaFuncSetAttribute(k2_zy_oct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs);
+                    if (e != cudaSuccess) return e;
+                }
+                k2_zy_oct<N><<<dim3((unsigned)P, (unsigned)a.n[0]), kOctThreads, zs, st>>>(
+                    uv, uc, nc, a.w[1], a.w[2], a.s[1], a.s[2], Bp);
+            });
+            const long lines = (long)a.w[1] * a.w[2];
+            const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
+            const long groups = P * lines;
+            BGW_FOR_EACH_COOP_LEN(a.n[0], (k2_xpass_scatter_oct<N><<<(unsigned)((groups + 31) / 32), kOctThreads,
+                                                                      0, st>>>(Bp, P, a.w[0], a.w[1], a.w[2], a.s[0],
+                                                                               gmap + ng, scale, Mp, ldm)));
+            return cudaGetLastError();
         } else {
             const long plane = (long)a.n[0] * a.n[1];
             BGW_FOR_EACH_COOP_LEN(a.n[2], (k2_zpass_c4<N><<<quads_for(P * plane), kLineThreads, 0, st>>>(

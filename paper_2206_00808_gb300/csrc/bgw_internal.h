@@ -64,6 +64,16 @@ inline bool mtxel_uses_a(const Axes &a) {
     return !(four_lane && cubic && a.n[0] <= 64);
 }
 
+// Whether wfn_to_grid may need the y-pass scratch R: only the one-line-per-
+// thread pass kernels use it (FP64 boxes that the one-kernel transform does
+// not take, and non-square FP32 boxes); the eight-lane kernels (cubic 48 and
+// 64) and the FP32 square-plane kernels keep it on chip.
+inline bool wfn_uses_r(const Axes &a, size_t csize) {
+    if (!mtxel_uses_a(a)) return false;
+    const bool fp32_square = csize == 8 && a.n[1] == a.n[2] && a.n[0] < 48 && a.n[1] < 48;
+    return !fp32_square;
+}
+
 // Valence bands per batch of the matrix-element kernels: their scratch
 // (A, where used, + Bs per pair) stays under 1 GiB.
 inline int mtxel_v_batch(int nv, int nc, const Axes &a, size_t csize) {
