@@ -41,6 +41,9 @@ WORKLOADS = {
     "bi2se3": ("bi2se3", "Bi2Se3-like rhombohedral cell (hex a=4.143 A, c=28.636 A), 64^3 box, "
                          "N_w~9000 per spinor component, N_G=2000, N_k=216 (6x6x6), N_v=48, N_c=1000, "
                          "8 imaginary freqs, q=(1/6,0,0); real-space grids streamed through 8 slots"),
+    # profiling case: the 64^3 box and N_G = 2000 on a 2x2x2 k-grid with 8 + 40 bands (~1.5 GB)
+    "bi2se3_small": ("bi2se3_small", "Bi2Se3-like cell, 64^3 box, N_G=2000, 2x2x2 k-grid, N_v=8, N_c=40, "
+                                     "2 freqs, q=(1/2,0,0)"),
 }
 METRIC = "spinor chi0 q-points/s and TFLOP/s, FP64 vs mixed at ≤2e-5 rel. Frobenius error"
 
@@ -87,8 +90,11 @@ def parse_args():
     ap.add_argument("--grid-slots", type=int, default=-1,
                     help="real-space grid slots (0 = all k resident; default 8 for bi2se3, else 0)")
     ap.add_argument("--kchunk", type=int, default=0, help="k-chunk when not autotuning")
-    ap.add_argument("--k1-path", type=int, default=0, choices=[0, 1, 2],
-                    help="sphere -> grid kernels: 0 automatic, 1 per axis, 2 one kernel per band component")
+    ap.add_argument("--k1-path", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="sphere -> grid kernels: 0 automatic, 1 per axis, 2 one kernel per band component, "
+                         "3 eight lanes per line (cubic 32/40/48/64)")
+    ap.add_argument("--mtxel-lanes", type=int, default=0, choices=[0, 1, 8],
+                    help="FFT lanes per line of the matrix-element kernels (0 automatic)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")
     ap.add_argument("--alu-peaks", action="store_true",
                     help="only time cuBLAS FP64 and FP32 (no TF32) GEMMs of 8192^3 through torch.matmul "
@@ -274,6 +280,8 @@ def make_workload(name):
         return syn.make_batched_problem(), desc
     if over == "bi2se3":
         return syn.make_bi2se3_problem(), desc
+    if over == "bi2se3_small":
+        return syn.make_bi2se3_problem(kgrid=(2, 2, 2), nv=8, nc=40, q=(0.5, 0, 0), nfreq=2), desc
     if isinstance(over, str):
         return syn.make_problem(over), desc
     return syn.make_problem("si24", **over), desc
@@ -334,6 +342,8 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk)
     if args.k1_path > 0:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_K1_PATH, args.k1_path)
+    if args.mtxel_lanes > 0:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_MTXEL_LANES, args.mtxel_lanes)
     ctx.upload(device_inputs=dev_in)
     tune_span = min(p.nk, 16 if precision == "mixed" else 4)
     tuning = ctx.autotune(0, tune_span) if not args.no_autotune else None

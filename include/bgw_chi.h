@@ -280,7 +280,14 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        bgw_wfn_upload: 0 automatic (default), 1 one kernel
  *                        per axis, 2 one kernel for the whole transform of a
  *                        band component where the box fits in shared memory
- *                        (else as 1).  All give the same grids up to rounding.
+ *                        (else as 1), 3 eight lanes per FFT line where the box
+ *                        is cubic with N = 32, 40, 48 or 64 (else automatic).
+ *                        All give the same grids up to rounding.
+ *   BGW_OPT_MTXEL_LANES  FFT lanes per line of the matrix-element kernels:
+ *                        0 automatic (default: eight for cubic 48 and 64 boxes,
+ *                        one elsewhere), 1 one, 8 eight where the box is cubic
+ *                        with N = 32, 40, 48 or 64.  Same results up to
+ *                        rounding.
  *   BGW_OPT_TEST_FAIL_ALLOC for failure-handling tests only: when n > 0, the
  *                        n-th device allocation made by the library from now on
  *                        (by any context of the process) fails as if the device
@@ -295,7 +302,8 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        reports as BGW_E_TIMEOUT.  No fault, trap or hang.
  */
 enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
-       BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7 };
+       BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7,
+       BGW_OPT_MTXEL_LANES = 8 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

@@ -177,6 +177,7 @@ struct bgw_ctx_s {
     int tile_v = 0, tile_c = 0;   // pair tile of the FP32 plane kernel (0 = automatic)
     int test_drop_load = 0;       // BGW_OPT_TEST_DROP_LOAD
     int k1_path = 0;              // BGW_OPT_K1_PATH
+    int mtxel_lanes = 0;          // BGW_OPT_MTXEL_LANES
     // k-points summed into the running sum (accumulate calls made since the
     // q-set was installed; replays of a captured graph are not counted)
     std::vector<int> kcount;
@@ -463,8 +464,8 @@ cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const in
     const int *gmap = static_cast<const int *>(s.gmap_dev.p);
     const int rec = c->stage_begin(1);
     cudaError_t e = (c->prec == BGW_FP64)
-        ? bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st)
-        : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, tv, tc);
+        ? bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, 0, 0, c->mtxel_lanes)
+        : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, tv, tc, c->mtxel_lanes);
     c->stage_end(rec, 3);
     return e;
 }
@@ -1168,8 +1169,13 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
             c->test_drop_load = value != 0;
             return BGW_OK;
         case BGW_OPT_K1_PATH:
-            if (value < 0 || value > 2) return c->fail(BGW_E_ARG, "set_option: K1 path must be 0..2");
+            if (value < 0 || value > 3) return c->fail(BGW_E_ARG, "set_option: K1 path must be 0..3");
             c->k1_path = (int)value;
+            return BGW_OK;
+        case BGW_OPT_MTXEL_LANES:
+            if (value != 0 && value != 1 && value != 8)
+                return c->fail(BGW_E_ARG, "set_option: matrix-element lanes must be 0, 1 or 8");
+            c->mtxel_lanes = (int)value;
             return BGW_OK;
         case BGW_OPT_TEST_FAIL_ALLOC:
             if (value < 0) return c->fail(BGW_E_ARG, "set_option: allocation count must be >= 0");
@@ -1196,6 +1202,7 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_TEST_DROP_LOAD: *value = c->test_drop_load; return BGW_OK;
         case BGW_OPT_TEST_FAIL_ALLOC: *value = g_fail_alloc.load(); return BGW_OK;
         case BGW_OPT_K1_PATH: *value = c->k1_path; return BGW_OK;
+        case BGW_OPT_MTXEL_LANES: *value = c->mtxel_lanes; return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }

@@ -11,7 +11,7 @@ cudaError_t wfn_to_grid_f64(const double *coeff, int ngw, int B, const int *cube
 }
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv, int tc) {
-    return f64::mtxel(Uv, Uc, nv, nc, a, gmap, ng, A, Bs, M, ldm, st, tv, tc);
+                      cudaStream_t st, int tv, int tc, int lanes) {
+    return f64::mtxel(Uv, Uc, nv, nc, a, gmap, ng, A, Bs, M, ldm, st, tv, tc, lanes);
 }
 }  // namespace bgw

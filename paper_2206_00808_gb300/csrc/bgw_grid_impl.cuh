@@ -865,8 +865,23 @@ static bool use_coop(const Axes &a) {
 
 // The eight-lane kernels: cubic boxes of the four-lane lengths (48, 64).
 static bool use_oct(const Axes &a) { return a.n[0] == a.n[1] && a.n[1] == a.n[2] && a.n[0] <= 64; }
+// Cubic boxes the eight-lane kernels can take at all (N = 8M, 4 <= M <= 8);
+// automatically chosen only for the four-lane lengths, on request for 32, 40.
+static bool oct_len(const Axes &a) {
+    const int n = a.n[0];
+    return a.n[1] == n && a.n[2] == n && (n == 32 || n == 40 || n == 48 || n == 64);
+}
 
 static inline unsigned quads_for(long lines) { return (unsigned)((4 * lines + kLineThreads - 1) / kLineThreads); }
+
+#define BGW_FOR_EACH_OCT_LEN(n, ...)                                                  \
+    switch (n) {                                                                      \
+        case 32: { constexpr int N = 32; __VA_ARGS__; } break;                        \
+        case 40: { constexpr int N = 40; __VA_ARGS__; } break;                        \
+        case 48: { constexpr int N = 48; __VA_ARGS__; } break;                        \
+        case 64: { constexpr int N = 64; __VA_ARGS__; } break;                        \
+        default: return cudaErrorInvalidValue;                                        \
+    }
 
 #define BGW_FOR_EACH_COOP_LEN(n, ...)                                                 \
     switch (n) {                                                                      \
@@ -881,7 +896,8 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
     C *Sp = static_cast<C *>(S), *Rp = static_cast<C *>(R), *Up = static_cast<C *>(U);
     const double2 *cf = reinterpret_cast<const double2 *>(coeff);
     const int *inv = cube_map + (long)a.w[0] * a.w[1] * a.w[2];
-    if (const int KP = path == 1 ? 0 : fused_planes(a, path == 2 ? kFusedSmemMax : kFusedSmemAuto)) {
+    const bool oct = oct_len(a) && (path == 3 || (use_coop(a) && use_oct(a)));
+    if (const int KP = (path == 1 || oct) ? 0 : fused_planes(a, path == 2 ? kFusedSmemMax : kFusedSmemAuto)) {
         const size_t smem = fused_smem(a, KP);
         cudaError_t e = cudaSuccess;
         BGW_FOR_EACH_LEN(a.n[0], {
@@ -902,14 +918,14 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
         BGW_FOR_EACH_LEN(a.n[0], (k1_xpass<N><<<blocks_for(lines), kLineThreads, 0, st>>>(
                                      cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
     }
-    if (use_coop(a) && use_oct(a)) {
+    if (oct) {
         const long groups = nb * a.w[1] * a.w[2];
-        BGW_FOR_EACH_COOP_LEN(a.n[0], (k1_xpass_oct<N><<<(unsigned)((groups + 31) / 32), kOctThreads, 0, st>>>(
-                                          cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
+        BGW_FOR_EACH_OCT_LEN(a.n[0], (k1_xpass_oct<N><<<(unsigned)((groups + 31) / 32), kOctThreads, 0, st>>>(
+                                         cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
         const size_t ys = sizeof(C) * ((((size_t)a.n[1] * (a.w[2] | 1)) + 1) / 2 * 2 +
                                        (size_t)(kOctThreads / 8) * kOctBlock);
         cudaError_t e = cudaSuccess;
-        BGW_FOR_EACH_COOP_LEN(a.n[1], {
+        BGW_FOR_EACH_OCT_LEN(a.n[1], {
             if (ys > 48 * 1024) {
                 e = cudaFuncSetAttribute(k1_yz_oct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys);
                 if (e != cudaSuccess) return e;
@@ -1008,8 +1024,42 @@ static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int 
 
 static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const Axes &a,
                                const int *gmap, int ng, C *Ap, C *Bp, C *Mp, long ldm,
-                               cudaStream_t st, int tv_req, int tc_req) {
+                               cudaStream_t st, int tv_req, int tc_req, int lanes) {
     const long P = (long)nv * nc;
+    if (oct_len(a) && (lanes == 8 || (lanes == 0 && use_coop(a) && use_oct(a)))) {
+        // eight lanes per line: fused z+y, then the x pass
+        const size_t zs = sizeof(C) * ((((size_t)a.n[1] * (a.w[2] | 1)) + 1) / 2 * 2 +
+                                       (size_t)(kOctThreads / 8) * kOctBlock);
+        cudaError_t e = cudaSuccess;
+        BGW_FOR_EACH_OCT_LEN(a.n[2], {
+            if (zs > 48 * 1024) {
+                e = cudaFuncSetAttribute(k2_zy_oct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs);
+                if (e != cudaSuccess) return e;
+            }
+            k2_zy_oct<N><<<dim3((unsigned)P, (unsigned)a.n[0]), kOctThreads, zs, st>>>(
+                uv, uc, nc, a.w[1], a.w[2], a.s[1], a.s[2], Bp);
+        });
+        const long lines = (long)a.w[1] * a.w[2];
+        const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
+        if (mtxel_scatter_mode(a, sizeof(C))) {
+            const long groups = P * lines;
+            BGW_FOR_EACH_OCT_LEN(a.n[0], (k2_xpass_scatter_oct<N><<<(unsigned)((groups + 31) / 32), kOctThreads,
+                                                                     0, st>>>(Bp, P, a.w[0], a.w[1], a.w[2], a.s[0],
+                                                                              gmap + ng, scale, Mp, ldm)));
+            return cudaGetLastError();
+        }
+        const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
+        BGW_FOR_EACH_LEN(a.n[0], {
+            if (smem > 48 * 1024) {
+                e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            k2_xpass_gather<N><<<(unsigned)P, kLineThreads, smem, st>>>(
+                Bp, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
+        });
+        return cudaGetLastError();
+    }
     int TV = 0, TC = 0;
     if (use_plane_kernels(a)) {
         const size_t budget = plane_smem(1, 1, a.n[1], a.w[2]) <= kPlaneSmemMax ? kPlaneSmemMax : kPlaneSmemLarge;
@@ -1021,34 +1071,13 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         }
     }
     const size_t psmem = TV > 0 ? plane_smem(TV, TC, a.n[1], a.w[2]) : 0;
-    if (use_coop(a)) {
-        if (use_oct(a)) {
-            const size_t zs = sizeof(C) * ((((size_t)a.n[1] * (a.w[2] | 1)) + 1) / 2 * 2 +
-                                           (size_t)(kOctThreads / 8) * kOctBlock);
-            cudaError_t e = cudaSuccess;
-            BGW_FOR_EACH_COOP_LEN(a.n[2], {
-                if (zs > 48 * 1024) {
-                    e = cudaFuncSetAttribute(k2_zy_oct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs);
-                    if (e != cudaSuccess) return e;
-                }
-                k2_zy_oct<N><<<dim3((unsigned)P, (unsigned)a.n[0]), kOctThreads, zs, st>>>(
-                    uv, uc, nc, a.w[1], a.w[2], a.s[1], a.s[2], Bp);
-            });
-            const long lines = (long)a.w[1] * a.w[2];
-            const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
-            const long groups = P * lines;
-            BGW_FOR_EACH_COOP_LEN(a.n[0], (k2_xpass_scatter_oct<N><<<(unsigned)((groups + 31) / 32), kOctThreads,
-                                                                      0, st>>>(Bp, P, a.w[0], a.w[1], a.w[2], a.s[0],
-                                                                               gmap + ng, scale, Mp, ldm)));
-            return cudaGetLastError();
-        } else {
-            const long plane = (long)a.n[0] * a.n[1];
-            BGW_FOR_EACH_COOP_LEN(a.n[2], (k2_zpass_c4<N><<<quads_for(P * plane), kLineThreads, 0, st>>>(
-                                              uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
-            const long npx = P * a.n[0];
-            BGW_FOR_EACH_COOP_LEN(a.n[1], (k2_ypass_c4<N><<<quads_for(npx * a.w[2]), kLineThreads, 0, st>>>(
-                                              Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
-        }
+    if (use_coop(a)) {                                  // non-cubic boxes of the four-lane lengths
+        const long plane = (long)a.n[0] * a.n[1];
+        BGW_FOR_EACH_COOP_LEN(a.n[2], (k2_zpass_c4<N><<<quads_for(P * plane), kLineThreads, 0, st>>>(
+                                          uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
+        const long npx = P * a.n[0];
+        BGW_FOR_EACH_COOP_LEN(a.n[1], (k2_ypass_c4<N><<<quads_for(npx * a.w[2]), kLineThreads, 0, st>>>(
+                                          Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
         const long lines = (long)a.w[1] * a.w[2];
         const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
         BGW_FOR_EACH_COOP_LEN(a.n[0], (k2_xpass_scatter_c4<N><<<quads_for(P * lines), kLineThreads, 0, st>>>(
@@ -1101,7 +1130,7 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
 
 static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                          const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                         cudaStream_t st, int tv_req, int tc_req) {
+                         cudaStream_t st, int tv_req, int tc_req, int lanes) {
     if ((long)nv * nc == 0) return cudaSuccess;
     const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
     C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
@@ -1110,7 +1139,7 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
     for (int vb0 = 0; vb0 < nv; vb0 += VB) {
         const int nvb = nv - vb0 < VB ? nv - vb0 : VB;
         cudaError_t e = mtxel_batch(uv + (long)vb0 * 2 * vol, uc, nvb, nc, a, gmap, ng, Ap, Bp,
-                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req);
+                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req, lanes);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1118,6 +1147,7 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
 
 #undef BGW_FOR_EACH_LEN
 #undef BGW_FOR_EACH_COOP_LEN
+#undef BGW_FOR_EACH_OCT_LEN
 
 }  // namespace BGW_SUFFIX
 }  // namespace bgw

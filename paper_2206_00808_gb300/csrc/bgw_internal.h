@@ -23,7 +23,8 @@ cudaError_t grid_tables_init_f32();
 // -1 (cube origin at Miller index s, i.e. a.s = sphere minimum), followed by
 // the inverse map [ngw] -> cube cell; S: [B][n0][w1][w2], R: [B][n0][n1][w2]
 // scratch of T-complex; U: [B][n0][n1][n2] T-complex.  path: 0 automatic,
-// 1 the per-axis pass kernels, 2 the one-kernel transform where it fits.
+// 1 the per-axis pass kernels, 2 the one-kernel transform where it fits,
+// 3 the eight-lane kernels where the box is cubic with N = 32, 40, 48 or 64.
 cudaError_t wfn_to_grid_f64(const double *coeff, int ngw, int B, const int *cube_map,
                             const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path = 0);
 cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube_map,
@@ -36,14 +37,16 @@ cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube
 // a.w = kept widths; gmap[g] = j0*w1*w2 + j1*w2 + j2 (position in the kept
 // cube); A: [P][n0][n1][w2], Bs: [P][n0][w1][w2] scratch; M row stride ldm.
 // tv, tc: pair tile of the plane-fused FP32 kernel (0 = choose automatically).
+// lanes: 0 automatic; 8 eight lanes per line wherever the box is cubic with
+// N = 32, 40, 48 or 64 (automatic choice uses them for 48 and 64 only).
 // Pairs are processed in batches of mtxel_v_batch(...) valence bands x nc, so
 // A and Bs need room for that many pairs only.
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv = 0, int tc = 0);
+                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0);
 cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv = 0, int tc = 0);
+                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0);
 // The last forward pass gathers the kept w0*w1*w2 cube through shared memory
 // when it is small; a larger cube is written straight to M through an
 // inverse map (cube cell -> G index or -1) stored in the map buffer right
