@@ -281,7 +281,11 @@ def make_workload(name):
     if over == "bi2se3":
         return syn.make_bi2se3_problem(), desc
     if over == "bi2se3_small":
-        return syn.make_bi2se3_problem(kgrid=(2, 2, 2), nv=8, nc=40, q=(0.5, 0, 0), nfreq=2), desc
+        # generated on the host (torch CPU QR): profilers run this case, and the
+        # device QR's lazily loaded library is not found under them
+        p = syn.make_bi2se3_problem(kgrid=(2, 2, 2), nv=8, nc=40, q=(0.5, 0, 0), nfreq=2, device="cpu")
+        p.coeff = [c.numpy() for c in p.coeff]
+        return p, desc
     if isinstance(over, str):
         return syn.make_problem(over), desc
     return syn.make_problem("si24", **over), desc

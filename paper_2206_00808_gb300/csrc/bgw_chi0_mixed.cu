@@ -19,8 +19,11 @@
 // accumulator (the FP64 reduction across k blocks).
 //
 // Kernels:
-//   k5_split   M -> X planes [1 + nfreq][hi, lo][R][Kp] BF16 (K-major,
-//              zero padded to R = 128-multiple rows, Kp = 64-multiple pairs)
+//   k5_split   M -> X planes [1 + nfreq][hi, lo], each stored as tiles
+//              [R/128][Kp/64][128 rows][64 pairs] BF16 (K-major inside a tile,
+//              zero padded to R = 128-multiple rows, Kp = 64-multiple pairs):
+//              one 16 KB TMA box is one contiguous piece of memory, so the
+//              split writes and the GEMM loads whole DRAM pages
 //   k5_gemm    one CTA per (lower 128x128 tile of D, frequency): TMA loads
 //              (128B swizzle) into a 3-stage ring of 64 KB, one thread issues
 //              tcgen05.mma, all four warps drain TMEM and update chi in FP64.
@@ -53,7 +56,8 @@ constexpr uint64_t kWaitNs = 2000000000ull;          // a device-side wait gives
 constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
 
 // ------------------------------------------------------------ split kernel --
-// plane 0: A = X; plane 1 + j: B_j = w_j X.  Output [plane][hi|lo][R][Kp].
+// plane 0: A = X; plane 1 + j: B_j = w_j X.  Output [plane][hi|lo] of tiles
+// [R/128][Kp/64][128][64].
 // One CTA per (32 complex G = 64 real rows) x (64 pairs) block writes every
 // plane of that block: M is read once, the weights are converted to FP32
 // once per pair, and each thread stores 16 consecutive pairs of one row
@@ -95,15 +99,18 @@ k5_split(const float2 *__restrict__ M, int P, int ng, const double *__restrict__
         im[i * kSplitRow + tx] = v.y;
     }
     __syncthreads();
-    const int r = threadIdx.x % 64;                      // local real row: G = g0 + r/2, Re/Im = r&1
-    const int pq = (threadIdx.x / 64) * 16;              // first of this thread's 16 pairs
+    // four threads per row (16 pairs each): a warp stores 8 whole rows of the
+    // tile, 1 KB of contiguous memory
+    const int r = threadIdx.x / 4;                       // local real row: G = g0 + r/2, Re/Im = r&1
+    const int pq = (threadIdx.x % 4) * 16;               // first of this thread's 16 pairs
     const int row = 2 * g0 + r;
     const float *src = ((r & 1) ? im : re) + (r >> 1);
     float x[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) x[i] = src[(pq + i) * kSplitRow];
     const long planeElems = (long)R * Kp;
-    __nv_bfloat16 *base = X + (long)row * Kp + p0 + pq;
+    const long kblocks = Kp / kSplitP;                   // 64-pair blocks per row tile
+    __nv_bfloat16 *base = X + (((long)(row / 128) * kblocks + p0 / kSplitP) * 128 + row % 128) * kSplitP + pq;
     for (int plane = 0; plane <= nfreq; ++plane) {
         const float *wp = wt + (plane - 1) * kSplitP + pq;
         uint32_t h[8], l[8];
@@ -172,12 +179,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int x, int y, int z) {
+// One 128 x 64 tile (k-block kb, row tile rt, plane) of the tiled operand
+// layout: coordinates {0, 0, kb, rt, plane} of the 5-D map.
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap *map, uint32_t bar, int kb,
+                                              int rt, int plane) {
+    const int zero = 0;
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %3, %4, %5, %6}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(zero), "r"(kb), "r"(rt), "r"(plane)
         : "memory");
 }
 
@@ -335,7 +345,6 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
                 const Item w = decode(gp, item);
                 const CUtensorMap *map = &gp.map[w.q];
                 asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-                const int a_row = w.ti * kTileM, b_row = w.tj * kTileN;
                 const int bhi = 2 + 2 * w.j, blo = 3 + 2 * w.j;
                 for (int it = 0; it < w.nkb; ++it, ++pit) {
                     const int s = (int)(pit % kStages);
@@ -351,12 +360,11 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
                     }
                     const uint32_t st0 = ring + s * kStageBytes;
                     const uint32_t fb = smem_u32(&full_bar[s]);
-                    const int x = it * kBlockK;
                     mbar_expect_tx(fb, kStageBytes);
-                    tma_load_3d(st0, map, fb, x, a_row, 0);
-                    tma_load_3d(st0 + kTileBytes, map, fb, x, a_row, 1);
-                    tma_load_3d(st0 + 2 * kTileBytes, map, fb, x, b_row, bhi);
-                    tma_load_3d(st0 + 3 * kTileBytes, map, fb, x, b_row, blo);
+                    tma_load_tile(st0, map, fb, it, w.ti, 0);
+                    tma_load_tile(st0 + kTileBytes, map, fb, it, w.ti, 1);
+                    tma_load_tile(st0 + 2 * kTileBytes, map, fb, it, w.tj, bhi);
+                    tma_load_tile(st0 + 3 * kTileBytes, map, fb, it, w.tj, blo);
                 }
                 if (*(volatile int *)&abort_flag) break;
             }
@@ -595,12 +603,16 @@ cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaSt
         gp.kp[i] = (int)Kp;
         gp.ng[i] = qs[i].ng;
         gp.acc[i] = static_cast<double2 *>(qs[i].acc);
+        // tiled planes [plane][R/128][Kp/64][128][64]: a box is one whole tile
         const int planes = 2 * (1 + nfreq);
-        const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)planes};
-        const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
-        const cuuint32_t box[3] = {kBlockK, kTileM, 1};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        CUresult cr = g_encode(&gp.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, qs[i].ws, dims, strides,
+        const cuuint64_t tile = (cuuint64_t)kTileM * kBlockK * 2;
+        const cuuint64_t dims[5] = {(cuuint64_t)kBlockK, (cuuint64_t)kTileM, (cuuint64_t)(Kp / kBlockK),
+                                    (cuuint64_t)(R / kTileM), (cuuint64_t)planes};
+        const cuuint64_t strides[4] = {(cuuint64_t)kBlockK * 2, tile, tile * (cuuint64_t)(Kp / kBlockK),
+                                       tile * (cuuint64_t)(Kp / kBlockK) * (cuuint64_t)(R / kTileM)};
+        const cuuint32_t box[5] = {kBlockK, kTileM, 1, 1, 1};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        CUresult cr = g_encode(&gp.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, qs[i].ws, dims, strides,
                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;

@@ -295,9 +295,10 @@ constexpr int kOctThreads = 256;
 // its own 8 x 9 exchange block after Zs.  Lane t handles z = 8m + t on the
 // way in and the outputs f = t + (N/8) k1 on the way out.  A warp whose four
 // groups all lie past the last line skips the iteration (the lanes of a warp
-// synchronise inside the transform).  grid (P, n0).
+// synchronise inside the transform).  Three CTAs per SM (80 registers) hide
+// the latency of the grid loads.  grid (P, n0).
 template <int N>
-__global__ void __launch_bounds__(kOctThreads, 2)
+__global__ void __launch_bounds__(kOctThreads, 3)
 k2_zy_oct(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, int w1, int w2, int s1, int s2,
           C *__restrict__ Bs) {
     extern __shared__ unsigned char zy_sm[];
