@@ -63,8 +63,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch, from one ncu capture of the
 # full-size workload with that k-chunk (profiles/traffic_si24.md); valid for
 # the kernel sources they were taken on.  Keyed by (workload, kernel, k-chunk).
-TRAFFIC = {("si24", "k4_herk_f64", 16): 145.66e6 + 67.13e6,
-           ("si24", "k5_gemm", 16): 477.86e6 + 3.16e6}
+TRAFFIC = {("si24", "k4_herk_f64", 16): 145.66e6 + 67.13e6}
 
 
 def traffic(workload, kernel, kchunk):
