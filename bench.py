@@ -63,7 +63,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch, from one ncu capture of the
 # full-size workload with that k-chunk (profiles/traffic_si24.md); valid for
 # the kernel sources they were taken on.  Keyed by (workload, kernel, k-chunk).
-TRAFFIC = {("si24", "k4_herk_f64", 16): 145.66e6 + 67.13e6}
+TRAFFIC = {("si24", "k4_herk_f64", 4): 36.19e6 + 44.94e6,
+           ("si24", "k4_herk_f64", 16): 145.66e6 + 67.13e6,
+           ("si24", "k5_gemm", 16): 477.86e6 + 3.10e6}
 
 
 def traffic(workload, kernel, kchunk):
@@ -341,15 +343,22 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     ctx = B.Chi0Context(p, precision, stream)
     if args.grid_slots > 0:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_GRID_SLOTS, args.grid_slots)
-    if args.kchunk > 0:
-        B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk)
+    # FP64 has no tile to tune; its k-chunk is fixed at 4 k-points per launch
+    # (the fastest in the autotuner's timings on si24, and the configuration
+    # whose DRAM traffic was captured for the roofline line)
+    fixed_fp64 = precision == "fp64" and not args.no_autotune and args.kchunk == 0
+    if args.kchunk > 0 or fixed_fp64:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk if args.kchunk > 0 else min(4, p.nk))
     if args.k1_path > 0:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_K1_PATH, args.k1_path)
     if args.mtxel_lanes > 0:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_MTXEL_LANES, args.mtxel_lanes)
     ctx.upload(device_inputs=dev_in)
-    tune_span = min(p.nk, 16 if precision == "mixed" else 4)
-    tuning = ctx.autotune(0, tune_span) if not args.no_autotune else None
+    tune_span = min(p.nk, 16)
+    if fixed_fp64:
+        tuning = {"kchunk": min(4, p.nk), "pair_tile": [0, 0], "autotuned": False}
+    else:
+        tuning = ctx.autotune(0, tune_span) if not args.no_autotune else None
 
     def step():
         ctx.reset()

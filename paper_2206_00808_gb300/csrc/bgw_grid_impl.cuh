@@ -189,33 +189,54 @@ k2_ypass(const C *__restrict__ A, long npx, int w1, int w2, int s1, C *__restric
     }
 }
 
-// Pass x + gather: one block per pair; the kept w0*w1*w2 cube goes to shared
+// Pass x + gather: one block per PP pairs (so that the w1*w2 x lines of
+// all of them fill the block); each pair's kept w0*w1*w2 cube goes to shared
 // memory, then M[p][g] = cube[gmap[g]] / N^3.
+constexpr int kGatherThreads = 256;
+
 template <int N>
-__global__ void __launch_bounds__(kLineThreads)
-k2_xpass_gather(const C *__restrict__ Bs, int w0, int w1, int w2, int s0,
+__global__ void __launch_bounds__(kGatherThreads)
+k2_xpass_gather(const C *__restrict__ Bs, long P, int PP, int w0, int w1, int w2, int s0,
                 const int *__restrict__ gmap, int ng, T scale, C *__restrict__ M, long ldm) {
     extern __shared__ unsigned char smem_raw[];
-    C *cube = reinterpret_cast<C *>(smem_raw);
-    const long p = blockIdx.x;
-    const int lines = w1 * w2;
+    C *cube = reinterpret_cast<C *>(smem_raw);          // [PP][w0][w1][w2]
+    const long p0 = (long)blockIdx.x * PP;
+    const int np = (int)(P - p0 < PP ? P - p0 : PP);
+    const int lines = w1 * w2, csz = w0 * lines;
     const int ns = N - s0;
-    for (int l = threadIdx.x; l < lines; l += blockDim.x) {
+    for (int l = threadIdx.x; l < np * lines; l += kGatherThreads) {
+        const int pp = l / lines, ll = l % lines;
+        const C *bi = Bs + ((p0 + pp) * N) * lines + ll;
         C a[N];
 #pragma unroll
-        for (int x = 0; x < N; ++x) a[x] = Bs[(p * N + x) * lines + l];
+        for (int x = 0; x < N; ++x) a[x] = bi[x * lines];
         fft_line<T, -1, N>(a);
+        C *co = cube + pp * csz + ll;
 #pragma unroll
         for (int f = 0; f < N; ++f) {
             const int j = rot<N>(f, ns);
-            if (j < w0) cube[j * lines + l] = a[f];
+            if (j < w0) co[j * lines] = a[f];
         }
     }
     __syncthreads();
-    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-        const C v = cube[__ldg(gmap + g)];
-        M[p * ldm + g] = C{v.x * scale, v.y * scale};
+    for (int i = threadIdx.x; i < np * ng; i += kGatherThreads) {
+        const int pp = i / ng, g = i % ng;
+        const C v = cube[pp * csz + __ldg(gmap + g)];
+        M[(p0 + pp) * ldm + g] = C{v.x * scale, v.y * scale};
     }
+}
+
+// Pairs per CTA of k2_xpass_gather: enough x lines to fill its threads,
+// within 96 KB of kept cubes.
+static int gather_pairs(const Axes &a, long P) {
+    const int lines = a.w[1] * a.w[2];
+    const size_t csz = sizeof(C) * (size_t)a.w[0] * lines;
+    int pp = kGatherThreads / lines;
+    if (pp < 1) pp = 1;
+    if (pp > 8) pp = 8;
+    while (pp > 1 && (size_t)pp * csz > (size_t)96 * 1024) --pp;
+    if (pp > P) pp = (int)(P > 0 ? P : 1);
+    return pp;
 }
 
 // Pass x + scatter: one thread per (pair, line); every kept output goes to
@@ -1051,13 +1072,14 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         }
         const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
         BGW_FOR_EACH_LEN(a.n[0], {
-            if (smem > 48 * 1024) {
+            const int PP = gather_pairs(a, P);
+            if (smem * PP > 48 * 1024) {
                 e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)(smem * PP));
                 if (e != cudaSuccess) return e;
             }
-            k2_xpass_gather<N><<<(unsigned)P, kLineThreads, smem, st>>>(
-                Bp, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
+            k2_xpass_gather<N><<<(unsigned)((P + PP - 1) / PP), kGatherThreads, smem * PP, st>>>(
+                Bp, P, PP, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
         });
         return cudaGetLastError();
     }
@@ -1118,13 +1140,14 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         return cudaGetLastError();
     }
     BGW_FOR_EACH_LEN(a.n[0], {
-        if (smem > 48 * 1024) {
+        const int PP = gather_pairs(a, P);
+        if (smem * PP > 48 * 1024) {
             e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
+                                     (int)(smem * PP));
             if (e != cudaSuccess) return e;
         }
-        k2_xpass_gather<N><<<(unsigned)P, kLineThreads, smem, st>>>(
-            Bp, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
+        k2_xpass_gather<N><<<(unsigned)((P + PP - 1) / PP), kGatherThreads, smem * PP, st>>>(
+            Bp, P, PP, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
     });
     return cudaGetLastError();
 }
