@@ -332,6 +332,16 @@ def bf16_peaks():
         return 1900.0, 1700.0, "fallback"
 
 
+def measured_hbm_gbs():
+    """The measured copy rate (read + write bytes) of this machine, else the
+    fallback figure."""
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_clocks):
     """Time `args.steps` full steps of one precision; returns a dict.
 
@@ -452,6 +462,48 @@ def epsinv_measure(B, torch, p, res, stream, reps=3):
             "peak_tflops": FP64_PEAK_TFLOPS, "roofline_frac": tf / FP64_PEAK_TFLOPS}
 
 
+def unfold_measure(B, torch, p, dev_in, stream, reps=3):
+    """Spinor symmetry unfolding by one operation of the FCC lattice with a
+    fractional translation, on as many bands as the step uploads in all (the
+    band sets of every k-point, here on the sphere of k-point 0 in one call so
+    that one launch is timed, not 64 host round trips), timed with CUDA
+    events.  DRAM-bound: 64 bytes read and written per band, spin pair and
+    plane wave, against the measured copy rate."""
+    A = np.asarray(p.avec).T
+    Rc = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])   # 120 degrees about (1,1,1)
+    R_lat = np.rint(np.linalg.inv(A) @ Rc @ A).astype(np.int32)
+    tau = (0.25, 0.25, 0.25)
+    nb = sum(int(c.shape[0]) for c, _ in dev_in)
+    ngw = len(p.gvec[0])
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    cin = torch.randn((nb, 2, ngw), dtype=torch.complex128, device="cuda", generator=g)
+    cout = torch.empty_like(cin)
+    times = []
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.bgw_unfold_spinor(p.avec, R_lat, tau, p.gvec[0], cin, cout, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times[1:])
+    nbytes = 2 * cin.numel() * cin.element_size()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    hbm = measured_hbm_gbs()
+    # per band, spin pair and plane wave: the 2 x 2 complex product, 16 FP64
+    # fused multiply-adds (the phase is folded into U once per plane wave)
+    dfma = 16.0 * nb * ngw
+    dfma_peak = FP64_PEAK_TFLOPS * 1e12 / 2              # DFMA instructions per second
+    del cin, cout
+    return {"what": "c(G) -> U c(R^-1 G) e^{-iG.tau} (FP64), one launch over the bands of every k of the step",
+            "bands": nb, "plane_waves": ngw, "bytes": nbytes, "ms": ms, "gbs": gbs, "peak_gbs": hbm,
+            "hbm_frac": gbs / hbm if hbm else None,
+            "fp64_fma_per_s": dfma / (ms * 1e-3), "fp64_frac": dfma / (ms * 1e-3) / dfma_peak,
+            "bound": "alu (FP64): 16 DFMA per 64 bytes outruns the DRAM time on this part"}
+
+
 def e2e_measure(B, torch, p, res, args, dist, stream):
     """Same step from pinned host buffers, chi0 read back to host."""
     ctx = res["ctx"]
@@ -540,6 +592,7 @@ def run_ours(args, world, rank, local):
                     "traffic": traffic(args.workload, "k5_gemm", head_kchunk),
                     "peak_source": f"{src} BF16 sustained {sustained} / 3 products"}
     epsinv = epsinv_measure(B, torch, p, head, stream) if args.precision == "fp64" else None
+    unfold = unfold_measure(B, torch, p, dev_in, stream) if args.precision == "fp64" else None
     e2e = None if args.no_e2e else e2e_measure(B, torch, p, head, args, dist, stream)
     check = None
     if args.precision == "mixed" and args.check_fp64 > 0:
@@ -618,7 +671,7 @@ def run_ours(args, world, rank, local):
                 "tflops": fl["total"] / (ms * 1e-3) / 1e12,
                 "pairs_per_s": value / nq * sum(p.pairs(i) for i in range(nq)),
                 "stages": head["stages"],
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "epsinv": epsinv,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "epsinv": epsinv, "unfold": unfold,
                 "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
                 "tuning": head["tuning"], "fp64_check": check,
                 "mixed": other}

@@ -239,6 +239,43 @@ BGW_API bgw_status bgw_epsinv(int ng, int nfreq, const double *s, void *chi, int
                               size_t work_bytes, void *stream);
 
 /*
+ * Spinor symmetry unfolding (Sec. "Spinor wavefunctions and symmetries": the
+ * unfolding relation c_{n,k}(G) -> c~_{n,Rk}(R^-1 G) e^{-i G.tau}, the 2 x 2
+ * SU(2) spin rotation, and the axis/angle extraction by Markley's version of
+ * Shepperd's quaternion algorithm).  Lets a caller that stores states in the
+ * irreducible wedge build the states at symmetry-equivalent k-points on the
+ * GPU and upload them (bgw_wfn_upload with on_device = 1).
+ *
+ * bgw_symmetry_su2: for the operation rot_lat[3][3] (integers, row-major,
+ *   acting on crystal coordinates of r: r' = R_lat r + tau) of the cell
+ *   avec[3][3] (rows a_i, bohr): U[8] = row-major complex [2][2] (re, im)
+ *   of cos(theta/2) I - i sin(theta/2) n.sigma, the spin rotation whose
+ *   adjoint action turns spin vectors with the Cartesian rotation
+ *   A R_lat A^-1 (its proper part -R for det = -1); axis_angle[4] = (n_x,
+ *   n_y, n_z, theta), theta in [0, 2 pi].  Either output may be NULL.  Host
+ *   only.  BGW_E_ARG if R_lat is not unimodular or not a rotation of this
+ *   cell (R^T R != I to 1e-8).
+ * bgw_unfold_spinor: coefficients at Rk from those at k.  gvec_in[ngw][3]
+ *   (host) is the Miller list of the sphere at k; gvec_out[ngw][3] (host,
+ *   caller-owned) receives h'_i = R_lat^-T h_i, the sphere at Rk in the same
+ *   order.  c_in (device, complex128 [nb][2][ngw]) is read and c_out (device,
+ *   same shape, must not alias c_in) written on `stream`:
+ *       c_out[n][a][i] = e^{-2 pi i h'_i . tau} sum_b U[a][b] c_in[n][b][i],
+ *   tau[3] in crystal coordinates; the common phase e^{-i Rk.tau} of all
+ *   bands is dropped.  When Rk differs from the stored grid point k' by a
+ *   reciprocal vector G0 (Rk = k' + G0), the caller adds G0 to gvec_out
+ *   before uploading at k'.  gvec_out is written before the call returns;
+ *   c_out when the stream reaches the call.  Uses a stream-ordered device
+ *   allocation of 12 ngw bytes (the Miller list; the phases are formed on the
+ *   device).  BGW_E_ARG on bad arguments, as for
+ *   bgw_symmetry_su2, or aliasing; errors via bgw_last_error(NULL).
+ */
+BGW_API bgw_status bgw_symmetry_su2(const double *avec, const int *rot_lat, double *U, double *axis_angle);
+BGW_API bgw_status bgw_unfold_spinor(const double *avec, const int *rot_lat, const double *tau, int nb, int ngw,
+                                     const int *gvec_in, int *gvec_out, const void *c_in, void *c_out,
+                                     void *stream);
+
+/*
  * CUDA-graph capture of a sequence of calls on this context (for repeated
  * identical steps, e.g. serving the same workload).  bgw_graph_begin starts
  * capturing the context stream (which must not be the legacy default

@@ -29,7 +29,8 @@ EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "
             "bgw_mtxel_spinor_noalloc", "bgw_set_option", "bgw_get_option", "bgw_autotune",
             "bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch", "bgw_chi0_progress",
             "bgw_chi0_checkpoint_bytes", "bgw_chi0_checkpoint", "bgw_chi0_resume", "bgw_coulomb_sqrt",
-            "bgw_epsinv_workspace_bytes", "bgw_epsinv", "bgw_destroy", "bgw_last_error"]
+            "bgw_epsinv_workspace_bytes", "bgw_epsinv", "bgw_symmetry_su2", "bgw_unfold_spinor",
+            "bgw_destroy", "bgw_last_error"]
 BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C, BGW_OPT_GRID_SLOTS = 1, 2, 3, 4
 BGW_OPT_TEST_DROP_LOAD, BGW_OPT_TEST_FAIL_ALLOC, BGW_OPT_K1_PATH, BGW_OPT_MTXEL_LANES = 5, 6, 7, 8
 STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split"]
@@ -67,6 +68,9 @@ _lib.bgw_epsinv_workspace_bytes.argtypes = [_I, _I]
 _lib.bgw_epsinv_workspace_bytes.restype = ctypes.c_size_t
 _lib.bgw_epsinv.argtypes = [_I, _I, _P, _P, _I, _P, ctypes.c_size_t, _P]
 _lib.bgw_epsinv.restype = ctypes.c_int
+_lib.bgw_symmetry_su2.argtypes, _lib.bgw_symmetry_su2.restype = [_P, _P, _P, _P], ctypes.c_int
+_lib.bgw_unfold_spinor.argtypes = [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]
+_lib.bgw_unfold_spinor.restype = ctypes.c_int
 _lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
 _lib.bgw_last_error.argtypes, _lib.bgw_last_error.restype = [_P], ctypes.c_char_p
 for _f in ["bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
@@ -238,6 +242,31 @@ def bgw_epsinv(chi_dev, s, mode="W", work=None, stream=None) -> int:
     pw, wb = (None, 0) if work is None else (work.data_ptr(), work.numel() * work.element_size())
     return _check(_lib.bgw_epsinv(ng, nf, _host_ptr(sv), ctypes.c_void_p(chi_dev.data_ptr()),
                                   EPSINV_MODES[mode], ctypes.c_void_p(pw), wb, _stream_handle(stream)), None)
+
+
+def bgw_symmetry_su2(avec, rot_lat):
+    """(U complex [2][2], n [3], theta) of a lattice-basis symmetry operation."""
+    a = np.ascontiguousarray(np.asarray(avec, dtype=np.float64).reshape(9))
+    r = np.ascontiguousarray(np.asarray(rot_lat).reshape(9), dtype=np.int32)
+    u = np.zeros(8, dtype=np.float64)
+    na = np.zeros(4, dtype=np.float64)
+    _check(_lib.bgw_symmetry_su2(_host_ptr(a), _host_ptr(r), _host_ptr(u), _host_ptr(na)), None)
+    return u.view(np.complex128).reshape(2, 2), na[:3].copy(), float(na[3])
+
+
+def bgw_unfold_spinor(avec, rot_lat, tau, gvec, c_in, c_out, stream=None) -> np.ndarray:
+    """Coefficients at Rk into the device tensor c_out from c_in ([nb][2][ngw]
+    complex128 on the device); returns the rotated Miller list (host)."""
+    a = np.ascontiguousarray(np.asarray(avec, dtype=np.float64).reshape(9))
+    r = np.ascontiguousarray(np.asarray(rot_lat).reshape(9), dtype=np.int32)
+    t = np.ascontiguousarray(tau, dtype=np.float64)
+    g = np.ascontiguousarray(gvec, dtype=np.int32)
+    g2 = np.zeros_like(g)
+    nb, ngw = int(c_in.shape[0]), int(c_in.shape[2])
+    _check(_lib.bgw_unfold_spinor(_host_ptr(a), _host_ptr(r), _host_ptr(t), nb, ngw, _host_ptr(g), _host_ptr(g2),
+                                  ctypes.c_void_p(c_in.data_ptr()), ctypes.c_void_p(c_out.data_ptr()),
+                                  _stream_handle(stream)), None)
+    return g2
 
 
 def bgw_profile(ctx, enable: bool) -> int:

@@ -93,3 +93,29 @@ def test_epsinv_argument_errors_without_gpu():
     rc = B._lib.bgw_epsinv(1, 1, B._host_ptr(s), B.ctypes.c_void_p(16), 1, None, 0, None)
     assert rc == B.BGW_E_ARG
     assert b"finite" in B._lib.bgw_last_error(None)
+
+
+def test_symmetry_su2_host_matches_oracle_for_fcc_operations():
+    """bgw_symmetry_su2 is a host computation: every operation of the FCC
+    lattice (48, improper ones through their proper part) against the oracle."""
+    from oracle import symmetry as sym
+    from paper_2206_00808_gb300 import binding as B
+    from paper_2206_00808_gb300 import synthetic as syn
+    avec = syn.fcc_cell(10.26)
+    A = avec.T
+    for R in sym.cubic_operations():
+        R_lat = np.rint(np.linalg.inv(A) @ R @ A).astype(np.int32)
+        U, n, theta = B.bgw_symmetry_su2(avec, R_lat)
+        assert np.abs(U - sym.spin_matrix(avec, R_lat)).max() < 1e-13
+        P = -R if np.linalg.det(R) < 0 else R
+        assert np.abs(sym.axis_angle_matrix(n, theta) - P).max() < 1e-13
+
+
+def test_symmetry_rejects_non_rotations():
+    from paper_2206_00808_gb300 import binding as B
+    from paper_2206_00808_gb300 import synthetic as syn
+    avec = syn.fcc_cell(10.26)
+    with pytest.raises(B.BgwError):
+        B.bgw_symmetry_su2(avec, np.array([[2, 0, 0], [0, 1, 0], [0, 0, 1]]))   # not unimodular
+    with pytest.raises(B.BgwError):
+        B.bgw_symmetry_su2(avec, np.array([[1, 1, 0], [0, 1, 0], [0, 0, 1]]))   # shear: not a rotation
