@@ -168,6 +168,7 @@ __global__ void k8_unfold(const double2 *__restrict__ in, double2 *__restrict__ 
     for (int k = 0; k < 4; ++k)
         v[k] = make_double2(cs * op.u[k].x - sn * op.u[k].y, cs * op.u[k].y + sn * op.u[k].x);
     const int n1 = min(nb, (int)(blockIdx.y + 1) * kBandChunk);
+#pragma unroll 4
     for (int n = blockIdx.y * kBandChunk; n < n1; ++n) {
         const double2 a = in[(2L * n) * ngw + i], b = in[(2L * n + 1) * ngw + i];
 #pragma unroll
