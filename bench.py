@@ -91,9 +91,9 @@ def parse_args():
     ap.add_argument("--grid-slots", type=int, default=-1,
                     help="real-space grid slots (0 = all k resident; default 8 for bi2se3, else 0)")
     ap.add_argument("--kchunk", type=int, default=0, help="k-chunk when not autotuning")
-    ap.add_argument("--k1-path", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--k1-path", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="sphere -> grid kernels: 0 automatic, 1 per axis, 2 one kernel per band component, "
-                         "3 eight lanes per line (cubic 32/40/48/64)")
+                         "3 eight lanes per line (cubic 32/40/48/64), 4 one kernel without the shared cube")
     ap.add_argument("--mtxel-lanes", type=int, default=0, choices=[0, 1, 8],
                     help="FFT lanes per line of the matrix-element kernels (0 automatic)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")

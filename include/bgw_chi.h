@@ -318,8 +318,11 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        per axis, 2 one kernel for the whole transform of a
  *                        band component where the box fits in shared memory
  *                        (else as 1), 3 eight lanes per FFT line where the box
- *                        is cubic with N = 32, 40, 48 or 64 (else automatic).
- *                        All give the same grids up to rounding.
+ *                        is cubic with N = 32, 40, 48 or 64 (else automatic),
+ *                        4 (FP32 cubic boxes below 48) one kernel per band
+ *                        component without the shared cube, three per SM,
+ *                        where it fits (else automatic).  All give the same
+ *                        grids up to rounding.
  *   BGW_OPT_MTXEL_LANES  FFT lanes per line of the matrix-element kernels:
  *                        0 automatic (default: eight for cubic 48 and 64 boxes,
  *                        one elsewhere), 1 one, 8 eight where the box is cubic

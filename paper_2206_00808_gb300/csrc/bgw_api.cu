@@ -1169,7 +1169,7 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
             c->test_drop_load = value != 0;
             return BGW_OK;
         case BGW_OPT_K1_PATH:
-            if (value < 0 || value > 3) return c->fail(BGW_E_ARG, "set_option: K1 path must be 0..3");
+            if (value < 0 || value > 4) return c->fail(BGW_E_ARG, "set_option: K1 path must be 0..4");
             c->k1_path = (int)value;
             return BGW_OK;
         case BGW_OPT_MTXEL_LANES:

@@ -573,10 +573,14 @@ k2_xpass_scatter_c4(const C *__restrict__ Bs, long P, int w0, int w1, int w2, in
 // intermediate array leaves the SM.
 constexpr int kFusedThreads = 256;
 
-template <int N>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
-k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv, int w0, int w1,
-         int w2, int s0, int s1, int s2, int KP, C *__restrict__ U) {
+// kCube = false (FP32, on request): no shared cube; the x lines gather their
+// coefficients from global memory through the cube map (cmap), which frees
+// the cube's shared memory for a third CTA per SM.
+template <int N, bool kCube>
+__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (kCube ? 2 : 3) : 1)
+k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv,
+         const int *__restrict__ cmap, int w0, int w1, int w2, int s0, int s1, int s2, int KP,
+         C *__restrict__ U) {
     extern __shared__ unsigned char smem_raw[];
     C *X = reinterpret_cast<C *>(smem_raw);
     const int yzs = w1 * w2;
@@ -585,21 +589,35 @@ k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv
     C *Y = cube;
     const long b = blockIdx.x;
     const double2 *cb = coeff + b * ngw;
-    const int ncube = w0 * yzs;
-    for (int i = threadIdx.x; i < ncube; i += kFusedThreads) cube[i] = C{T(0), T(0)};
-    __syncthreads();
-    for (int i = threadIdx.x; i < ngw; i += kFusedThreads) {
-        const double2 c = __ldg(cb + i);
-        cube[__ldg(inv + i)] = C{(T)c.x, (T)c.y};
+    if constexpr (kCube) {
+        const int ncube = w0 * yzs;
+        for (int i = threadIdx.x; i < ncube; i += kFusedThreads) cube[i] = C{T(0), T(0)};
+        __syncthreads();
+        for (int i = threadIdx.x; i < ngw; i += kFusedThreads) {
+            const double2 c = __ldg(cb + i);
+            cube[__ldg(inv + i)] = C{(T)c.x, (T)c.y};
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int ns0 = N - s0, ns1 = N - s1, ns2 = N - s2;
     for (int l = threadIdx.x; l < yzs; l += kFusedThreads) {
         C a[N];
 #pragma unroll
         for (int f = 0; f < N; ++f) {
             const int j = rot<N>(f, ns0);
-            a[f] = (j < w0) ? cube[j * yzs + l] : C{T(0), T(0)};
+            if constexpr (kCube) {
+                a[f] = (j < w0) ? cube[j * yzs + l] : C{T(0), T(0)};
+            } else {
+                C v = {T(0), T(0)};
+                if (j < w0) {
+                    const int idx = __ldg(cmap + j * yzs + l);
+                    if (idx >= 0) {
+                        const double2 c = __ldg(cb + idx);
+                        v = {(T)c.x, (T)c.y};
+                    }
+                }
+                a[f] = v;
+            }
         }
         fft_line<T, +1, N>(a);
 #pragma unroll
@@ -649,11 +667,13 @@ k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv
 }
 
 // Shared bytes of k1_fused with KP planes per chunk (Y reuses the cube).
-static size_t fused_smem(const Axes &a, int KP) {
-    const size_t cube = (size_t)a.w[0] * a.w[1] * a.w[2];
+static size_t fused_smem(const Axes &a, int KP, bool cube_in_smem = true) {
+    const size_t cube = cube_in_smem ? (size_t)a.w[0] * a.w[1] * a.w[2] : 0;
     const size_t y = (size_t)KP * a.n[1] * (a.w[2] | 1);
     return sizeof(C) * ((size_t)a.n[0] * a.w[1] * a.w[2] + (cube > y ? cube : y));
 }
+// The cube-less variant: three CTAs per SM.
+static constexpr size_t kFusedSmem3 = 72 * 1024;
 // Automatic choice: two CTAs per SM; on request (path 2) up to one per SM.
 static constexpr size_t kFusedSmemAuto = 110 * 1024;
 static constexpr size_t kFusedSmemMax = 200 * 1024;
@@ -919,26 +939,45 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
     const double2 *cf = reinterpret_cast<const double2 *>(coeff);
     const int *inv = cube_map + (long)a.w[0] * a.w[1] * a.w[2];
     const bool oct = oct_len(a) && (path == 3 || (use_coop(a) && use_oct(a)));
+    if (path == 4 && sizeof(T) == 4 && a.n[0] == a.n[1] && a.n[1] == a.n[2] && a.n[0] < kCoopMinN) {
+        // cube-less one-kernel transform, three CTAs per SM, where it fits
+        int KP = 0;
+        for (int chunks = 1; chunks <= a.n[0] && !KP; ++chunks) {
+            const int kp = (a.n[0] + chunks - 1) / chunks;
+            if (fused_smem(a, kp, false) <= kFusedSmem3) KP = kp;
+        }
+        if (KP) {
+            const size_t smem = fused_smem(a, KP, false);
+            cudaError_t e = cudaSuccess;
+            BGW_FOR_EACH_LEN(a.n[0], {
+                if constexpr (N < kCoopMinN) {
+                    if (smem > 48 * 1024) {
+                        e = cudaFuncSetAttribute(k1_fused<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+                        if (e != cudaSuccess) return e;
+                    }
+                    k1_fused<N, false><<<(unsigned)nb, kFusedThreads, smem, st>>>(
+                        cf, ngw, inv, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], a.s[1], a.s[2], KP, Up);
+                }
+            });
+            return cudaGetLastError();
+        }
+    }
     if (const int KP = (path == 1 || oct) ? 0 : fused_planes(a, path == 2 ? kFusedSmemMax : kFusedSmemAuto)) {
         const size_t smem = fused_smem(a, KP);
         cudaError_t e = cudaSuccess;
         BGW_FOR_EACH_LEN(a.n[0], {
             if constexpr (N < kCoopMinN) {
                 if (smem > 48 * 1024) {
-                    e = cudaFuncSetAttribute(k1_fused<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                    e = cudaFuncSetAttribute(k1_fused<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
                     if (e != cudaSuccess) return e;
                 }
-                k1_fused<N><<<(unsigned)nb, kFusedThreads, smem, st>>>(
-                    cf, ngw, inv, a.w[0], a.w[1], a.w[2], a.s[0], a.s[1], a.s[2], KP, Up);
+                k1_fused<N, true><<<(unsigned)nb, kFusedThreads, smem, st>>>(
+                    cf, ngw, inv, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], a.s[1], a.s[2], KP, Up);
             }
         });
         return cudaGetLastError();
-    }
-    {
-        const long lines = nb * a.w[1] * a.w[2];
-        BGW_FOR_EACH_LEN(a.n[0], (k1_xpass<N><<<blocks_for(lines), kLineThreads, 0, st>>>(
-                                     cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
     }
     if (oct) {
         const long groups = nb * a.w[1] * a.w[2];
@@ -956,6 +995,11 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
                                                                                           a.s[2], Up);
         });
         return cudaGetLastError();
+    }
+    {
+        const long lines = nb * a.w[1] * a.w[2];
+        BGW_FOR_EACH_LEN(a.n[0], (k1_xpass<N><<<blocks_for(lines), kLineThreads, 0, st>>>(
+                                     cf, ngw, nb, cube_map, a.w[0], a.w[1], a.w[2], a.s[0], Sp)));
     }
     if (use_plane_kernels(a)) {
         const int n = a.n[1];

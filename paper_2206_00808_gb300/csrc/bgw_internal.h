@@ -24,7 +24,8 @@ cudaError_t grid_tables_init_f32();
 // the inverse map [ngw] -> cube cell; S: [B][n0][w1][w2], R: [B][n0][n1][w2]
 // scratch of T-complex; U: [B][n0][n1][n2] T-complex.  path: 0 automatic,
 // 1 the per-axis pass kernels, 2 the one-kernel transform where it fits,
-// 3 the eight-lane kernels where the box is cubic with N = 32, 40, 48 or 64.
+// 3 the eight-lane kernels where the box is cubic with N = 32, 40, 48 or 64,
+// 4 the one-kernel transform without the shared cube (FP32, three CTAs/SM).
 cudaError_t wfn_to_grid_f64(const double *coeff, int ngw, int B, const int *cube_map,
                             const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path = 0);
 cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube_map,

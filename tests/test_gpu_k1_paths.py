@@ -11,7 +11,7 @@ from paper_2206_00808_gb300 import synthetic as syn
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("k1_path,lanes", [(1, 1), (2, 0), (3, 8)])
+@pytest.mark.parametrize("k1_path,lanes", [(1, 1), (2, 0), (3, 8), (4, 0)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 5e-6)])
 @pytest.mark.parametrize("name,overrides", [("si18_qx", {}), ("si16_q0", {"box": (20, 20, 20)}),
                                             ("si18_qx", {"box": (32, 32, 32)}),
