@@ -1,4 +1,5 @@
-// In-register mixed-radix FFT of one line per thread, for the short box
+// Mixed-radix FFT of one line per thread in registers (with four- and
+// eight-lane variants for long lines, below), for the short box
 // lengths of plane-wave codes (products of 2, 3 and 5 up to 64).
 //
 // The transform of Eq. (matrix_el) of arXiv:2206.00808 is a 3-D DFT; it is

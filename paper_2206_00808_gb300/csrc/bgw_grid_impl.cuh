@@ -4,8 +4,10 @@
 // Included once per precision by bgw_grid_f64.cu / bgw_grid_f32.cu with
 // BGW_REAL and BGW_SUFFIX defined.
 //
-// Both 3-D transforms are done one axis at a time, one line per thread, with
-// pruning on the side where most of the box is empty:
+// Both 3-D transforms are done one axis at a time (one line per thread up to
+// N = 40; eight lanes per line through shared memory for cubic 48 and 64;
+// four lanes per line with warp shuffles for non-cubic boxes of those
+// lengths), with pruning on the side where most of the box is empty:
 //   sphere -> grid (inverse, u(r) = sum_h c(h) e^{+2 pi i h.r/N}): only the
 //     lines that meet the sphere's bounding cube are transformed along x,
 //     then along y, then along z (cube w0*w1*w2 -> n0*w1*w2 -> n0*n1*w2 -> n0*n1*n2);
@@ -264,7 +266,7 @@ k2_xpass_scatter(const C *__restrict__ Bs, long P, int w0, int w1, int w2, int s
     }
 }
 
-// ------------------------------------- four lanes per line (N >= 48) --
+// -------------------- four lanes per line (non-cubic boxes, N >= 48) --
 // Long lines do not fit one thread's registers; four lanes share each line
 // (fft_line_coop4).  Whole quads of lanes stay alive through the shuffles:
 // a quad past the end works on line 0 and stores nothing.

@@ -59,7 +59,7 @@ inline bool mtxel_scatter_mode(const Axes &a, size_t csize) {
 }
 
 // Whether the matrix-element kernels keep the z-pass output in the global
-// scratch A: every path but the fused z+y four-lane kernel (cubic boxes of
+// scratch A: every path but the fused z+y eight-lane kernel (cubic boxes of
 // N = 48 or 64), which keeps it in shared memory.
 inline bool mtxel_uses_a(const Axes &a) {
     const bool four_lane = a.n[0] >= 48 && a.n[1] >= 48 && a.n[2] >= 48 && a.n[0] % 16 == 0 &&
