@@ -706,8 +706,8 @@ __host__ __device__ constexpr int plane_row() { return N % 2 == 0 ? N + 2 : N + 
 
 // Pair density + z pass + y pass for one x-plane and a tile of tv x tc pairs.
 // Shared: planes[(tv+tc)][2][N][N+1], then Z[tv*tc][N][w2].
-template <int N, int MINB>
-__global__ void __launch_bounds__(kPlaneThreads, MINB)
+template <int N, int MINB, int THREADS>
+__global__ void __launch_bounds__(THREADS, MINB)
 k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int TV, int TC,
             int w1, int w2, int s1, int s2, C *__restrict__ Bs) {
     extern __shared__ unsigned char smem_raw[];
@@ -725,11 +725,11 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
     // 1. stage the x-plane of every band of the tile (both spin components)
     constexpr int VW = kVec ? 2 : 1;            // complex values per access
     const int total = (tv + tc) * 2 * NN / VW;
-    for (int base = threadIdx.x; base < total; base += kPlaneThreads * kStageU) {
+    for (int base = threadIdx.x; base < total; base += THREADS * kStageU) {
         C tmp[kStageU][VW];
 #pragma unroll
         for (int u = 0; u < kStageU; ++u) {
-            const int i = base + u * kPlaneThreads;
+            const int i = base + u * THREADS;
             if (i < total) {
                 const int ba = (i * VW) / NN, yz = (i * VW) % NN;     // ba = band * 2 + alpha
                 const int b = ba >> 1, a = ba & 1;
@@ -746,7 +746,7 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
         }
 #pragma unroll
         for (int u = 0; u < kStageU; ++u) {
-            const int i = base + u * kPlaneThreads;
+            const int i = base + u * THREADS;
             if (i < total) {
                 const int ba = (i * VW) / NN, yz = (i * VW) % NN;
                 C *dst = planes + ba * PS + (yz / N) * RS + (yz % N);
@@ -763,7 +763,7 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
     // 2. z lines: rho(z) = sum_alpha conj(u_v) u_c, forward FFT, keep w2 outputs
     const int npair = tv * tc;
     const int ns2 = N - s2, ns1 = N - s1;
-    for (int l = threadIdx.x; l < npair * N; l += kPlaneThreads) {
+    for (int l = threadIdx.x; l < npair * N; l += THREADS) {
         const int pr = l / N, y = l % N;
         const int v = pr / tc, c = pr % tc;
         const C *pv = planes + (v * 2) * PS + y * RS;
@@ -793,7 +793,7 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
     }
     __syncthreads();
     // 3. y lines over the kept z outputs; keep w1 outputs -> Bs[p][x][jy][jz]
-    for (int l = threadIdx.x; l < npair * w2; l += kPlaneThreads) {
+    for (int l = threadIdx.x; l < npair * w2; l += THREADS) {
         const int pr = l / w2, jz = l % w2;
         const int v = pr / tc, c = pr % tc;
         const C *zi = Z + (long)pr * N * w2 + jz;
@@ -1050,23 +1050,25 @@ static size_t plane_smem(int tv, int tc, int n, int w2) {
 }
 
 // Three CTAs per SM (80 registers per thread, no spills up to N = 30) for
-// tiles whose shared memory allows it.
+// tiles whose shared memory allows it; tiles above kPlaneSmemMax run one CTA
+// of 512 threads per SM.
 static constexpr size_t kPlaneSmem3 = 72 * 1024;
 static bool plane_three_per_sm(const Axes &a, size_t smem) { return a.n[1] <= 30 && smem <= kPlaneSmem3; }
+static constexpr int kPlaneThreadsLarge = 512;
 
 static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int max) {
     if (!use_plane_kernels(a)) return 0;
     struct Cand { double cost; int tv, tc; };
-    // two ranked lists: tiles for two CTAs per SM (the default first), and
-    // smaller tiles that allow three
-    Cand best[2][64];
-    int nbest[2] = {0, 0};
-    const size_t budget = plane_smem(1, 1, a.n[1], a.w[2]) <= kPlaneSmemMax ? kPlaneSmemMax : kPlaneSmemLarge;
+    // three ranked lists: tiles for two CTAs per SM (the default first),
+    // smaller tiles that allow three, and large tiles for one CTA of 512
+    // threads
+    Cand best[3][64];
+    int nbest[3] = {0, 0, 0};
     for (int tv = 1; tv <= nv && tv <= 16; ++tv)
         for (int tc = 1; tc <= nc && tc <= 16; ++tc) {
             const size_t sm = plane_smem(tv, tc, a.n[1], a.w[2]);
-            if (sm > budget) continue;
-            const int cls = plane_three_per_sm(a, sm) ? 1 : 0;
+            if (sm > kPlaneSmemLarge) continue;
+            const int cls = sm > kPlaneSmemMax ? 2 : plane_three_per_sm(a, sm) ? 1 : 0;
             Cand *b = best[cls];
             const Cand c{(double)(tv + tc) / (tv * tc) - 1e-3 * tv * tc, tv, tc};
             int pos = nbest[cls] < 64 ? nbest[cls]++ : 63;
@@ -1080,8 +1082,8 @@ static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int 
             }
         }
     int n = 0;
-    for (int i = 0; n < max && (i < nbest[0] || i < nbest[1]); ++i)
-        for (int cls = 0; cls < 2 && n < max; ++cls)
+    for (int i = 0; n < max && (i < nbest[0] || i < nbest[1] || i < nbest[2]); ++i)
+        for (int cls = 0; cls < 3 && n < max; ++cls)
             if (i < nbest[cls]) {
                 TV[n] = best[cls][i].tv;
                 TC[n] = best[cls][i].tc;
@@ -1131,8 +1133,7 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
     }
     int TV = 0, TC = 0;
     if (use_plane_kernels(a)) {
-        const size_t budget = plane_smem(1, 1, a.n[1], a.w[2]) <= kPlaneSmemMax ? kPlaneSmemMax : kPlaneSmemLarge;
-        if (tv_req > 0 && tc_req > 0 && plane_smem(tv_req, tc_req, a.n[1], a.w[2]) <= budget) {
+        if (tv_req > 0 && tc_req > 0 && plane_smem(tv_req, tc_req, a.n[1], a.w[2]) <= kPlaneSmemLarge) {
             TV = tv_req < nv ? tv_req : nv;
             TC = tc_req < nc ? tc_req : nc;
         } else {
@@ -1157,16 +1158,18 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         dim3 grid((unsigned)a.n[0], (unsigned)((nv + TV - 1) / TV), (unsigned)((nc + TC - 1) / TC));
         cudaError_t e = cudaSuccess;
         const bool three = plane_three_per_sm(a, psmem);
+        const bool large = psmem > kPlaneSmemMax;
         BGW_FOR_EACH_LEN(a.n[1], {
-            auto kern = k2_zy_plane<N, 2>;
+            auto kern = k2_zy_plane<N, 2, kPlaneThreads>;
             if constexpr (N <= 30)
-                if (three) kern = k2_zy_plane<N, 3>;
+                if (three) kern = k2_zy_plane<N, 3, kPlaneThreads>;
+            if (large) kern = k2_zy_plane<N, 1, kPlaneThreadsLarge>;
             if (psmem > 48 * 1024) {
                 e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
                 if (e != cudaSuccess) return e;
             }
-            kern<<<grid, kPlaneThreads, psmem, st>>>(uv, uc, nv, nc, TV, TC, a.w[1], a.w[2], a.s[1], a.s[2],
-                                                     Bp);
+            kern<<<grid, large ? kPlaneThreadsLarge : kPlaneThreads, psmem, st>>>(
+                uv, uc, nv, nc, TV, TC, a.w[1], a.w[2], a.s[1], a.s[2], Bp);
         });
     } else {
         const long plane = (long)a.n[0] * a.n[1];

@@ -51,7 +51,7 @@ def test_kchunk_aligned_splits_are_bitwise_identical(gpu_lib, case, prec):
     assert np.array_equal(one, split)
 
 
-@pytest.mark.parametrize("tile", [(1, 1), (2, 3), (8, 2)])
+@pytest.mark.parametrize("tile", [(1, 1), (2, 3), (8, 2), (2, 2), (8, 8)])
 def test_pair_tiles_give_identical_results(gpu_lib, case, tile):
     p, _ = case
     auto = run(gpu_lib, p, "mixed")
