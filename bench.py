@@ -36,6 +36,9 @@ WORKLOADS = {
                    "si24 shapes (24^3, N_G=350, N_v=8, N_c=200, 5 freqs) on a 2x2x2 k-grid, q=(1/2,0,0)"),
     "gasb32": ("gasb32", "GaSb-like FCC a=11.53 bohr, 32^3 box, N_w~5000 per spinor component, "
                          "N_G=800, N_k=216 (6x6x6), N_v=18, N_c=400, 16 imaginary freqs, q=(1/6,0,0)"),
+    # profiling case: the GaSb-like per-launch shapes on a 2x2x2 k-grid (~2 GB on the device)
+    "gasb32_small": (dict(config="gasb32", kgrid=(2, 2, 2), q=(0.5, 0, 0)),
+                     "gasb32 shapes (32^3, N_G=800, N_v=18, N_c=400, 16 freqs) on a 2x2x2 k-grid, q=(1/2,0,0)"),
     "gasb32_batch": ("batch", "40 q-points of the GaSb-like 6x6x6 grid in one accumulate call: "
                               "32^3 box, N_G(q)~U{700..900}, N_c(q)~U{300..500}, N_v=18, 16 freqs"),
     "bi2se3": ("bi2se3", "Bi2Se3-like rhombohedral cell (hex a=4.143 A, c=28.636 A), 64^3 box, "
@@ -289,7 +292,8 @@ def make_workload(name):
         return p, desc
     if isinstance(over, str):
         return syn.make_problem(over), desc
-    return syn.make_problem("si24", **over), desc
+    over = dict(over)
+    return syn.make_problem(over.pop("config", "si24"), **over), desc
 
 
 def run_reference(args, world, rank):

@@ -284,10 +284,15 @@ __device__ __forceinline__ Item decode(const GroupParams &gp, int item) {
     Item it;
     int q = 0;
     while (q + 1 < gp.nq && gp.first[q + 1] <= item) ++q;
+    // frequency-major within a q-point: the CTAs working at the same time
+    // cover whole lower triangles of one or two frequencies, so they share
+    // the A tiles (every frequency) and each B_j tile (every row below it)
+    // while they stream K together, and most operand reads hit L2
     const int local = item - gp.first[q];
-    lower_tile(local / gp.nfreq, it.ti, it.tj);
+    const int ntiles = (gp.first[q + 1] - gp.first[q]) / gp.nfreq;
+    lower_tile(local % ntiles, it.ti, it.tj);
     it.q = q;
-    it.j = local % gp.nfreq;
+    it.j = local / ntiles;
     it.nkb = gp.kp[q] / kBlockK;
     return it;
 }
