@@ -99,6 +99,9 @@ def parse_args():
                          "3 eight lanes per line (cubic 32/40/48/64), 4 one kernel without the shared cube")
     ap.add_argument("--mtxel-lanes", type=int, default=0, choices=[0, 1, 8],
                     help="FFT lanes per line of the matrix-element kernels (0 automatic)")
+    ap.add_argument("--defer-k1", type=int, default=1, choices=[0, 1],
+                    help="1 (default): build the grids of a step's uploads together at the accumulate "
+                         "(one launch per 64 k-points where the box allows); 0: at each upload")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")
     ap.add_argument("--alu-peaks", action="store_true",
                     help="only time cuBLAS FP64 and FP32 (no TF32) GEMMs of 8192^3 through torch.matmul "
@@ -367,6 +370,8 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_K1_PATH, args.k1_path)
     if args.mtxel_lanes > 0:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_MTXEL_LANES, args.mtxel_lanes)
+    if args.defer_k1:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_DEFER_K1, 1)
     ctx.upload(device_inputs=dev_in)
     tune_span = min(p.nk, 16)
     if fixed_fp64:
@@ -670,7 +675,8 @@ def run_ours(args, world, rank, local):
                 "config": {"workload": desc, "precision": args.precision,
                            "timing": "one captured CUDA graph per step, replayed; stages from an "
                                      "eager profiled pass of the same steps",
-                           "q_points": nq, "pairs_per_q": p.pairs(), "l2": "inputs larger than L2 (coefficients "
+                           "q_points": nq, "pairs_per_q": p.pairs(), "defer_k1": args.defer_k1,
+                           "l2": "inputs larger than L2 (coefficients "
                            f"{sum(c.nbytes for c in p.coeff) / 1e9:.2f} GB, grids resident per step)"},
                 "tflops": fl["total"] / (ms * 1e-3) / 1e12,
                 "pairs_per_s": value / nq * sum(p.pairs(i) for i in range(nq)),

@@ -328,6 +328,19 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        one elsewhere), 1 one, 8 eight where the box is cubic
  *                        with N = 32, 40, 48 or 64.  Same results up to
  *                        rounding.
+ *   BGW_OPT_DEFER_K1     0 (default): bgw_wfn_upload builds the k-point's
+ *                        real-space grid before it returns (on the stream).
+ *                        1: the build is deferred to the next call that reads
+ *                        grids (bgw_mtxel_spinor, bgw_chi0_accumulate,
+ *                        bgw_autotune) or to bgw_graph_begin, and the grids of
+ *                        all deferred k-points are built together, in one
+ *                        launch per 64 k-points where the box and path allow.
+ *                        A device upload (on_device = 1) then keeps a reference
+ *                        to the caller's coefficient buffer until that build:
+ *                        keep it alive and unchanged until then; a host upload
+ *                        is kept in a device copy per k-point.  No effect with
+ *                        k-point streaming (BGW_OPT_GRID_SLOTS), whose grids
+ *                        are built on demand already.  Same grids, bitwise.
  *   BGW_OPT_TEST_FAIL_ALLOC for failure-handling tests only: when n > 0, the
  *                        n-th device allocation made by the library from now on
  *                        (by any context of the process) fails as if the device
@@ -343,7 +356,7 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  */
 enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
        BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7,
-       BGW_OPT_MTXEL_LANES = 8 };
+       BGW_OPT_MTXEL_LANES = 8, BGW_OPT_DEFER_K1 = 9 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

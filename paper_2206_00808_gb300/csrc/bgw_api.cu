@@ -85,6 +85,7 @@ struct KPoint {
     DevBuf coeff;                               // streaming mode: device copy of host coefficients
     const double *coeff_src = nullptr;          // streaming mode: coefficients the grid is built from
     int slot = -1;                              // grid slot holding this k (-1: none)
+    const double *pending = nullptr;            // BGW_OPT_DEFER_K1: grid not built yet, from these
 };
 
 struct QState {
@@ -178,6 +179,8 @@ struct bgw_ctx_s {
     int test_drop_load = 0;       // BGW_OPT_TEST_DROP_LOAD
     int k1_path = 0;              // BGW_OPT_K1_PATH
     int mtxel_lanes = 0;          // BGW_OPT_MTXEL_LANES
+    int defer_k1 = 0;             // BGW_OPT_DEFER_K1
+    int npending = 0;             // uploads whose grid is not built yet
     // k-points summed into the running sum (accumulate calls made since the
     // q-set was installed; replays of a captured graph are not counted)
     std::vector<int> kcount;
@@ -328,6 +331,47 @@ int ensure_grid(bgw_ctx_s *c, int ik, cudaError_t &e) {
     }
     c->slot_stamp[kp.slot] = ++c->use_clock;
     return kp.slot;
+}
+
+// Builds the grids of the deferred uploads (BGW_OPT_DEFER_K1): one launch
+// per up to 64 k-points where every pending k takes the one-kernel transform
+// of the automatic path, else one run_k1 per k.  Queued on the context
+// stream ahead of the kernels that read the grids.
+cudaError_t flush_k1(bgw_ctx_s *c) {
+    if (c->npending == 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    std::vector<bgw::K1Job> jobs;
+    std::vector<int> ks;
+    for (int ik = 0; ik < c->nk; ++ik) {
+        KPoint &kp = c->k[ik];
+        if (!kp.pending) continue;
+        bgw::K1Job j;
+        j.coeff = kp.pending;
+        j.ngw = kp.ngw;
+        j.cube_map = static_cast<const int *>(kp.map_dev.p);
+        for (int a = 0; a < 3; ++a) {
+            j.a.n[a] = c->box[a];
+            j.a.w[a] = kp.hi[a] - kp.lo[a] + 1;
+            j.a.s[a] = pmod(kp.lo[a], c->box[a]);
+        }
+        j.U = c->slot_ptr(ik, 0);
+        jobs.push_back(j);
+        ks.push_back(ik);
+    }
+    bool batched = false;
+    if (c->k1_path == 0) {
+        const int rec = c->stage_begin(0);
+        const int B = 2 * c->nb;
+        e = (c->prec == BGW_FP64) ? bgw::wfn_to_grid_batch_f64(jobs.data(), (int)jobs.size(), B, c->st, &batched)
+                                  : bgw::wfn_to_grid_batch_f32(jobs.data(), (int)jobs.size(), B, c->st, &batched);
+        c->stage_end(rec, batched ? (long)((jobs.size() + 63) / 64) : 0);
+    }
+    for (size_t i = 0; e == cudaSuccess && !batched && i < ks.size(); ++i)
+        e = run_k1(c, ks[i], jobs[i].coeff, ks[i]);
+    if (e != cudaSuccess) return e;
+    for (int ik : ks) c->k[ik].pending = nullptr;
+    c->npending = 0;
+    return cudaSuccess;
 }
 
 // k + q = k' + G0 with k' on the list (tolerance 1e-6 in crystal units).
@@ -903,6 +947,16 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
             if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: coefficient store");
             kp.coeff_src = static_cast<const double *>(kp.coeff.p);
         }
+    } else if (c->defer_k1) {
+        // the grid is built by the next call that reads grids; host inputs
+        // are kept in a per-k device copy until then
+        if (!on_device) {
+            e = kp.coeff.ensure(cbytes, c->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(kp.coeff.p, coeff, cbytes, cudaMemcpyHostToDevice, c->st);
+            if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: coefficient store");
+            src = static_cast<const double *>(kp.coeff.p);
+        }
     } else if (!on_device) {
         e = c->stage.ensure(cbytes, c->st);
         if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: staging buffer");
@@ -925,7 +979,14 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
             c->slot_stamp[kp.slot] = 0;
             kp.slot = -1;
         }
+    } else if (c->defer_k1) {
+        if (!kp.pending) ++c->npending;
+        kp.pending = src;
     } else {
+        if (kp.pending) {                // a deferred build of an older upload is void now
+            kp.pending = nullptr;
+            --c->npending;
+        }
         e = run_k1(c, ik, src, ik);
         if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: sphere-to-grid kernels");
     }
@@ -953,7 +1014,9 @@ bgw_status bgw_mtxel_spinor(bgw_ctx c, const bgw_q *q, int ik, int v0, int nv, i
     if (nv == 0 || nc == 0) return BGW_OK;
     const bool clean = alias_free(c, ik, kp, G0, s);
     const long P = (long)nv * nc;
-    cudaError_t e = ensure_mtxel_scratch(c, s, P);
+    cudaError_t e = flush_k1(c);
+    if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: deferred sphere-to-grid kernels");
+    e = ensure_mtxel_scratch(c, s, P);
     if (e != cudaSuccess) return c->cuda_fail(e, "mtxel: scratch");
     // The per-call map goes to a context buffer; reuse is stream-ordered and
     // a pageable-memory copy has read the host vector when the call returns.
@@ -1002,6 +1065,8 @@ bgw_status bgw_chi0_accumulate(bgw_ctx c, int nq, const bgw_q *qs, int nfreq,
         bgw_status st = install_qset(c, fresh, nfreq, freq_eV);
         if (st != BGW_OK) return st;
     }
+    e = flush_k1(c);
+    if (e != cudaSuccess) return c->cuda_fail(e, "accumulate: deferred sphere-to-grid kernels");
     bool clean = true;
     e = run_range(c, c->qs, nfreq, static_cast<const double *>(c->freq_dev.p), k_begin, k_end, kchunk,
                   c->tile_v, c->tile_c, clean);
@@ -1177,6 +1242,10 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
                 return c->fail(BGW_E_ARG, "set_option: matrix-element lanes must be 0, 1 or 8");
             c->mtxel_lanes = (int)value;
             return BGW_OK;
+        case BGW_OPT_DEFER_K1:
+            if (value != 0 && value != 1) return c->fail(BGW_E_ARG, "set_option: deferred K1 must be 0 or 1");
+            c->defer_k1 = (int)value;
+            return BGW_OK;
         case BGW_OPT_TEST_FAIL_ALLOC:
             if (value < 0) return c->fail(BGW_E_ARG, "set_option: allocation count must be >= 0");
             g_fail_alloc.store(value);
@@ -1203,6 +1272,7 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_TEST_FAIL_ALLOC: *value = g_fail_alloc.load(); return BGW_OK;
         case BGW_OPT_K1_PATH: *value = c->k1_path; return BGW_OK;
         case BGW_OPT_MTXEL_LANES: *value = c->mtxel_lanes; return BGW_OK;
+        case BGW_OPT_DEFER_K1: *value = c->defer_k1; return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }
@@ -1241,10 +1311,12 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
         }
     }
     // scratch accumulators and maps for the timing runs (the running sums are untouched)
+    cudaError_t e = flush_k1(c);
+    if (e != cudaSuccess) return c->cuda_fail(e, "autotune: deferred sphere-to-grid kernels");
     const bool prof = c->prof;
     c->prof = false;
     DevBuf tfreq;
-    cudaError_t e = tfreq.ensure(sizeof(double) * nfreq, c->st);
+    e = tfreq.ensure(sizeof(double) * nfreq, c->st);
     for (auto &s : tq) {
         if (e == cudaSuccess) e = s.gmap_dev.ensure(sizeof(int) * s.gmap.size(), c->st);
         if (e == cudaSuccess) e = s.kmap_dev.ensure(sizeof(int) * (size_t)c->nk, c->st);
@@ -1346,7 +1418,8 @@ bgw_status bgw_graph_begin(bgw_ctx c) {
     c->err.clear();
     if (!c->st) return c->fail(BGW_E_ARG, "graph_begin: the context stream is the legacy default stream");
     if (c->capturing) return c->fail(BGW_E_STATE, "graph_begin: already capturing");
-    cudaError_t e = c->drain();
+    cudaError_t e = flush_k1(c);   // uploads made before the capture are not part of it
+    if (e == cudaSuccess) e = c->drain();
     if (e == cudaSuccess) e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return c->cuda_fail(e, "graph_begin");
     c->capturing = true;

@@ -9,6 +9,9 @@ cudaError_t wfn_to_grid_f64(const double *coeff, int ngw, int B, const int *cube
                             const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path) {
     return f64::wfn_to_grid(coeff, ngw, B, cube_map, a, S, R, U, st, path);
 }
+cudaError_t wfn_to_grid_batch_f64(const K1Job *jobs, int n, int B, cudaStream_t st, bool *batched) {
+    return f64::wfn_to_grid_batch(jobs, n, B, st, batched);
+}
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
                       cudaStream_t st, int tv, int tc, int lanes) {

@@ -578,19 +578,17 @@ constexpr int kFusedThreads = 256;
 // kCube = false (FP32, on request): no shared cube; the x lines gather their
 // coefficients from global memory through the cube map (cmap), which frees
 // the cube's shared memory for a third CTA per SM.
+// The transform of one band component: coefficients cb[ngw] -> grid out[N^3].
 template <int N, bool kCube>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (kCube ? 2 : 3) : 1)
-k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv,
-         const int *__restrict__ cmap, int w0, int w1, int w2, int s0, int s1, int s2, int KP,
-         C *__restrict__ U) {
-    extern __shared__ unsigned char smem_raw[];
+__device__ __forceinline__ void k1_fused_body(const double2 *__restrict__ cb, int ngw, const int *__restrict__ inv,
+                                              const int *__restrict__ cmap, int w0, int w1, int w2, int s0,
+                                              int s1, int s2, int KP, C *__restrict__ out,
+                                              unsigned char *smem_raw) {
     C *X = reinterpret_cast<C *>(smem_raw);
     const int yzs = w1 * w2;
     const int w2p = w2 | 1;                    // odd row stride: conflict-free z-line reads
     C *cube = X + (long)N * yzs;               // [w0][w1][w2], later Y[KP][N][w2p]
     C *Y = cube;
-    const long b = blockIdx.x;
-    const double2 *cb = coeff + b * ngw;
     if constexpr (kCube) {
         const int ncube = w0 * yzs;
         for (int i = threadIdx.x; i < ncube; i += kFusedThreads) cube[i] = C{T(0), T(0)};
@@ -626,7 +624,6 @@ k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv
         for (int x = 0; x < N; ++x) X[x * yzs + l] = a[x];
     }
     __syncthreads();
-    C *out = U + b * (long)N * N * N;
     for (int x0 = 0; x0 < N; x0 += KP) {
         const int kp = min(KP, N - x0);
         for (int l = threadIdx.x; l < kp * w2; l += kFusedThreads) {
@@ -666,6 +663,42 @@ k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv
         }
         __syncthreads();
     }
+}
+
+template <int N, bool kCube>
+__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (kCube ? 2 : 3) : 1)
+k1_fused(const double2 *__restrict__ coeff, int ngw, const int *__restrict__ inv,
+         const int *__restrict__ cmap, int w0, int w1, int w2, int s0, int s1, int s2, int KP,
+         C *__restrict__ U) {
+    extern __shared__ unsigned char smem_raw[];
+    const long b = blockIdx.x;
+    k1_fused_body<N, kCube>(coeff + b * ngw, ngw, inv, cmap, w0, w1, w2, s0, s1, s2, KP,
+                            U + b * (long)N * N * N, smem_raw);
+}
+
+// Several k-points in one launch (deferred uploads): CTA x = (job, band
+// component), so the launch has no wave tail per k-point.
+constexpr int kK1BatchMax = 64;
+struct K1BatchJob {
+    const double2 *coeff;
+    const int *inv;
+    C *U;
+    int ngw, w0, w1, w2, s0, s1, s2, KP;
+};
+struct K1Batch {
+    int njobs, B;
+    K1BatchJob job[kK1BatchMax];
+};
+
+template <int N>
+__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
+k1_fused_batch(const __grid_constant__ K1Batch jb) {
+    extern __shared__ unsigned char smem_raw[];
+    const int j = blockIdx.x / jb.B;
+    const long b = blockIdx.x % jb.B;
+    const K1BatchJob &e = jb.job[j];
+    k1_fused_body<N, true>(e.coeff + b * e.ngw, e.ngw, e.inv, nullptr, e.w0, e.w1, e.w2, e.s0, e.s1, e.s2, e.KP,
+                           e.U + b * (long)N * N * N, smem_raw);
 }
 
 // Shared bytes of k1_fused with KP planes per chunk (Y reuses the cube).
@@ -1040,6 +1073,61 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
                                      Rp, nbxy, a.w[2], a.s[2], Up)));
     }
     return cudaGetLastError();
+}
+
+// K1 of several k-points in launches of up to kK1BatchMax: only when every
+// job takes the shared-cube one-kernel transform of the automatic path with
+// the same box (else *batched = false and nothing is launched; the caller
+// runs them one by one).  Same body, planes per chunk and launch bounds as
+// k1_fused<N, true>, so the grids are the ones wfn_to_grid writes.
+static cudaError_t wfn_to_grid_batch(const K1Job *jobs, int n, int B, cudaStream_t st, bool *batched) {
+    *batched = false;
+    if (n < 1) return cudaSuccess;
+    const int N0 = jobs[0].a.n[0];
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        const Axes &a = jobs[i].a;
+        if (a.n[0] != N0 || (oct_len(a) && use_coop(a) && use_oct(a))) return cudaSuccess;
+        const int KP = fused_planes(a, kFusedSmemAuto);
+        if (!KP) return cudaSuccess;
+        const size_t sm = fused_smem(a, KP);
+        smem = sm > smem ? sm : smem;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int i0 = 0; i0 < n; i0 += kK1BatchMax) {
+        K1Batch jb;
+        jb.njobs = n - i0 < kK1BatchMax ? n - i0 : kK1BatchMax;
+        jb.B = B;
+        for (int i = 0; i < jb.njobs; ++i) {
+            const K1Job &j = jobs[i0 + i];
+            K1BatchJob &d = jb.job[i];
+            d.coeff = reinterpret_cast<const double2 *>(j.coeff);
+            d.inv = j.cube_map + (long)j.a.w[0] * j.a.w[1] * j.a.w[2];
+            d.U = static_cast<C *>(j.U);
+            d.ngw = j.ngw;
+            d.w0 = j.a.w[0];
+            d.w1 = j.a.w[1];
+            d.w2 = j.a.w[2];
+            d.s0 = j.a.s[0];
+            d.s1 = j.a.s[1];
+            d.s2 = j.a.s[2];
+            d.KP = fused_planes(j.a, kFusedSmemAuto);
+        }
+        BGW_FOR_EACH_LEN(N0, {
+            if constexpr (N < kCoopMinN) {
+                if (smem > 48 * 1024) {
+                    e = cudaFuncSetAttribute(k1_fused_batch<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+                    if (e != cudaSuccess) return e;
+                }
+                k1_fused_batch<N><<<(unsigned)(jb.njobs * B), kFusedThreads, smem, st>>>(jb);
+            }
+        });
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    *batched = true;
+    return cudaSuccess;
 }
 
 // Pair tiles (TV valence x TC conduction) of the plane kernel that fit

@@ -31,6 +31,20 @@ cudaError_t wfn_to_grid_f64(const double *coeff, int ngw, int B, const int *cube
 cudaError_t wfn_to_grid_f32(const double *coeff, int ngw, int B, const int *cube_map,
                             const Axes &a, void *S, void *R, void *U, cudaStream_t st, int path = 0);
 
+// One k-point's sphere -> grid job for the batched launcher.
+struct K1Job {
+    const double *coeff;      // complex128 [B][ngw] (device)
+    int ngw;
+    const int *cube_map;      // cube map followed by the inverse map (device)
+    Axes a;
+    void *U;                  // grid slot [B][n0][n1][n2]
+};
+// K1 of n k-points in as few launches as possible, when every job takes the
+// shared-cube one-kernel transform with one box length; *batched = false and
+// nothing launched otherwise.
+cudaError_t wfn_to_grid_batch_f64(const K1Job *jobs, int n, int B, cudaStream_t st, bool *batched);
+cudaError_t wfn_to_grid_batch_f32(const K1Job *jobs, int n, int B, cudaStream_t st, bool *batched);
+
 // Pair density, pruned forward FFT and gather for P = nv*nc pairs of one k:
 //   M[v*nc+c][g] = N^-3 sum_r sum_alpha conj(u_v,alpha(r)) u_c,alpha(r) e^{-2 pi i f_g.r/N}
 // with f_g the output frequency of G-vector g (G + G0).  Uv: [nv][2][N^3],
