@@ -341,6 +341,20 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        is kept in a device copy per k-point.  No effect with
  *                        k-point streaming (BGW_OPT_GRID_SLOTS), whose grids
  *                        are built on demand already.  Same grids, bitwise.
+ *   BGW_OPT_COPY_AHEAD   0 (default): a host upload (on_device = 0) copies
+ *                        the coefficients on the context stream, after the
+ *                        work queued there before it.  1: the copy runs on a
+ *                        second stream of the context into a device buffer of
+ *                        the k-point's own, so the copies of later k-points
+ *                        overlap the transforms of earlier ones; work queued
+ *                        on the context stream after the call still waits for
+ *                        the copy.  The host buffer must hold its data when
+ *                        the call is made (the copy is not ordered after
+ *                        earlier work on the context stream) and stay
+ *                        unchanged until the context stream has passed the
+ *                        call.  Costs one device copy of every k-point's
+ *                        coefficients.  Not used during a graph capture nor
+ *                        with k-point streaming.  Same grids, bitwise.
  *   BGW_OPT_TEST_FAIL_ALLOC for failure-handling tests only: when n > 0, the
  *                        n-th device allocation made by the library from now on
  *                        (by any context of the process) fails as if the device
@@ -356,7 +370,7 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  */
 enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
        BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7,
-       BGW_OPT_MTXEL_LANES = 8, BGW_OPT_DEFER_K1 = 9 };
+       BGW_OPT_MTXEL_LANES = 8, BGW_OPT_DEFER_K1 = 9, BGW_OPT_COPY_AHEAD = 10 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

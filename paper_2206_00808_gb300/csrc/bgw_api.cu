@@ -86,6 +86,10 @@ struct KPoint {
     const double *coeff_src = nullptr;          // streaming mode: coefficients the grid is built from
     int slot = -1;                              // grid slot holding this k (-1: none)
     const double *pending = nullptr;            // BGW_OPT_DEFER_K1: grid not built yet, from these
+    // BGW_OPT_COPY_AHEAD: `coeff` is written on the copy stream; `copied`
+    // marks that copy complete, `consumed` the last transform that read it
+    cudaEvent_t copied = nullptr, consumed = nullptr;
+    bool consumed_set = false;
 };
 
 struct QState {
@@ -180,6 +184,8 @@ struct bgw_ctx_s {
     int k1_path = 0;              // BGW_OPT_K1_PATH
     int mtxel_lanes = 0;          // BGW_OPT_MTXEL_LANES
     int defer_k1 = 0;             // BGW_OPT_DEFER_K1
+    int copy_ahead = 0;           // BGW_OPT_COPY_AHEAD
+    cudaStream_t cst = nullptr;   // copy stream of copy-ahead host uploads
     int npending = 0;             // uploads whose grid is not built yet
     // k-points summed into the running sum (accumulate calls made since the
     // q-set was installed; replays of a captured graph are not counted)
@@ -333,6 +339,24 @@ int ensure_grid(bgw_ctx_s *c, int ik, cudaError_t &e) {
     return kp.slot;
 }
 
+// Copy-ahead host uploads: the copy stream and the k-point's two events.
+cudaError_t ensure_copy_events(bgw_ctx_s *c, KPoint &kp) {
+    cudaError_t e = cudaSuccess;
+    if (!c->cst) e = cudaStreamCreateWithFlags(&c->cst, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !kp.copied) e = cudaEventCreateWithFlags(&kp.copied, cudaEventDisableTiming);
+    if (e == cudaSuccess && !kp.consumed) e = cudaEventCreateWithFlags(&kp.consumed, cudaEventDisableTiming);
+    return e;
+}
+
+// Marks the end of the kernels that read k's device coefficients, for the
+// next copy-ahead copy into the same buffer.  Inside a graph capture the
+// graph's launches are marked instead (bgw_graph_launch).
+cudaError_t mark_consumed(bgw_ctx_s *c, KPoint &kp) {
+    if (!kp.consumed || c->capturing) return cudaSuccess;
+    kp.consumed_set = true;
+    return cudaEventRecord(kp.consumed, c->st);
+}
+
 // Builds the grids of the deferred uploads (BGW_OPT_DEFER_K1): one launch
 // per up to 64 k-points where every pending k takes the one-kernel transform
 // of the automatic path, else one run_k1 per k.  Queued on the context
@@ -368,6 +392,7 @@ cudaError_t flush_k1(bgw_ctx_s *c) {
     }
     for (size_t i = 0; e == cudaSuccess && !batched && i < ks.size(); ++i)
         e = run_k1(c, ks[i], jobs[i].coeff, ks[i]);
+    for (size_t i = 0; e == cudaSuccess && i < ks.size(); ++i) e = mark_consumed(c, c->k[ks[i]]);
     if (e != cudaSuccess) return e;
     for (int ik : ks) c->k[ik].pending = nullptr;
     c->npending = 0;
@@ -947,6 +972,24 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
             if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: coefficient store");
             kp.coeff_src = static_cast<const double *>(kp.coeff.p);
         }
+    } else if (c->copy_ahead && !on_device && !c->capturing) {
+        // copy on the copy stream into the k's own buffer, once the last
+        // transform that read that buffer has run; the transform waits for it
+        e = ensure_copy_events(c, kp);
+        if (e == cudaSuccess && !kp.consumed_set) {
+            // first copy-ahead copy of this k: after everything queued so far
+            e = cudaEventRecord(kp.consumed, c->st);
+            kp.consumed_set = true;
+        }
+        if (e == cudaSuccess && cbytes > kp.coeff.cap) e = cudaStreamSynchronize(c->cst);
+        if (e == cudaSuccess) e = kp.coeff.ensure(cbytes, c->st);
+        if (e == cudaSuccess && kp.consumed_set) e = cudaStreamWaitEvent(c->cst, kp.consumed, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(kp.coeff.p, coeff, cbytes, cudaMemcpyHostToDevice, c->cst);
+        if (e == cudaSuccess) e = cudaEventRecord(kp.copied, c->cst);
+        // later work on the context stream (this k's transform first) waits for the copy
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, kp.copied, 0);
+        if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: copy-ahead coefficient copy");
+        src = static_cast<const double *>(kp.coeff.p);
     } else if (c->defer_k1) {
         // the grid is built by the next call that reads grids; host inputs
         // are kept in a per-k device copy until then
@@ -988,6 +1031,7 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
             --c->npending;
         }
         e = run_k1(c, ik, src, ik);
+        if (e == cudaSuccess && src == kp.coeff.p) e = mark_consumed(c, kp);
         if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: sphere-to-grid kernels");
     }
     kp.uploaded = true;
@@ -1246,6 +1290,10 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
             if (value != 0 && value != 1) return c->fail(BGW_E_ARG, "set_option: deferred K1 must be 0 or 1");
             c->defer_k1 = (int)value;
             return BGW_OK;
+        case BGW_OPT_COPY_AHEAD:
+            if (value != 0 && value != 1) return c->fail(BGW_E_ARG, "set_option: copy-ahead must be 0 or 1");
+            c->copy_ahead = (int)value;
+            return BGW_OK;
         case BGW_OPT_TEST_FAIL_ALLOC:
             if (value < 0) return c->fail(BGW_E_ARG, "set_option: allocation count must be >= 0");
             g_fail_alloc.store(value);
@@ -1273,6 +1321,7 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_K1_PATH: *value = c->k1_path; return BGW_OK;
         case BGW_OPT_MTXEL_LANES: *value = c->mtxel_lanes; return BGW_OK;
         case BGW_OPT_DEFER_K1: *value = c->defer_k1; return BGW_OK;
+        case BGW_OPT_COPY_AHEAD: *value = c->copy_ahead; return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }
@@ -1420,6 +1469,7 @@ bgw_status bgw_graph_begin(bgw_ctx c) {
     if (c->capturing) return c->fail(BGW_E_STATE, "graph_begin: already capturing");
     cudaError_t e = flush_k1(c);   // uploads made before the capture are not part of it
     if (e == cudaSuccess) e = c->drain();
+    if (e == cudaSuccess && c->cst) e = cudaStreamSynchronize(c->cst);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return c->cuda_fail(e, "graph_begin");
     c->capturing = true;
@@ -1458,6 +1508,12 @@ bgw_status bgw_graph_launch(bgw_ctx c) {
     if (!c->gexec) return c->fail(BGW_E_STATE, "graph_launch: nothing captured");
     if (c->capturing) return c->fail(BGW_E_STATE, "graph_launch: still capturing");
     cudaError_t e = cudaGraphLaunch(c->gexec, c->st);
+    // the graph may read any k's copy-ahead buffer
+    for (auto &kp : c->k)
+        if (e == cudaSuccess && kp.consumed) {
+            e = cudaEventRecord(kp.consumed, c->st);
+            kp.consumed_set = true;
+        }
     if (e != cudaSuccess) return c->cuda_fail(e, "graph_launch");
     return BGW_OK;
 }
@@ -1505,6 +1561,14 @@ void bgw_destroy(bgw_ctx c) {
             cudaGetLastError();
         }
         cudaStreamSynchronize(c->st);
+        if (c->cst) {
+            cudaStreamSynchronize(c->cst);
+            cudaStreamDestroy(c->cst);
+        }
+        for (auto &k : c->k) {
+            if (k.copied) cudaEventDestroy(k.copied);
+            if (k.consumed) cudaEventDestroy(k.consumed);
+        }
         if (c->gexec) cudaGraphExecDestroy(c->gexec);
         for (auto &r : c->recs) {
             cudaEventDestroy(r.a);

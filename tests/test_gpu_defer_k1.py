@@ -3,7 +3,9 @@ batched build writes are the ones an eager upload writes, bit for bit, on
 boxes where the batched launch applies (cubic, one kernel per band component)
 and where it falls back to one transform per k-point; uploads re-made before
 the build, host and device inputs, more than one launch's worth of k-points,
-graph capture and k-point streaming all keep chi0 equal to the oracle's."""
+graph capture and k-point streaming all keep chi0 equal to the oracle's;
+copy-ahead host uploads (a second stream, per-k buffers) give the same grids
+and stay correct across steps and graph replays."""
 import numpy as np
 import pytest
 
@@ -137,3 +139,91 @@ def test_defer_is_inert_with_k_point_streaming(gpu_lib):
     got = ctx.finalize()
     ctx.close()
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def _pinned_inputs(p, coeff=None):
+    import torch
+    coeff = p.coeff if coeff is None else coeff
+    return [(torch.from_numpy(np.ascontiguousarray(coeff[ik])).pin_memory(),
+             torch.from_numpy(np.ascontiguousarray(p.energy[ik])).pin_memory()) for ik in range(p.nk)]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+@pytest.mark.parametrize("defer", [0, 1])
+def test_copy_ahead_host_uploads_over_two_steps(gpu_lib, precision, tol, defer):
+    """Copy-ahead host uploads (BGW_OPT_COPY_AHEAD): a step on other
+    coefficients, then a step on the problem's; the second reuses every
+    k's device buffer after the first step's transforms read it."""
+    import torch
+    B = gpu_lib
+    p = syn.make_problem("si18_qx", box=(24, 24, 24), nv=4, nc=6, nfreq=2)
+    ref = oracle.chi0(p)
+    rng = np.random.default_rng(11)
+    other = [rng.normal(size=c.shape) + 1j * rng.normal(size=c.shape) for c in p.coeff]
+    s = torch.cuda.Stream()
+    ctx = B.Chi0Context(p, precision, s)
+    B.bgw_set_option(ctx.ctx, B.BGW_OPT_COPY_AHEAD, 1)
+    B.bgw_set_option(ctx.ctx, B.BGW_OPT_DEFER_K1, defer)
+    first, second = _pinned_inputs(p, other), _pinned_inputs(p)
+    ctx.upload(device_inputs=first)
+    ctx.accumulate()
+    ctx.reset()
+    ctx.upload(device_inputs=second)
+    ctx.accumulate()
+    got = ctx.finalize()
+    ctx.close()
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+
+
+def test_copy_ahead_grids_equal_stream_ordered_copies(gpu_lib):
+    import torch
+    B = gpu_lib
+    p = syn.make_problem("si18_qx", box=(20, 20, 20), nv=4, nc=6)
+    pin = _pinned_inputs(p)
+    got = {}
+    for ahead in (0, 1):
+        ctx = B.Chi0Context(p, "fp64")
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_COPY_AHEAD, ahead)
+        ctx.upload(device_inputs=pin)
+        got[ahead] = _mtxel_all(B, ctx, p, torch.complex128)
+        ctx.close()
+    for a, b in zip(got[0], got[1]):
+        assert torch.equal(a, b)
+
+
+def test_copy_ahead_after_graph_replays(gpu_lib):
+    """Host uploads captured in a graph use the stream-ordered copy; a
+    copy-ahead upload after the replays waits for them, and a later replay
+    still gives the eager bits."""
+    import torch
+    B = gpu_lib
+    p = syn.make_problem("si18_qx", box=(24, 24, 24), nv=4, nc=6, nfreq=2)
+    ref = oracle.chi0(p)
+    ng = len(p.qs[0][1])
+    pin = _pinned_inputs(p)
+    s = torch.cuda.Stream()
+    out = torch.zeros((len(p.freq), ng, ng), dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    ctx = B.Chi0Context(p, "mixed", s)
+    B.bgw_set_option(ctx.ctx, B.BGW_OPT_COPY_AHEAD, 1)
+    B.bgw_set_option(ctx.ctx, B.BGW_OPT_DEFER_K1, 1)
+
+    def step():
+        ctx.reset()
+        ctx.upload(device_inputs=pin)
+        ctx.accumulate()
+        B.bgw_chi0_finalize(ctx.ctx, 0, out)
+
+    step()
+    s.synchronize()
+    eager = out.cpu().numpy()
+    assert np.linalg.norm(eager - ref) <= 2e-5 * np.linalg.norm(ref)
+    B.bgw_graph_begin(ctx.ctx)
+    step()
+    B.bgw_graph_end(ctx.ctx)
+    B.bgw_graph_launch(ctx.ctx)
+    step()                                          # copy-ahead again, after the replay
+    B.bgw_graph_launch(ctx.ctx)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), eager)
+    ctx.close()
