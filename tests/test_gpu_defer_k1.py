@@ -227,3 +227,18 @@ def test_copy_ahead_after_graph_replays(gpu_lib):
     s.synchronize()
     assert np.array_equal(out.cpu().numpy(), eager)
     ctx.close()
+
+
+def test_option_values(gpu_lib):
+    B = gpu_lib
+    p = syn.make_problem("si16_q0", nv=2, nc=2)
+    ctx = B.Chi0Context(p, "fp64")
+    for opt in (B.BGW_OPT_DEFER_K1, B.BGW_OPT_COPY_AHEAD):
+        assert B.bgw_get_option(ctx.ctx, opt) == 0
+        B.bgw_set_option(ctx.ctx, opt, 1)
+        assert B.bgw_get_option(ctx.ctx, opt) == 1
+        for bad in (-1, 2):
+            with pytest.raises(B.BgwError):
+                B.bgw_set_option(ctx.ctx, opt, bad)
+        assert B.bgw_get_option(ctx.ctx, opt) == 1
+    ctx.close()
