@@ -258,6 +258,21 @@ def flop_model_q(p, iq=0):
             "contraction": herk, "total": band_fft + pairs * (per_pair_fft + per_pair_rho) + herk}
 
 
+def byte_model(p, csize):
+    """Least DRAM bytes of the two FFT stages in one step (every q-point):
+    the sphere -> grid transform reads each band's coefficients (complex128)
+    and writes its grid once; the matrix elements read the grids of the
+    valence bands at k and the conduction bands at k+q once and write M once
+    (csize bytes per complex value of the path's precision)."""
+    vol = float(np.prod(p.box))
+    coeff = sum(p.nbands * 2 * len(g) * 16.0 for g in p.gvec)
+    grids = p.nk * p.nbands * 2 * vol * csize
+    mtxel = 0.0
+    for q, geps, nc in p.qs:
+        mtxel += p.nk * (p.nv + nc) * 2 * vol * csize + p.nk * p.nv * nc * len(geps) * csize
+    return {"wfn_to_grid": coeff + grids, "mtxel": mtxel}
+
+
 # ---------------------------------------------------------------- oracle --
 
 def oracle_sample(p, k_indices):
@@ -441,11 +456,16 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
              {"wfn_to_grid": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
               "mtxel": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
               "contraction": (sustained / 3, "BF16 sustained / 3 products")})
+    bm = byte_model(p, 16 if precision == "fp64" else 8)
+    hbm = measured_hbm_gbs()
     for name, st in res["stages"].items():
         if name in peaks and st["ms_per_step"] > 0:
             tf = fl[name] / (st["ms_per_step"] * 1e-3) / 1e12
             st.update({"tflops": tf, "peak_tflops": peaks[name][0], "roofline_frac": tf / peaks[name][0],
                        "peak": peaks[name][1]})
+        if name in bm and st["ms_per_step"] > 0:
+            gbs = bm[name] / (st["ms_per_step"] * 1e-3) / 1e9
+            st.update({"hbm_bytes_min": bm[name], "hbm_gbs_min": gbs, "hbm_frac_min": gbs / hbm})
     return res
 
 
