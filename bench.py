@@ -105,6 +105,9 @@ def parse_args():
     ap.add_argument("--copy-ahead", type=int, default=1, choices=[0, 1],
                     help="1 (default): host uploads copy on a second stream, overlapping the transforms; "
                          "0: on the context stream")
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
+                    help="mixed path: 1 (default) contracts each k-chunk on a second stream while the next "
+                         "chunk's matrix elements run; 0: one stream")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")
     ap.add_argument("--alu-peaks", action="store_true",
                     help="only time cuBLAS FP64 and FP32 (no TF32) GEMMs of 8192^3 through torch.matmul "
@@ -392,6 +395,8 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_DEFER_K1, 1)
     if args.copy_ahead:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_COPY_AHEAD, 1)
+    if args.overlap and precision == "mixed":
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_OVERLAP, 1)
     ctx.upload(device_inputs=dev_in)
     tune_span = min(p.nk, 16)
     if fixed_fp64:
@@ -729,7 +734,7 @@ def run_ours(args, world, rank, local):
                            "timing": "one captured CUDA graph per step, replayed; stages from an "
                                      "eager profiled pass of the same steps",
                            "q_points": nq, "pairs_per_q": p.pairs(), "defer_k1": args.defer_k1,
-                           "copy_ahead": args.copy_ahead,
+                           "copy_ahead": args.copy_ahead, "overlap": args.overlap,
                            "l2": "inputs larger than L2 (coefficients "
                            f"{sum(c.nbytes for c in p.coeff) / 1e9:.2f} GB, grids resident per step)"},
                 "tflops": fl["total"] / (ms * 1e-3) / 1e12,

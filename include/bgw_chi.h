@@ -355,6 +355,17 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        call.  Costs one device copy of every k-point's
  *                        coefficients.  Not used during a graph capture nor
  *                        with k-point streaming.  Same grids, bitwise.
+ *   BGW_OPT_OVERLAP      mixed precision only.  0 (default): every step of an
+ *                        accumulate runs on the context stream.  1: each
+ *                        contraction launch runs on a second, high-priority
+ *                        stream of the context while the matrix elements of
+ *                        the next k-chunk are computed on the context stream,
+ *                        its split operands in one of two workspace halves
+ *                        (twice the contraction workspace).  The launches
+ *                        still sum into each accumulator in the same order,
+ *                        so the result is bitwise the same; work queued on
+ *                        the context stream after the call waits for all of
+ *                        it.  Not changeable during a graph capture.
  *   BGW_OPT_TEST_FAIL_ALLOC for failure-handling tests only: when n > 0, the
  *                        n-th device allocation made by the library from now on
  *                        (by any context of the process) fails as if the device
@@ -370,7 +381,8 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  */
 enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
        BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7,
-       BGW_OPT_MTXEL_LANES = 8, BGW_OPT_DEFER_K1 = 9, BGW_OPT_COPY_AHEAD = 10 };
+       BGW_OPT_MTXEL_LANES = 8, BGW_OPT_DEFER_K1 = 9, BGW_OPT_COPY_AHEAD = 10,
+       BGW_OPT_OVERLAP = 11 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

@@ -161,6 +161,7 @@ struct bgw_ctx_s {
     DevBuf S, R;         // sphere -> grid scratch
     DevBuf A, Bs, M, W;  // mtxel scratch, M block, weights
     DevBuf mixed_ws;     // contraction workspace (split operands / FP64 partial sums)
+    size_t ws_half = 0;  // one half of mixed_ws when the contraction is overlapped
     DevBuf freq_dev;
     DevBuf out_stage;    // finalize to host
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
@@ -186,6 +187,9 @@ struct bgw_ctx_s {
     int defer_k1 = 0;             // BGW_OPT_DEFER_K1
     int copy_ahead = 0;           // BGW_OPT_COPY_AHEAD
     cudaStream_t cst = nullptr;   // copy stream of copy-ahead host uploads
+    int overlap = 0;              // BGW_OPT_OVERLAP
+    cudaStream_t gst = nullptr;   // contraction stream of the overlapped mixed path
+    cudaEvent_t ov_fork = nullptr, ov_join = nullptr, ov_free[2] = {nullptr, nullptr};
     int npending = 0;             // uploads whose grid is not built yet
     // k-points summed into the running sum (accumulate calls made since the
     // q-set was installed; replays of a captured graph are not counted)
@@ -193,7 +197,7 @@ struct bgw_ctx_s {
     // stage timing (bgw_profile)
     static constexpr int kStages = 6;
     bool prof = false;
-    struct Rec { int stage; long kernels; cudaEvent_t a, b; };
+    struct Rec { int stage; long kernels; cudaEvent_t a, b; cudaStream_t s; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
     double prof_ms[kStages] = {0};
@@ -209,18 +213,19 @@ struct bgw_ctx_s {
         return e;
     }
     // Bracket a launch group; returns the index to close, or -1.
-    int stage_begin(int stage) {
+    int stage_begin(int stage) { return stage_begin_on(stage, st); }
+    int stage_begin_on(int stage, cudaStream_t s) {
         if (!prof || capturing) return -1;
-        Rec r{stage, 0, take_event(), take_event()};
+        Rec r{stage, 0, take_event(), take_event(), s};
         if (!r.a || !r.b) return -1;
-        cudaEventRecord(r.a, st);
+        cudaEventRecord(r.a, s);
         recs.push_back(r);
         return (int)recs.size() - 1;
     }
     void stage_end(int idx, long kernels) {
         if (idx < 0) return;
         recs[idx].kernels = kernels;
-        cudaEventRecord(recs[idx].b, st);
+        cudaEventRecord(recs[idx].b, recs[idx].s);
     }
     // Fold finished records into the totals (blocks on the stream).
     cudaError_t drain() {
@@ -604,6 +609,24 @@ std::vector<std::pair<size_t, size_t>> form_groups(const bgw_ctx_s *c, const std
     return groups;
 }
 
+// The mixed contraction overlaps the next chunk's matrix elements
+// (BGW_OPT_OVERLAP): split operands in two halves of the workspace, the
+// contraction on its own stream.
+bool overlapped(const bgw_ctx_s *c) { return c->overlap && c->prec != BGW_FP64; }
+
+cudaError_t ensure_overlap_stream(bgw_ctx_s *c) {
+    cudaError_t e = cudaSuccess;
+    if (!c->gst) {
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->gst, cudaStreamNonBlocking, hi);
+    }
+    cudaEvent_t *evs[] = {&c->ov_fork, &c->ov_join, &c->ov_free[0], &c->ov_free[1]};
+    for (cudaEvent_t *ev : evs)
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    return e;
+}
+
 // Scratch for contraction launches of up to kchunk k-points on every q
 // (mixed: the split operands of a whole group of q-points at once).
 cudaError_t ensure_chunk_scratch(bgw_ctx_s *c, const std::vector<QState> &qs, int nfreq, int kchunk) {
@@ -631,7 +654,8 @@ cudaError_t ensure_chunk_scratch(bgw_ctx_s *c, const std::vector<QState> &qs, in
     }
     e = c->M.ensure((size_t)Mbytes, c->st);
     if (e == cudaSuccess) e = c->W.ensure(sizeof(double) * (size_t)kchunk * Pmax * nfreq, c->st);
-    if (e == cudaSuccess && ws) e = c->mixed_ws.ensure(ws, c->st);
+    if (e == cudaSuccess && ws) e = c->mixed_ws.ensure(overlapped(c) ? 2 * ws : ws, c->st);
+    if (e == cudaSuccess) c->ws_half = ws;
     return e;
 }
 
@@ -712,11 +736,30 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
     const double *energy = static_cast<const double *>(c->energy.p);
     const auto groups = form_groups(c, qs, nfreq, kchunk);
     std::vector<bgw::MixedQ> group;
+    // Overlapped: group launch i splits into workspace half i % 2 on the
+    // context stream (after the contraction that last read that half) and
+    // contracts on the contraction stream, in launch order, so every
+    // accumulator sees the same sums in the same order as without overlap.
+    const bool ovl = overlapped(c);
+    if (ovl) {
+        e = ensure_overlap_stream(c);
+        if (e != cudaSuccess) return e;
+    }
+    bool half_used[2] = {false, false};
+    int turn = 0;
+    bool joined = true;
+    auto join = [&]() -> cudaError_t {
+        if (joined) return cudaSuccess;
+        joined = true;
+        cudaError_t r = cudaEventRecord(c->ov_join, c->gst);
+        return r == cudaSuccess ? cudaStreamWaitEvent(c->st, c->ov_join, 0) : r;
+    };
     for (int k0 = k_begin; k0 < k_end; k0 += kchunk) {
         const int kn = std::min(kchunk, k_end - k0);
         for (auto &gr : groups) {
             group.clear();
-            size_t off = 0;
+            size_t off = ovl ? (size_t)turn * c->ws_half : 0;
+            bool wait_half = ovl && half_used[turn];   // before the first split into this half
             for (size_t iq = gr.first; iq < gr.second; ++iq) {
                 QState &s = qs[iq];
                 const long P = (long)c->nv * s.nc;
@@ -727,7 +770,7 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
                     clean = clean && alias_free(c, ik, kp, G0, s);
                     char *Mk = static_cast<char *>(c->M.p) + (size_t)kl * P * s.ng * c->csize;
                     e = launch_mtxel(c, s, ik, kp, G0, 0, c->nv, 0, s.nc, Mk, s.ng, tv, tc);
-                    if (e != cudaSuccess) return e;
+                    if (e != cudaSuccess) return join(), e;
                 }
                 const int PT = (int)(P * kn);
                 {
@@ -735,35 +778,57 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
                     e = bgw::pair_weights(energy, c->nb, c->nv, s.nc, static_cast<const int *>(s.kmap_dev.p),
                                           k0, kn, freq, nfreq, static_cast<double *>(c->W.p), c->st);
                     c->stage_end(rec, 1);
-                    if (e != cudaSuccess) return e;
+                    if (e != cudaSuccess) return join(), e;
                 }
                 if (c->prec == BGW_FP64) {
                     const int rec = c->stage_begin(3);
                     e = bgw::herk_f64(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
                                       s.acc.p, c->mixed_ws.p, c->sm_count, c->st);
                     c->stage_end(rec, 2);
-                    if (e != cudaSuccess) return e;
+                    if (e != cudaSuccess) return join(), e;
                 } else {
                     void *ws = static_cast<char *>(c->mixed_ws.p) + off;
                     off += mixed_q_bytes(c, s, nfreq, kchunk);
+                    if (wait_half) {
+                        wait_half = false;
+                        e = cudaStreamWaitEvent(c->st, c->ov_free[turn], 0);
+                        if (e != cudaSuccess) return join(), e;
+                    }
                     const int rec = c->stage_begin(5);
                     e = bgw::mixed_split(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq, ws,
                                          c->st);
                     c->stage_end(rec, 1);
-                    if (e != cudaSuccess) return e;
+                    if (e != cudaSuccess) return join(), e;
                     group.push_back(bgw::MixedQ{ws, PT, s.ng, s.acc.p});
                 }
             }
             if (c->prec != BGW_FP64) {
-                const int rec = c->stage_begin(3);
-                e = bgw::mixed_gemm(group.data(), (int)group.size(), nfreq, c->sm_count, c->st,
+                cudaStream_t gs = c->st;
+                if (ovl) {
+                    gs = c->gst;
+                    e = cudaEventRecord(c->ov_fork, c->st);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, c->ov_fork, 0);
+                    if (e != cudaSuccess) return join(), e;
+                    joined = false;
+                }
+                const int rec = c->stage_begin_on(3, gs);
+                e = bgw::mixed_gemm(group.data(), (int)group.size(), nfreq, c->sm_count, gs,
                                     static_cast<int *>(c->errflag.p), c->test_drop_load);
                 c->stage_end(rec, 1);
-                if (e != cudaSuccess) return e;
+                if (e == cudaSuccess && ovl) e = cudaEventRecord(c->ov_free[turn], gs);
+                if (e != cudaSuccess) {
+                    join();
+                    return e;
+                }
+                if (ovl) {
+                    half_used[turn] = true;
+                    turn ^= 1;
+                }
             }
         }
     }
-    return e;
+    cudaError_t ej = join();
+    return e != cudaSuccess ? e : ej;
 }
 }  // namespace
 
@@ -1294,6 +1359,11 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
             if (value != 0 && value != 1) return c->fail(BGW_E_ARG, "set_option: copy-ahead must be 0 or 1");
             c->copy_ahead = (int)value;
             return BGW_OK;
+        case BGW_OPT_OVERLAP:
+            if (value != 0 && value != 1) return c->fail(BGW_E_ARG, "set_option: overlap must be 0 or 1");
+            if (c->capturing) return c->fail(BGW_E_STATE, "set_option: overlap cannot change during a capture");
+            c->overlap = (int)value;
+            return BGW_OK;
         case BGW_OPT_TEST_FAIL_ALLOC:
             if (value < 0) return c->fail(BGW_E_ARG, "set_option: allocation count must be >= 0");
             g_fail_alloc.store(value);
@@ -1322,6 +1392,7 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_MTXEL_LANES: *value = c->mtxel_lanes; return BGW_OK;
         case BGW_OPT_DEFER_K1: *value = c->defer_k1; return BGW_OK;
         case BGW_OPT_COPY_AHEAD: *value = c->copy_ahead; return BGW_OK;
+        case BGW_OPT_OVERLAP: *value = c->overlap; return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }
@@ -1565,6 +1636,12 @@ void bgw_destroy(bgw_ctx c) {
             cudaStreamSynchronize(c->cst);
             cudaStreamDestroy(c->cst);
         }
+        if (c->gst) {
+            cudaStreamSynchronize(c->gst);
+            cudaStreamDestroy(c->gst);
+        }
+        for (cudaEvent_t ev : {c->ov_fork, c->ov_join, c->ov_free[0], c->ov_free[1]})
+            if (ev) cudaEventDestroy(ev);
         for (auto &k : c->k) {
             if (k.copied) cudaEventDestroy(k.copied);
             if (k.consumed) cudaEventDestroy(k.consumed);
