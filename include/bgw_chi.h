@@ -356,16 +356,17 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        coefficients.  Not used during a graph capture nor
  *                        with k-point streaming.  Same grids, bitwise.
  *   BGW_OPT_OVERLAP      mixed precision only.  0 (default): every step of an
- *                        accumulate runs on the context stream.  1: each
- *                        contraction launch runs on a second, high-priority
+ *                        accumulate runs on the context stream.  1: the
+ *                        weights, operand split and contraction of each block
+ *                        of matrix elements run on a second, high-priority
  *                        stream of the context while the matrix elements of
- *                        the next k-chunk are computed on the context stream,
- *                        its split operands in one of two workspace halves
- *                        (twice the contraction workspace).  The launches
- *                        still sum into each accumulator in the same order,
- *                        so the result is bitwise the same; work queued on
- *                        the context stream after the call waits for all of
- *                        it.  Not changeable during a graph capture.
+ *                        the next block are computed on the context stream
+ *                        (the blocks alternate between two M buffers: twice
+ *                        the M scratch).  The launches still sum into each
+ *                        accumulator in the same order, so the result is
+ *                        bitwise the same; work queued on the context stream
+ *                        after the call waits for all of it.  Not changeable
+ *                        during a graph capture.
  *   BGW_OPT_TEST_FAIL_ALLOC for failure-handling tests only: when n > 0, the
  *                        n-th device allocation made by the library from now on
  *                        (by any context of the process) fails as if the device

@@ -161,7 +161,7 @@ struct bgw_ctx_s {
     DevBuf S, R;         // sphere -> grid scratch
     DevBuf A, Bs, M, W;  // mtxel scratch, M block, weights
     DevBuf mixed_ws;     // contraction workspace (split operands / FP64 partial sums)
-    size_t ws_half = 0;  // one half of mixed_ws when the contraction is overlapped
+    size_t M_half = 0;   // one half of M when the contraction is overlapped
     DevBuf freq_dev;
     DevBuf out_stage;    // finalize to host
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
@@ -609,9 +609,9 @@ std::vector<std::pair<size_t, size_t>> form_groups(const bgw_ctx_s *c, const std
     return groups;
 }
 
-// The mixed contraction overlaps the next chunk's matrix elements
-// (BGW_OPT_OVERLAP): split operands in two halves of the workspace, the
-// contraction on its own stream.
+// The mixed contraction overlaps the next block's matrix elements
+// (BGW_OPT_OVERLAP): M in two halves, weights, split and contraction on
+// their own stream.
 bool overlapped(const bgw_ctx_s *c) { return c->overlap && c->prec != BGW_FP64; }
 
 cudaError_t ensure_overlap_stream(bgw_ctx_s *c) {
@@ -652,10 +652,11 @@ cudaError_t ensure_chunk_scratch(bgw_ctx_s *c, const std::vector<QState> &qs, in
         e = ensure_mtxel_scratch(c, s, P);
         if (e != cudaSuccess) return e;
     }
-    e = c->M.ensure((size_t)Mbytes, c->st);
+    const size_t mhalf = align256((size_t)Mbytes);
+    e = c->M.ensure(overlapped(c) ? 2 * mhalf : mhalf, c->st);
+    if (e == cudaSuccess) c->M_half = mhalf;
     if (e == cudaSuccess) e = c->W.ensure(sizeof(double) * (size_t)kchunk * Pmax * nfreq, c->st);
-    if (e == cudaSuccess && ws) e = c->mixed_ws.ensure(overlapped(c) ? 2 * ws : ws, c->st);
-    if (e == cudaSuccess) c->ws_half = ws;
+    if (e == cudaSuccess && ws) e = c->mixed_ws.ensure(ws, c->st);
     return e;
 }
 
@@ -736,15 +737,18 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
     const double *energy = static_cast<const double *>(c->energy.p);
     const auto groups = form_groups(c, qs, nfreq, kchunk);
     std::vector<bgw::MixedQ> group;
-    // Overlapped: group launch i splits into workspace half i % 2 on the
-    // context stream (after the contraction that last read that half) and
-    // contracts on the contraction stream, in launch order, so every
-    // accumulator sees the same sums in the same order as without overlap.
+    // Overlapped (mixed): the matrix elements stay on the context stream and
+    // write M blocks alternately into two halves of M; weights, split and
+    // contraction run in order on the contraction stream, each block forked
+    // after its matrix elements, and the matrix elements of a block wait for
+    // the split that last read their half.  Every accumulator sees the same
+    // launches in the same order as on one stream.
     const bool ovl = overlapped(c);
     if (ovl) {
         e = ensure_overlap_stream(c);
         if (e != cudaSuccess) return e;
     }
+    cudaStream_t gs = ovl ? c->gst : c->st;
     bool half_used[2] = {false, false};
     int turn = 0;
     bool joined = true;
@@ -758,72 +762,65 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
         const int kn = std::min(kchunk, k_end - k0);
         for (auto &gr : groups) {
             group.clear();
-            size_t off = ovl ? (size_t)turn * c->ws_half : 0;
-            bool wait_half = ovl && half_used[turn];   // before the first split into this half
+            size_t off = 0;
             for (size_t iq = gr.first; iq < gr.second; ++iq) {
                 QState &s = qs[iq];
                 const long P = (long)c->nv * s.nc;
+                char *M = static_cast<char *>(c->M.p) + (ovl ? (size_t)turn * c->M_half : 0);
+                if (ovl && half_used[turn]) {
+                    e = cudaStreamWaitEvent(c->st, c->ov_free[turn], 0);
+                    if (e != cudaSuccess) return join(), e;
+                }
                 for (int kl = 0; kl < kn; ++kl) {
                     const int ik = k0 + kl;
                     int kp, G0[3];
                     find_umklapp(c, ik, s.q, kp, G0);
                     clean = clean && alias_free(c, ik, kp, G0, s);
-                    char *Mk = static_cast<char *>(c->M.p) + (size_t)kl * P * s.ng * c->csize;
+                    char *Mk = M + (size_t)kl * P * s.ng * c->csize;
                     e = launch_mtxel(c, s, ik, kp, G0, 0, c->nv, 0, s.nc, Mk, s.ng, tv, tc);
                     if (e != cudaSuccess) return join(), e;
                 }
+                if (ovl) {
+                    e = cudaEventRecord(c->ov_fork, c->st);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, c->ov_fork, 0);
+                    if (e != cudaSuccess) return join(), e;
+                    joined = false;
+                }
                 const int PT = (int)(P * kn);
                 {
-                    const int rec = c->stage_begin(2);
+                    const int rec = c->stage_begin_on(2, gs);
                     e = bgw::pair_weights(energy, c->nb, c->nv, s.nc, static_cast<const int *>(s.kmap_dev.p),
-                                          k0, kn, freq, nfreq, static_cast<double *>(c->W.p), c->st);
+                                          k0, kn, freq, nfreq, static_cast<double *>(c->W.p), gs);
                     c->stage_end(rec, 1);
                     if (e != cudaSuccess) return join(), e;
                 }
                 if (c->prec == BGW_FP64) {
                     const int rec = c->stage_begin(3);
-                    e = bgw::herk_f64(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
+                    e = bgw::herk_f64(M, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
                                       s.acc.p, c->mixed_ws.p, c->sm_count, c->st);
                     c->stage_end(rec, 2);
                     if (e != cudaSuccess) return join(), e;
                 } else {
                     void *ws = static_cast<char *>(c->mixed_ws.p) + off;
                     off += mixed_q_bytes(c, s, nfreq, kchunk);
-                    if (wait_half) {
-                        wait_half = false;
-                        e = cudaStreamWaitEvent(c->st, c->ov_free[turn], 0);
-                        if (e != cudaSuccess) return join(), e;
-                    }
-                    const int rec = c->stage_begin(5);
-                    e = bgw::mixed_split(c->M.p, PT, s.ng, static_cast<const double *>(c->W.p), nfreq, ws,
-                                         c->st);
+                    const int rec = c->stage_begin_on(5, gs);
+                    e = bgw::mixed_split(M, PT, s.ng, static_cast<const double *>(c->W.p), nfreq, ws, gs);
                     c->stage_end(rec, 1);
+                    if (e == cudaSuccess && ovl) e = cudaEventRecord(c->ov_free[turn], gs);
                     if (e != cudaSuccess) return join(), e;
+                    if (ovl) {
+                        half_used[turn] = true;
+                        turn ^= 1;
+                    }
                     group.push_back(bgw::MixedQ{ws, PT, s.ng, s.acc.p});
                 }
             }
             if (c->prec != BGW_FP64) {
-                cudaStream_t gs = c->st;
-                if (ovl) {
-                    gs = c->gst;
-                    e = cudaEventRecord(c->ov_fork, c->st);
-                    if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, c->ov_fork, 0);
-                    if (e != cudaSuccess) return join(), e;
-                    joined = false;
-                }
                 const int rec = c->stage_begin_on(3, gs);
                 e = bgw::mixed_gemm(group.data(), (int)group.size(), nfreq, c->sm_count, gs,
                                     static_cast<int *>(c->errflag.p), c->test_drop_load);
                 c->stage_end(rec, 1);
-                if (e == cudaSuccess && ovl) e = cudaEventRecord(c->ov_free[turn], gs);
-                if (e != cudaSuccess) {
-                    join();
-                    return e;
-                }
-                if (ovl) {
-                    half_used[turn] = true;
-                    turn ^= 1;
-                }
+                if (e != cudaSuccess) return join(), e;
             }
         }
     }

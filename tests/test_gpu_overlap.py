@@ -1,10 +1,11 @@
-"""Overlapped mixed contraction (BGW_OPT_OVERLAP): each contraction launch
-runs on a second stream while the next k-chunk's matrix elements are
-computed, its split operands alternating between two workspace halves.  The
-launches sum into every accumulator in the same order, so chi0 must be
-bitwise the plain path's: for one q and for a ragged multi-q batch, over
-k-chunks that give many launches (each half reused several times), across
-accumulate calls, inside a captured graph, and for the autotuner."""
+"""Overlapped mixed contraction (BGW_OPT_OVERLAP): weights, operand split
+and contraction of each block of matrix elements run on a second stream
+while the next block's matrix elements are computed, the blocks alternating
+between two M buffers.  The launches sum into every accumulator in the same
+order, so chi0 must be bitwise the plain path's: for one q and for a ragged
+multi-q batch, over k-chunks that give many blocks (each buffer reused
+several times), across accumulate calls, inside a captured graph, and for
+the autotuner."""
 import numpy as np
 import pytest
 
