@@ -427,11 +427,17 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
 
     for _ in range(max(3, args.warmup)):
         step()
-    # eager, profiled: stage breakdown and per-kernel times
+    # eager, profiled: stage breakdown and per-kernel times, on one stream so
+    # that each kernel's events bracket it alone
+    ovl = args.overlap and precision == "mixed"
+    if ovl:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_OVERLAP, 0)
     B.bgw_profile(ctx.ctx, True)
     ms_eager = timed(step, args.steps)
     prof = B.bgw_profile_read(ctx.ctx)
     B.bgw_profile(ctx.ctx, False)
+    if ovl:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_OVERLAP, 1)
     # graph of one step, replayed
     B.bgw_graph_begin(ctx.ctx)
     step()
@@ -732,7 +738,7 @@ def run_ours(args, world, rank, local):
                 "data": "synthetic",
                 "config": {"workload": desc, "precision": args.precision,
                            "timing": "one captured CUDA graph per step, replayed; stages from an "
-                                     "eager profiled pass of the same steps",
+                                     "eager profiled pass of the same steps on one stream",
                            "q_points": nq, "pairs_per_q": p.pairs(), "defer_k1": args.defer_k1,
                            "copy_ahead": args.copy_ahead, "overlap": args.overlap,
                            "l2": "inputs larger than L2 (coefficients "
