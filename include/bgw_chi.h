@@ -355,6 +355,10 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        call.  Costs one device copy of every k-point's
  *                        coefficients.  Not used during a graph capture nor
  *                        with k-point streaming.  Same grids, bitwise.
+ *                        Replays through bgw_graph_launch are ordered before
+ *                        later copy-ahead copies; a graph the caller captures
+ *                        from the context stream itself is not tracked, so
+ *                        synchronise its replays before the next upload.
  *   BGW_OPT_OVERLAP      mixed precision only.  0 (default): every step of an
  *                        accumulate runs on the context stream.  1: the
  *                        weights, operand split and contraction of each block

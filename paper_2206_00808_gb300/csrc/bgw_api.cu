@@ -344,6 +344,14 @@ int ensure_grid(bgw_ctx_s *c, int ik, cudaError_t &e) {
     return kp.slot;
 }
 
+// The context stream is being captured (through bgw_graph_begin or by the
+// caller): copy-ahead then falls back to copies on the context stream.
+bool st_capturing(const bgw_ctx_s *c) {
+    if (c->capturing) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return c->st && cudaStreamIsCapturing(c->st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 // Copy-ahead host uploads: the copy stream and the k-point's two events.
 cudaError_t ensure_copy_events(bgw_ctx_s *c, KPoint &kp) {
     cudaError_t e = cudaSuccess;
@@ -357,7 +365,7 @@ cudaError_t ensure_copy_events(bgw_ctx_s *c, KPoint &kp) {
 // next copy-ahead copy into the same buffer.  Inside a graph capture the
 // graph's launches are marked instead (bgw_graph_launch).
 cudaError_t mark_consumed(bgw_ctx_s *c, KPoint &kp) {
-    if (!kp.consumed || c->capturing) return cudaSuccess;
+    if (!kp.consumed || st_capturing(c)) return cudaSuccess;
     kp.consumed_set = true;
     return cudaEventRecord(kp.consumed, c->st);
 }
@@ -1034,7 +1042,7 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
             if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: coefficient store");
             kp.coeff_src = static_cast<const double *>(kp.coeff.p);
         }
-    } else if (c->copy_ahead && !on_device && !c->capturing) {
+    } else if (c->copy_ahead && !on_device && !st_capturing(c)) {
         // copy on the copy stream into the k's own buffer, once the last
         // transform that read that buffer has run; the transform waits for it
         e = ensure_copy_events(c, kp);
