@@ -1,13 +1,19 @@
 #!/usr/bin/env python3
 """Benchmark of the spinor polarizability chi0_GG'(q, i w) on GB300.
 
-One step = the whole hot path for one q-point of the Si-like workload
-(FCC a = 10.26 bohr, 24^3 FFT box, ~2000 plane waves per spinor component,
-N_G = 350, 4x4x4 k-grid (N_k = 64), N_v = 8, N_c = 200, omega = 0 plus 4
-imaginary frequencies up to 40 eV, q = (1/4, 0, 0)): every k-point's spinor
-coefficients go to the real-space grid, every (v, c, k) pair's matrix
-elements are formed and contracted into chi0, and chi0 is finalised.
-Inputs are seeded synthetic states of that shape (no DFT data).
+Default workload (the mixed-precision configuration of the metric): the
+GaSb-like cell (FCC a = 11.53 bohr), 32^3 FFT box, ~5000 plane waves per
+spinor component, N_G = 800, 6x6x6 k-grid (N_k = 216), N_v = 18, N_c = 400,
+16 imaginary frequencies in [0, 40] eV, q = (1/6, 0, 0).  One step = the whole
+hot path for one q-point: every k-point's spinor coefficients go to the
+real-space grid, every (v, c, k) pair's matrix elements are formed and
+contracted into chi0 (FP32 FFTs, complex64 M, split-BF16 x3 tensor-core
+contraction, FP64 weights and k reduction), and chi0 is finalised.  The FP64
+path runs in the same line on a labelled k-subset (per-k time x N_k), with
+the mixed path's error against it and both paths' error against the CPU
+oracle on the oracle's timed sample.  Inputs are seeded synthetic states of
+that shape (no DFT data).  The Si-like 24^3 case (FP64 and mixed) is reported
+beside it.
 
 Prints one JSON line (metric q-points/s); see --help.
 """
@@ -29,13 +35,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "si24": (dict(), "Si-like FCC a=10.26 bohr, 24^3 box, N_w~2000 per spinor component, N_G=350, "
-             "N_k=64 (4x4x4), N_v=8, N_c=200, 5 imaginary freqs (0..40 eV), q=(1/4,0,0)"),
+    "gasb32": (dict(config="gasb32"), "GaSb-like FCC a=11.53 bohr, 32^3 box, N_w~5000 per spinor component, "
+                                      "N_G=800, N_k=216 (6x6x6), N_v=18, N_c=400, 16 imaginary freqs (0..40 eV), "
+                                      "q=(1/6,0,0)"),
+    "si24": (dict(config="si24"), "Si-like FCC a=10.26 bohr, 24^3 box, N_w~2000 per spinor component, N_G=350, "
+                                  "N_k=64 (4x4x4), N_v=8, N_c=200, 5 imaginary freqs (0..40 eV), q=(1/4,0,0)"),
     # profiling case: the same per-launch shapes on a 2x2x2 k-grid (< 1 GB on the device)
-    "si24_small": (dict(kgrid=(2, 2, 2), q=(0.5, 0, 0)),
+    "si24_small": (dict(config="si24", kgrid=(2, 2, 2), q=(0.5, 0, 0)),
                    "si24 shapes (24^3, N_G=350, N_v=8, N_c=200, 5 freqs) on a 2x2x2 k-grid, q=(1/2,0,0)"),
-    "gasb32": ("gasb32", "GaSb-like FCC a=11.53 bohr, 32^3 box, N_w~5000 per spinor component, "
-                         "N_G=800, N_k=216 (6x6x6), N_v=18, N_c=400, 16 imaginary freqs, q=(1/6,0,0)"),
     # profiling case: the GaSb-like per-launch shapes on a 2x2x2 k-grid (~2 GB on the device)
     "gasb32_small": (dict(config="gasb32", kgrid=(2, 2, 2), q=(0.5, 0, 0)),
                      "gasb32 shapes (32^3, N_G=800, N_v=18, N_c=400, 16 freqs) on a 2x2x2 k-grid, q=(1/2,0,0)"),
@@ -52,27 +59,13 @@ METRIC = "spinor chi0 q-points/s and TFLOP/s, FP64 vs mixed at ≤2e-5 rel. Frob
 
 # FP64 issue rate of GB300 derived from its nominal 1.25 TFLOP/s over 152 SMs
 # at the 2070 MHz maximum clock: 1.25e12 / (152 * 2.07e9) ~ 4 flop/clk/SM,
-# i.e. 2 DFMA per clock per SM.  Peak = 152 * 2 * 2 * 2.07e9.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-
-# cuBLAS DGEMM 8192^3 through torch.matmul on this GPU type
-# (profiles/alu_peaks_gb300.md; `bench.py --alu-peaks` measures it again).
-MEASURED_DGEMM_TFLOPS = 1.101
+# i.e. 2 DFMA per clock per SM.  Peak = 152 * 2 * 2 * 2.07e9.  The roofline
+# denominator of FP64 ALU stages is the DGEMM rate measured in the same run.
+FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # FP32 FFMA peak from unit counts and clocks: 152 SMs x 128 lanes x 2 flop x
-# 2.07 GHz (cuBLAS SGEMM measures 69.7 TFLOP/s on this GPU type).
+# 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-
-# DRAM bytes (read + write) of one launch, from one ncu capture of the
-# full-size workload with that k-chunk (profiles/traffic_si24.md); valid for
-# the kernel sources they were taken on.  Keyed by (workload, kernel, k-chunk).
-TRAFFIC = {("si24", "k4_herk_f64", 4): 36.19e6 + 44.94e6,
-           ("si24", "k4_herk_f64", 16): 145.66e6 + 67.13e6,
-           ("si24", "k5_gemm", 16): 477.86e6 + 3.10e6}
-
-
-def traffic(workload, kernel, kchunk):
-    return TRAFFIC.get((workload, kernel, kchunk))
 
 
 def parse_args():
@@ -81,16 +74,20 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="gasb32")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
+                    help="precision of the headline value (default mixed)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the other precision (FP64 k-subset leg of a mixed headline, or the mixed "
+                         "comparison of an FP64 one)")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the Si-like 24^3 secondary lines")
+    ap.add_argument("--fp64-ks", type=int, default=4, metavar="N",
+                    help="FP64 leg of a mixed headline: k-points 0..N-1 and the first N k-points with an "
+                         "umklapp (k+q = k'+G0, G0 != 0)")
     ap.add_argument("--no-autotune", action="store_true", help="default tiles and k-chunk")
-    ap.add_argument("--check-fp64", type=int, default=0, metavar="NQ",
-                    help="with --precision mixed: compare the first NQ q-points with one FP64 run")
-    ap.add_argument("--check-kspan", type=int, default=0, metavar="NK",
-                    help="restrict the FP64 comparison to k-points 0..NK-1 (both precisions)")
     ap.add_argument("--grid-slots", type=int, default=-1,
                     help="real-space grid slots (0 = all k resident; default 8 for bi2se3, else 0)")
     ap.add_argument("--kchunk", type=int, default=0, help="k-chunk when not autotuning")
@@ -108,7 +105,9 @@ def parse_args():
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="mixed path: 1 (default) contracts each k-chunk on a second stream while the next "
                          "chunk's matrix elements run; 0: one stream")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si24")
+    ap.add_argument("--traffic-bytes", type=float, default=None,
+                    help="DRAM bytes (read + write) per launch of the dominant kernel from an ncu capture of "
+                         "this configuration and the current sources; without it roofline.traffic is null")
     ap.add_argument("--alu-peaks", action="store_true",
                     help="only time cuBLAS FP64 and FP32 (no TF32) GEMMs of 8192^3 through torch.matmul "
                          "and print them (the measured ALU ceilings for the roofline)")
@@ -141,6 +140,27 @@ def alu_peaks():
         del a, b, c
     out["gpu"] = torch.cuda.get_device_name()
     return out
+
+
+def dgemm_tflops(n=8192, reps=3):
+    """cuBLAS FP64 GEMM rate (torch.matmul, n^3, CUDA events, median of
+    `reps` after one warm-up): the measured ceiling of FP64 ALU stages."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    ts = []
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        if i:
+            ts.append(e0.elapsed_time(e1))
+    del a, b, c
+    return 2 * n ** 3 / (statistics.median(ts) * 1e-3) / 1e12
 
 
 # ----------------------------------------------------------- distributed --
@@ -278,68 +298,197 @@ def byte_model(p, csize):
 
 # ---------------------------------------------------------------- oracle --
 
-def oracle_sample(p, k_indices):
-    """Time the CPU oracle on the given k-points of one q (all bands, all G,
-    all frequencies); returns (seconds, threads)."""
+def umklapp_ks(p, iq=0):
+    """k-points whose k + q leaves the grid's unit cell (k + q = k' + G0 with
+    G0 != 0), in index order."""
+    q = np.asarray(p.qs[iq][0], float)
+    t = np.asarray(p.kcrys, float) + q[None, :]
+    return [int(i) for i in np.nonzero((np.floor(t + 1e-9) != 0).any(1))[0]]
+
+
+def sample_nc(p, flop_target=5e10):
+    """Conduction bands of the oracle's per-k sample: all valence bands and as
+    many conduction bands as keep one k-point near `flop_target` flops of
+    convolution (8 per complex MAC over both spinor components of the sphere
+    per G) and contraction (8 per complex MAC per frequency)."""
+    q, geps, nc = p.qs[0]
+    ngw = float(np.mean([len(g) for g in p.gvec]))
+    per_pair = len(geps) * 2 * ngw * 8 + len(p.freq) * len(geps) ** 2 * 8
+    return int(max(1, min(nc, round(flop_target / per_pair / p.nv))))
+
+
+def with_partners(p, ks):
+    """ks and the grid index of each k + q."""
+    q = np.asarray(p.qs[0][0], float)
+    need = set(ks)
+    for ik in ks:
+        t = np.asarray(p.kcrys[ik]) + q
+        d = np.asarray(p.kcrys) - (t - np.floor(t + 1e-9))[None, :]
+        need.add(int(np.argmin(np.abs(d - np.round(d)).sum(1))))
+    return sorted(need)
+
+
+def host_problem(p, ks):
+    """A copy of problem p holding only the coefficients of ks and their
+    k + q partners, as numpy arrays (device tensors are copied to the host,
+    missing ones generated on the host); every other k's are None."""
+    import copy
+    h = copy.copy(p)
+    need = with_partners(p, ks)
+    h.coeff = [None] * p.nk
+    for ik in need:
+        c = p.coeff[ik]
+        if c is None:
+            from paper_2206_00808_gb300 import synthetic as syn
+            syn.fill_coefficients(h, [ik], on="host")
+        else:
+            h.coeff[ik] = c if isinstance(c, np.ndarray) else c.cpu().numpy()
+    return h
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def host_threads():
+    """Threads the oracle's OpenMP loops use: OMP_NUM_THREADS, else the CPUs
+    this process may run on."""
+    if os.environ.get("OMP_NUM_THREADS"):
+        return int(os.environ["OMP_NUM_THREADS"])
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_SINGLE_THREAD = r"""
+import sys, time, numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_2206_00808_gb300 import synthetic as syn
+d = np.load(sys.argv[2], allow_pickle=True)
+p = d["problem"].item()
+oracle.build()
+t0 = time.perf_counter()
+oracle.chi0(p, k_indices=[int(d["k"])], nc=int(d["nc"]))
+print(time.perf_counter() - t0)
+"""
+
+
+def cpu_baseline(p, with_single_thread=True):
+    """The oracle as it stands on the host cores: all N_v valence bands and a
+    sample of conduction bands at k = 0 and at the first umklapp k-point, all
+    G and frequencies; q-points/s scaled by (N_k / 2) x (N_c / sample).  Also
+    a single-thread run of one k-point with an eighth of that sample.
+    Returns (baseline dict, sampled chi0, sample)."""
     import oracle
     oracle.build()
+    ks = [0, umklapp_ks(p)[0]]
+    ncs = sample_nc(p)
+    hp = host_problem(p, ks)
     t0 = time.perf_counter()
-    oracle.chi0(p, k_indices=k_indices)
+    chi = oracle.chi0(hp, k_indices=ks, nc=ncs)
     dt = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return dt, threads
-
-
-def cpu_baseline(p):
-    ks = [0]
-    dt, cores = oracle_sample(p, ks)
-    qps = 1.0 / (dt * p.nk / len(ks))
-    return {"value": qps, "unit": "q-points/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(ks)} of {p.nk} k-points of one q (all {p.nv}x{p.qs[0][2]} pairs, "
-                      f"N_G={len(p.qs[0][1])}, {len(p.freq)} freqs) in {dt:.1f} s, scaled x{p.nk}"}
+    nc = p.qs[0][2]
+    scale = (p.nk / len(ks)) * (nc / ncs)
+    out = {"value": 1.0 / (dt * scale), "unit": "q-points/s", "cores": host_threads(), "kind": "oracle",
+           "cpu_model": cpu_model(),
+           "sample": f"k-points {ks} of {p.nk} (the second with an umklapp G0) x all {p.nv} valence x "
+                     f"{ncs} of {nc} conduction bands, N_G={len(p.qs[0][1])}, {len(p.freq)} freqs: "
+                     f"{dt:.1f} s, scaled x{scale:.0f}"}
+    if with_single_thread:
+        import tempfile
+        nc1 = max(1, ncs // 8)
+        sub = host_problem(hp, ks[:1])
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "sample.npz")
+            np.savez(path, problem=np.array(sub, dtype=object), k=ks[0], nc=nc1)
+            env = dict(os.environ, OMP_NUM_THREADS="1")
+            r = subprocess.run([sys.executable, "-c", _SINGLE_THREAD, ROOT, path], capture_output=True,
+                               text=True, env=env, timeout=600)
+        if r.returncode == 0:
+            t1 = float(r.stdout.strip().splitlines()[-1])
+            sc1 = p.nk * (nc / nc1)
+            out["single_thread"] = {"value": 1.0 / (t1 * sc1), "unit": "q-points/s", "cores": 1,
+                                    "sample": f"k-point {ks[0]} x all {p.nv} valence x {nc1} conduction bands: "
+                                              f"{t1:.1f} s, scaled x{sc1:.0f}"}
+        else:
+            out["single_thread"] = {"error": r.stderr[-300:]}
+    return out, chi, {"ks": ks, "nc": ncs}
 
 
 # ------------------------------------------------------------------ arms --
 
-def make_workload(name):
+def make_workload(name, coeff_on="cuda"):
+    """(problem, description); coefficients made on the device ("cuda"), on
+    the host ("host"), or left for fill_coefficients (None)."""
     from paper_2206_00808_gb300 import synthetic as syn
     over, desc = WORKLOADS[name]
     if over == "batch":
         return syn.make_batched_problem(), desc
     if over == "bi2se3":
-        return syn.make_bi2se3_problem(), desc
+        return syn.make_bi2se3_problem(device=coeff_on), desc
     if over == "bi2se3_small":
         # generated on the host (torch CPU QR): profilers run this case, and the
         # device QR's lazily loaded library is not found under them
         p = syn.make_bi2se3_problem(kgrid=(2, 2, 2), nv=8, nc=40, q=(0.5, 0, 0), nfreq=2, device="cpu")
         p.coeff = [c.numpy() for c in p.coeff]
         return p, desc
-    if isinstance(over, str):
-        return syn.make_problem(over), desc
     over = dict(over)
-    return syn.make_problem(over.pop("config", "si24"), **over), desc
+    return syn.make_problem(over.pop("config"), coeff_on=coeff_on, **over), desc
 
 
 def run_reference(args, world, rank):
+    """The oracle as it stands, timed on the host cores on this arm's
+    workload and metric: each step one k-point (k = 0 and the first umklapp
+    k-point in turn) with all valence bands and a quarter of the cpu_baseline
+    sample of conduction bands, scaled to one q-point."""
     if rank != 0:
         return 0
-    p, desc = make_workload(args.workload)
-    for _ in range(args.warmup and 1):
-        oracle_sample(p, [0])
-    times = []
-    cores = 1
-    for _ in range(args.steps):
-        dt, cores = oracle_sample(p, [0])
-        times.append(dt * p.nk)
+    import oracle
+    oracle.build()
+    p, desc = make_workload(args.workload, coeff_on=None)
+    ks = [0, umklapp_ks(p)[0]]
+    hp = host_problem(p, ks)
+    nc = p.qs[0][2]
+    ncs = max(1, sample_nc(p) // 4)
+    scale = p.nk * (nc / ncs)
+
+    def one(i):
+        t0 = time.perf_counter()
+        oracle.chi0(hp, k_indices=[ks[i % 2]], nc=ncs)
+        return time.perf_counter() - t0
+
+    for i in range(args.warmup):
+        one(i)
+    times = [one(i) * scale for i in range(args.steps)]
     ms = 1e3 * statistics.mean(times)
     value = 1e3 / ms
+    cores = host_threads()
     line = {"metric": METRIC, "value": value, "unit": "q-points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": desc, "precision": "fp64"},
+            "config": {"workload": desc, "precision": "fp64 (CPU oracle)"},
             "cpu_baseline": {"value": value, "unit": "q-points/s", "cores": cores, "kind": "oracle",
-                             "sample": f"each step: 1 of {p.nk} k-points, scaled x{p.nk}"},
+                             "cpu_model": cpu_model(),
+                             "sample": f"each step: k-point {ks[0]} or {ks[1]} of {p.nk} x all {p.nv} valence x "
+                                       f"{ncs} of {nc} conduction bands, all G and freqs, scaled x{scale:.0f}"},
             "e2e": {"value": value, "unit": "q-points/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -460,9 +609,8 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     # achieved algorithmic rate and roofline fraction of each stage with a FLOP model
     fl = flop_model(p)
     burst, sustained, _ = bf16_peaks()
-    peaks = ({"wfn_to_grid": (FP64_PEAK_TFLOPS, "FP64 ALU (derived)"),
-              "mtxel": (FP64_PEAK_TFLOPS, "FP64 ALU (derived)"),
-              "contraction": (FP64_PEAK_TFLOPS, "FP64 ALU (derived)")}
+    f64 = (args.fp64_peak, "FP64 DGEMM (measured in this run)")
+    peaks = ({"wfn_to_grid": f64, "mtxel": f64, "contraction": f64}
              if precision == "fp64" else
              {"wfn_to_grid": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
               "mtxel": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
@@ -480,7 +628,7 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     return res
 
 
-def epsinv_measure(B, torch, p, res, stream, reps=3):
+def epsinv_measure(B, torch, p, res, stream, fp64_peak, reps=3):
     """The step after chi0: W = eps^-1 v of every frequency of the first
     q-point from the device chi0 of the last timed step (bgw_epsinv, FP64),
     timed with CUDA events on the bench stream; FLOPs = 8 N_G^3 per matrix
@@ -504,7 +652,8 @@ def epsinv_measure(B, torch, p, res, stream, reps=3):
     tf = 8.0 * ng ** 3 * nf / (ms * 1e-3) / 1e12
     return {"what": "W = eps^-1 v(q+G') for every frequency of one q (FP64, blocked Gauss-Jordan on "
                     "the symmetrised eps)", "n_g": ng, "n_freq": nf, "ms_per_q": ms, "tflops": tf,
-            "peak_tflops": FP64_PEAK_TFLOPS, "roofline_frac": tf / FP64_PEAK_TFLOPS}
+            "peak_tflops": fp64_peak, "peak": "FP64 DGEMM (measured in this run)",
+            "roofline_frac": tf / fp64_peak, "derived_fp64_peak_tflops": FP64_PEAK_DERIVED_TFLOPS}
 
 
 def unfold_measure(B, torch, p, dev_in, stream, reps=3):
@@ -518,7 +667,7 @@ def unfold_measure(B, torch, p, dev_in, stream, reps=3):
     Rc = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])   # 120 degrees about (1,1,1)
     R_lat = np.rint(np.linalg.inv(A) @ Rc @ A).astype(np.int32)
     tau = (0.25, 0.25, 0.25)
-    nb = sum(int(c.shape[0]) for c, _ in dev_in)
+    nb = min(16384, sum(int(c.shape[0]) for c, _ in dev_in))
     ngw = len(p.gvec[0])
     g = torch.Generator(device="cuda")
     g.manual_seed(7)
@@ -540,9 +689,10 @@ def unfold_measure(B, torch, p, dev_in, stream, reps=3):
     # per band, spin pair and plane wave: the 2 x 2 complex product, 16 FP64
     # fused multiply-adds (the phase is folded into U once per plane wave)
     dfma = 16.0 * nb * ngw
-    dfma_peak = FP64_PEAK_TFLOPS * 1e12 / 2              # DFMA instructions per second
+    dfma_peak = FP64_PEAK_DERIVED_TFLOPS * 1e12 / 2      # DFMA instructions per second
     del cin, cout
-    return {"what": "c(G) -> U c(R^-1 G) e^{-iG.tau} (FP64), one launch over the bands of every k of the step",
+    return {"what": "c(G) -> U c(R^-1 G) e^{-iG.tau} (FP64), one launch over the bands of the step's "
+                    "k-points (at most 16384) on the sphere of k-point 0",
             "bands": nb, "plane_waves": ngw, "bytes": nbytes, "ms": ms, "gbs": gbs, "peak_gbs": hbm,
             "hbm_frac": gbs / hbm if hbm else None,
             "fp64_fma_per_s": dfma / (ms * 1e-3), "fp64_frac": dfma / (ms * 1e-3) / dfma_peak,
@@ -554,8 +704,11 @@ def e2e_measure(B, torch, p, res, args, dist, stream):
     ctx = res["ctx"]
     q, geps, nc = p.qs[0]
     ng, nf = len(geps), len(p.freq)
-    pin = [(torch.from_numpy(np.ascontiguousarray(p.coeff[ik])).pin_memory(),
-            torch.from_numpy(np.ascontiguousarray(p.energy[ik])).pin_memory()) for ik in range(p.nk)]
+    def pinned(x):
+        t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
+        return torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t)
+
+    pin = [(pinned(p.coeff[ik]), pinned(p.energy[ik])) for ik in range(p.nk)]
     host_out = torch.empty((nf, ng, ng), dtype=torch.complex128).pin_memory()
     h2d = sum(c.numel() * c.element_size() + e.numel() * e.element_size() for c, e in pin)
     d2h = host_out.numel() * host_out.element_size()
@@ -612,6 +765,137 @@ def rel_fro(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
+def error_stats(got, ref):
+    """Relative Frobenius error overall and per frequency, the off-diagonal
+    part's, and the largest entry error relative to the largest entry."""
+    nf, ng = ref.shape[0], ref.shape[1]
+    offd = ~np.eye(ng, dtype=bool)
+    per = [rel_fro(got[j], ref[j]) for j in range(nf)]
+    return {"rel_fro": rel_fro(got, ref), "rel_fro_per_freq": per, "rel_fro_per_freq_max": max(per),
+            "offdiag_rel_fro_max": max(rel_fro(got[j][offd], ref[j][offd]) for j in range(nf)),
+            "max_entry_err_rel_to_max": float(np.abs(got - ref).max() / np.abs(ref).max())}
+
+
+def k_runs(ks):
+    """Contiguous [a, b) runs of a sorted k list."""
+    out = []
+    for k in ks:
+        if out and out[-1][1] == k:
+            out[-1][1] = k + 1
+        else:
+            out.append([k, k + 1])
+    return [tuple(r) for r in out]
+
+
+def chi0_on(B, ctx, qlist, freq, ks):
+    """A new running sum over k-points ks on a context; chi0 of the first q (host)."""
+    B.bgw_chi0_reset(ctx.ctx)
+    for a, b in k_runs(sorted(ks)):
+        B.bgw_chi0_accumulate(ctx.ctx, qlist, freq, a, b)
+    ng = len(qlist[0][1])
+    out = np.zeros((len(freq), ng, ng), dtype=np.complex128)
+    B.bgw_chi0_finalize(ctx.ctx, 0, out)
+    return out
+
+
+def fp64_leg(B, torch, p, args, stream, dev_in, ks, reps=2):
+    """The FP64 path on k-points ks of the workload: every run re-uploads the
+    k-points it reads (so each includes the sphere-to-grid transforms of ks
+    and of their k + q partners), accumulates ks and finalises to the device.
+    Grids live in a few streaming slots, not all N_k.  CUDA events on the
+    stream, one warm-up run, median of `reps`."""
+    need = with_partners(p, ks)
+    ctx = B.Chi0Context(p, "fp64", stream)
+    if len(need) + 2 < p.nk:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_GRID_SLOTS, len(need) + 2)
+    B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk if args.kchunk > 0 else 4)
+    ctx.upload(device_inputs=dev_in)
+    q, geps, nc = p.qs[0]
+    ng, nf = len(geps), len(p.freq)
+    out = torch.empty((nf, ng, ng), dtype=torch.complex128, device="cuda")
+
+    def run():
+        ctx.upload(device_inputs=dev_in, ks=need)
+        B.bgw_chi0_reset(ctx.ctx)
+        for a, b in k_runs(sorted(ks)):
+            ctx.accumulate(a, b)
+        B.bgw_chi0_finalize(ctx.ctx, 0, out)
+
+    run()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    return ctx, out.cpu().numpy(), ms / len(ks)
+
+
+def head_roofline(p, res, precision, args, steps):
+    """Roofline of the dominant stage of the headline (matrix elements or
+    contraction, whichever takes longer): achieved = algorithmic FLOPs of the
+    profiled steps over that stage's summed device time."""
+    fl = flop_model(p)
+    burst, sustained, src = bf16_peaks()
+    st = res["stages"]
+    mt = st.get("mtxel", {}).get("ms_per_step", 0.0)
+    ct = st.get("contraction", {}).get("ms_per_step", 0.0)
+    traffic = args.traffic_bytes
+    note = None if traffic else ("null: per-launch DRAM bytes come from an ncu capture of this configuration "
+                                 "and these sources (pass --traffic-bytes); none is taken by the timed run")
+    if ct >= mt:
+        ach = fl["contraction"] / (ct * 1e-3) / 1e12
+        if precision == "fp64":
+            r = {"bound": "alu", "kernel": "k4_herk_f64", "achieved": ach, "peak": args.fp64_peak,
+                 "unit": "TFLOP/s", "frac": ach / args.fp64_peak,
+                 "peak_source": "FP64 DGEMM measured in this run (torch.matmul 8192^3)",
+                 "derived_fp64_peak_tflops": FP64_PEAK_DERIVED_TFLOPS}
+        else:
+            r = {"bound": "tensor", "kernel": "k5_gemm", "achieved": ach, "peak": sustained / 3,
+                 "unit": "TFLOP/s", "frac": ach / (sustained / 3),
+                 "peak_source": f"{src} BF16 sustained {sustained} TFLOP/s / 3 products"}
+    else:
+        ach = fl["mtxel"] / (mt * 1e-3) / 1e12
+        pk = args.fp64_peak if precision == "fp64" else FP32_PEAK_TFLOPS
+        r = {"bound": "alu", "kernel": "matrix elements (pair density + pruned FFT + gather)",
+             "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+             "peak_source": ("FP64 DGEMM measured in this run" if precision == "fp64" else
+                             "FP32 FFMA from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz")}
+    r["traffic"] = traffic
+    if note:
+        r["traffic_note"] = note
+    return r
+
+
+def secondary(B, torch, args, dist, stream, local, name="si24"):
+    """A smaller workload in both precisions (5 steps after 3 warm-ups each):
+    q-points/s, the mixed/FP64 speedup and the mixed error against FP64."""
+    import copy
+    p, desc = make_workload(name, coeff_on="cuda")
+    dev_in = [(p.coeff[ik], torch.from_numpy(np.ascontiguousarray(p.energy[ik])).cuda())
+              for ik in range(p.nk)]
+    a2 = copy.copy(args)
+    a2.steps, a2.warmup, a2.grid_slots = 5, 3, 0
+    f = measure(B, torch, p, "fp64", a2, dist, stream, dev_in, local, False)
+    ref = [o.cpu().numpy() for o in f["outs"]]
+    f["ctx"].close()
+    m = measure(B, torch, p, "mixed", a2, dist, stream, dev_in, local, False)
+    got = [o.cpu().numpy() for o in m["outs"]]
+    m["ctx"].close()
+    nq = len(p.qs)
+    return {"workload": desc,
+            "fp64": {"value": nq * 1e3 / f["ms"], "unit": "q-points/s", "ms_per_step": f["ms"],
+                     "stages": {k: v["ms_per_step"] for k, v in f["stages"].items()}},
+            "mixed": {"value": nq * 1e3 / m["ms"], "unit": "q-points/s", "ms_per_step": m["ms"],
+                      "stages": {k: v["ms_per_step"] for k, v in m["stages"].items()}, "tuning": m["tuning"]},
+            "speedup_mixed_vs_fp64": f["ms"] / m["ms"],
+            "mixed_vs_fp64": error_stats(got[0], ref[0])}
+
+
 def run_ours(args, world, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -620,7 +904,8 @@ def run_ours(args, world, rank, local):
     build.build()
     from paper_2206_00808_gb300 import binding as B
 
-    p, desc = make_workload(args.workload)
+    args.fp64_peak = dgemm_tflops()
+    p, desc = make_workload(args.workload, coeff_on="cuda")
     if args.grid_slots < 0:
         args.grid_slots = 8 if args.workload == "bi2se3" else 0
     q, geps, nc = p.qs[0]
@@ -633,103 +918,69 @@ def run_ours(args, world, rank, local):
     dev_in = [(dev(p.coeff[ik]), dev(p.energy[ik])) for ik in range(p.nk)]
     fl = flop_model(p)
     steps = args.steps
-
     nq = len(p.qs)
+    other_prec = "fp64" if args.precision == "mixed" else "mixed"
+
     head = measure(B, torch, p, args.precision, args, dist, stream, dev_in, local, True)
     ms = head["ms"]
     value = world * nq * 1e3 / ms
-    con_ms, con_calls, _ = head["prof"]["contraction"]
-    # algorithmic contraction FLOPs of the profiled steps over the kernel's summed device time
-    achieved = fl["contraction"] * steps / (con_ms * 1e-3) / 1e12
-    burst, sustained, src = bf16_peaks()
-    head_kchunk = head["tuning"]["kchunk"] if head["tuning"] else max(1, args.kchunk)
-    if args.precision == "fp64":
-        # The kernel forms conj(M_g) M_g' once per pair (4 FP64 operations) and
-        # weights it per frequency (2 FMAs each): (4 + 2 N_w) operations per
-        # entry and pair where the algorithmic count is 4 N_w multiply-adds.
-        nwc = -(-nf // 5)
-        ops_ratio = (4.0 * nwc + 2.0 * nf) / (4.0 * nf)
-        executed = achieved * ops_ratio
-        roofline = {"bound": "alu", "kernel": "k4_herk_f64", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "executed_fp64_tflops": executed, "executed_frac": executed / FP64_PEAK_TFLOPS,
-                    "executed_over_algorithmic_ops": ops_ratio,
-                    "traffic": traffic(args.workload, "k4_herk_f64", head_kchunk),
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
-                                   "(nominal FP64 1.25 TFLOP/s)",
-                    "measured_dgemm_tflops": MEASURED_DGEMM_TFLOPS,
-                    "executed_frac_of_dgemm": executed / MEASURED_DGEMM_TFLOPS}
-    else:
-        roofline = {"bound": "tensor", "kernel": "k5_gemm", "achieved": achieved,
-                    "peak": sustained / 3, "unit": "TFLOP/s", "frac": achieved / (sustained / 3),
-                    "traffic": traffic(args.workload, "k5_gemm", head_kchunk),
-                    "peak_source": f"{src} BF16 sustained {sustained} / 3 products"}
-    epsinv = epsinv_measure(B, torch, p, head, stream) if args.precision == "fp64" else None
-    unfold = unfold_measure(B, torch, p, dev_in, stream) if args.precision == "fp64" else None
+    roofline = head_roofline(p, head, args.precision, args, steps)
+    epsinv = epsinv_measure(B, torch, p, head, stream, args.fp64_peak)
+    unfold = unfold_measure(B, torch, p, dev_in, stream)
     e2e = None if args.no_e2e else e2e_measure(B, torch, p, head, args, dist, stream)
-    check = None
-    if args.precision == "mixed" and args.check_fp64 > 0:
-        import copy
-        sub = copy.copy(p)
-        sub.qs = p.qs[:args.check_fp64]
-        kspan = args.check_kspan if args.check_kspan > 0 else p.nk
-        res = {}
-        for prec in ("fp64", "mixed"):
-            cx = B.Chi0Context(sub, prec, stream)
-            if args.grid_slots > 0:
-                B.bgw_set_option(cx.ctx, B.BGW_OPT_GRID_SLOTS, args.grid_slots)
-            cx.upload(device_inputs=dev_in)
-            t0 = time.perf_counter()
-            cx.accumulate(0, kspan)
-            res[prec] = [cx.finalize(iq) for iq in range(len(sub.qs))]
-            res[prec + "_s"] = time.perf_counter() - t0
-            cx.close()
-        errs = [rel_fro(g, r) for g, r in zip(res["mixed"], res["fp64"])]
-        check = {"q_points_checked": len(sub.qs), "k_points": kspan,
-                 "rel_fro_err_vs_fp64_max": max(errs), "fp64_seconds": res["fp64_s"],
-                 "error_reference": "the FP64 GPU path (itself within 1e-10 of the CPU oracle)"}
 
-    other = None
-    if args.precision == "fp64" and not args.no_mixed:
-        refs = [o.cpu().numpy() for o in head["outs"]]
-        mix = measure(B, torch, p, "mixed", args, dist, stream, dev_in, local, False)
-        gots = [o.cpu().numpy() for o in mix["outs"]]
-        ref, got = refs[0], gots[0]
-        gm_ms, gm_calls, _ = mix["prof"]["contraction"]
-        gm_ach = fl["contraction"] * steps / (gm_ms * 1e-3) / 1e12
-        pad_r = -(-2 * ng // 128) * 128
-        nt = pad_r // 128
-        kc = mix["tuning"]["kchunk"] if mix["tuning"] else 1
-        pad_k = -(-(kc * p.nv * nc) // 64) * 64
-        executed = 3 * 2.0 * nt * (nt + 1) / 2 * 128 * 128 * pad_k * nf * gm_calls
-        offd = ~np.eye(ng, dtype=bool)
-        other = {"precision": "mixed (FP32 grids/FFT, complex64 M, split-BF16 x3 tcgen05, "
-                              "FP64 weights and k-reduction)",
-                 "value": world * nq * 1e3 / mix["ms"], "unit": "q-points/s", "ms_per_step": mix["ms"],
-                 "ms_per_step_eager": mix["ms_eager"],
-                 "speedup_vs_fp64": ms / mix["ms"],
-                 "rel_fro_err_vs_fp64": max(rel_fro(g, r) for g, r in zip(gots, refs)),
-                 "rel_fro_err_per_freq_max": max(rel_fro(got[j], ref[j]) for j in range(nf)),
-                 "offdiag_rel_fro_err": max(rel_fro(got[j][offd], ref[j][offd]) for j in range(nf)),
-                 "max_entry_err_rel_to_max": float(np.abs(got - ref).max() / np.abs(ref).max()),
-                 "error_reference": "the FP64 GPU path (itself within 1e-10 of the CPU oracle)",
-                 "tflops": fl["total"] / (mix["ms"] * 1e-3) / 1e12,
-                 "stages": mix["stages"], "gpu_launches": mix["gpu_launches"],
-                 "tuning": mix["tuning"],
-                 "roofline": {"bound": "tensor", "kernel": "k5_gemm", "achieved": gm_ach,
-                              "peak": sustained / 3, "unit": "TFLOP/s",
-                              "frac": gm_ach / (sustained / 3),
-                              "executed_bf16_tflops": executed / (gm_ms * 1e-3) / 1e12,
-                              "executed_frac_of_bf16": executed / (gm_ms * 1e-3) / 1e12 / sustained,
-                              "traffic": traffic(args.workload, "k5_gemm", kc),
-                              "peak_source": f"{src} BF16 sustained {sustained} TFLOP/s / 3 products"}}
-        mix["ctx"].close()
+    # the other precision: FP64 on a labelled k-subset (mixed headline), or
+    # the whole mixed step (FP64 headline)
+    other, octx = None, None
+    if not args.no_other and nq == 1:
+        if args.precision == "mixed":
+            n = min(args.fp64_ks, p.nk)
+            umk = umklapp_ks(p)
+            ks = sorted(set(range(n)) | set(umk[:n]))
+            octx, chi64, per_k = fp64_leg(B, torch, p, args, stream, dev_in, ks)
+            chimx = chi0_on(B, head["ctx"], [(q, geps, nc)], p.freq, ks)
+            ms64 = per_k * p.nk
+            other = {"precision": "fp64 (FP64 grids, FFTs, M and contraction)",
+                     "k_subset": ks, "k_subset_note": f"k = 0..{n - 1} and the first {n} k-points with an "
+                                                      "umklapp; per-k time x N_k",
+                     "ms_per_k": per_k, "ms_per_q_extrapolated": ms64,
+                     "value": world * 1e3 / ms64, "unit": "q-points/s (extrapolated from the k-subset)",
+                     "speedup_mixed_vs_fp64": ms64 / ms,
+                     "mixed_vs_fp64_on_subset": error_stats(chimx, chi64),
+                     "error_reference": "the FP64 GPU path on the same k-subset"}
+        else:
+            mix = measure(B, torch, p, "mixed", args, dist, stream, dev_in, local, False)
+            ref = head["outs"][0].cpu().numpy()
+            got = mix["outs"][0].cpu().numpy()
+            other = {"precision": "mixed (FP32 grids/FFT, complex64 M, split-BF16 x3 tcgen05, "
+                                  "FP64 weights and k-reduction)",
+                     "value": world * nq * 1e3 / mix["ms"], "unit": "q-points/s", "ms_per_step": mix["ms"],
+                     "speedup_mixed_vs_fp64": ms / mix["ms"],
+                     "mixed_vs_fp64": error_stats(got, ref),
+                     "stages": mix["stages"], "tuning": mix["tuning"],
+                     "roofline": head_roofline(p, mix, "mixed", args, steps)}
+            octx = mix["ctx"]
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p)
+    cpu, oracle_check = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and nq == 1:
+        cpu, chis, smp = cpu_baseline(p)
+        ql = [(q, geps, smp["nc"])]
+        oracle_check = {"sample": f"k-points {smp['ks']}, all {p.nv} valence x {smp['nc']} conduction bands, "
+                                  f"all {ng} G and {nf} freqs (the cpu_baseline run)"}
+        for prec, cx in ((args.precision, head["ctx"]), (other_prec, octx)):
+            if cx is not None:
+                oracle_check[prec] = error_stats(chi0_on(B, cx, ql, p.freq, smp["ks"]), chis)
+    if octx is not None:
+        octx.close()
+
+    sec = None
+    if rank == 0 and not args.no_secondary and args.workload != "si24":
+        head["ctx"].close()
+        head["ctx"] = None
+        sec = secondary(B, torch, args, dist, stream, local)
 
     if rank == 0:
+        coeff_gb = sum(c.numel() * c.element_size() for c, _ in dev_in) / 1e9
         line = {"metric": METRIC, "value": value, "unit": "q-points/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "ms_per_step_eager": head["ms_eager"],
@@ -741,17 +992,19 @@ def run_ours(args, world, rank, local):
                                      "eager profiled pass of the same steps on one stream",
                            "q_points": nq, "pairs_per_q": p.pairs(), "defer_k1": args.defer_k1,
                            "copy_ahead": args.copy_ahead, "overlap": args.overlap,
-                           "l2": "inputs larger than L2 (coefficients "
-                           f"{sum(c.nbytes for c in p.coeff) / 1e9:.2f} GB, grids resident per step)"},
+                           "l2": f"inputs larger than L2 (coefficients {coeff_gb:.2f} GB, grids resident "
+                                 "per step)"},
                 "tflops": fl["total"] / (ms * 1e-3) / 1e12,
                 "pairs_per_s": value / nq * sum(p.pairs(i) for i in range(nq)),
                 "stages": head["stages"],
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "epsinv": epsinv, "unfold": unfold,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
-                "tuning": head["tuning"], "fp64_check": check,
-                "mixed": other}
+                "tuning": head["tuning"], "fp64_dgemm_tflops": args.fp64_peak,
+                "other_precision": other, "oracle_check": oracle_check,
+                "epsinv": epsinv, "unfold": unfold, "secondary": sec}
         print(json.dumps(line), flush=True)
-    head["ctx"].close()
+    if head["ctx"] is not None:
+        head["ctx"].close()
     dist.close()
     return 0
 

@@ -442,15 +442,24 @@ BGW_API bgw_status bgw_profile_read(bgw_ctx ctx, double *ms, long *calls, long *
  *   M_dev  : DEVICE complex128 [nv][nc][ng]
  *   stream : cudaStream_t (NULL = default stream); asynchronous
  * Scratch: one static device array of BGW_NOALLOC_SCRATCH_BYTES inside the
- * library, reserved on every GPU that loads it until the process exits.  A
- * call whose pairs need more (about nv*nc*N1*N2*(w3 + w2*w3/N2)*16 bytes,
- * w the sphere's extent per axis) is rejected with BGW_E_ARG; split the band
- * range.  Every call shares the array and fully rewrites what it reads, so
- * nothing needs clearing, but calls that overlap on the GPU (different
- * streams or devices' threads racing on one device) corrupt each other:
- * serialise them.  The first call on a device sets up that device (FFT tables
- * and the array's device address); make it before any stream capture.
- * Errors go to bgw_last_error(NULL).
+ * library, reserved on every GPU that loads it until the process exits.  The
+ * call runs in blocks of whole valence bands sized to fit it; only a call
+ * where one valence band with all nc conduction bands needs more (about
+ * nc*N1*N2*(w3 + w2*w3/N2)*16 bytes, w the sphere's extent per axis) is
+ * rejected with BGW_E_ARG; split the conduction range then.  Every call
+ * shares the array and fully rewrites what it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU (different streams or host
+ * threads racing on one device) corrupt each other: serialise them.
+ * Uv, Uc and M_dev must be device (or managed) memory of the current device
+ * (checked with cudaPointerGetAttributes; BGW_E_ARG otherwise); their sizes
+ * cannot be checked here, so the shapes above are the caller's promise.
+ * The sphere map is copied from a static pageable host array, so the call
+ * waits for earlier work on `stream` before it returns, and it is rejected
+ * with BGW_E_ARG while `stream` is being captured (a captured copy would read
+ * that array at replay time).  The first call on a device sets up that
+ * device (FFT tables and the array's device address); make it before any
+ * stream capture.  Errors go to bgw_last_error(NULL), which keeps one
+ * message per host thread.
  */
 #define BGW_NOALLOC_SCRATCH_BYTES (64u << 20)
 BGW_API bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv, const void *Uc,
@@ -460,7 +469,8 @@ BGW_API bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv, co
 /* Release every device buffer of the context (synchronizes its stream). */
 BGW_API void bgw_destroy(bgw_ctx ctx);
 
-/* Message of the last failing call on ctx (NULL ctx: last failed create). */
+/* Message of the last failing call on ctx (NULL ctx: the last failed create or
+   context-free call of the calling host thread). */
 BGW_API const char *bgw_last_error(bgw_ctx ctx);
 
 #ifdef __cplusplus

@@ -129,16 +129,24 @@ def umklapp(kcrys: np.ndarray, ik: int, q) -> tuple[int, np.ndarray]:
     raise ValueError(f"k + q is not on the k-grid (k index {ik}, q = {q})")
 
 
-def chi0(problem, iq: int = 0, k_indices=None, nc=None) -> np.ndarray:
+def chi0(problem, iq: int = 0, k_indices=None, nc=None, g_indices=None,
+         contraction: str = "loop") -> np.ndarray:
     """chi0[j][G][G'] (complex128, eV^-1) of a synthetic Problem for q-point iq.
 
     Sums k over `k_indices` (default: every k, in index order) and always
     divides by the full N_k, so a subset gives that subset's share of the sum.
+    g_indices: only the G-vectors geps[g_indices] (rows and columns of that
+    block of chi0; each M(G) is an independent convolution sum).
+    contraction: "loop" (the C triple loop) or "matmul" (the same sum as the
+    library product A^H diag(w_j) A with A = M as a pairs x G matrix, for the
+    large cases; pinned against the loop on the CPU).
     """
     lib = _load()
     q, geps, ncq = problem.qs[iq]
     if nc is not None:
         ncq = nc
+    if g_indices is not None:
+        geps = np.asarray(geps)[np.asarray(g_indices)]
     nv = problem.nv
     ng = len(geps)
     freq = _f64(problem.freq)
@@ -148,7 +156,14 @@ def chi0(problem, iq: int = 0, k_indices=None, nc=None) -> np.ndarray:
         kp, G0 = umklapp(problem.kcrys, ik, q)
         M = mtxel(problem.box, problem.gvec[ik], problem.coeff[ik][:nv],
                   problem.gvec[kp], problem.coeff[kp][nv:nv + ncq], G0, geps)
-        chi0_accumulate(M, problem.energy[ik][:nv], problem.energy[kp][nv:nv + ncq], freq, chi)
+        e_v, e_c = problem.energy[ik][:nv], problem.energy[kp][nv:nv + ncq]
+        if contraction == "loop":
+            chi0_accumulate(M, e_v, e_c, freq, chi)
+        else:
+            A = M.reshape(nv * ncq, ng)
+            w = np.array([[weight(a, b, f) for a in e_v for b in e_c] for f in freq])
+            for j in range(len(freq)):
+                chi[j] += (A.conj().T * w[j][None, :]) @ A
     flat = chi.reshape(-1).view(np.float64)
     lib.oracle_scale(flat.size, 1.0 / problem.nk, _ptr(flat))
     return chi

@@ -287,14 +287,24 @@ def bgw_profile_read(ctx) -> dict:
 def bgw_mtxel_spinor_noalloc(fft, Uv, Uc, nv: int, nc: int, G0, gvec, M_dev, stream=None) -> int:
     """Allocation-free FP64 matrix elements from device grids Uv [nv][2][N^3]
     and Uc [nc][2][N^3] (complex128 tensors) into M_dev [nv][nc][ng]."""
+    import torch
     f = np.ascontiguousarray(fft, dtype=np.int32)
     g0 = np.ascontiguousarray(G0, dtype=np.int32)
     g = np.ascontiguousarray(gvec, dtype=np.int32)
-    pv, dv = _ptr_and_device(Uv)
-    pc, dc = _ptr_and_device(Uc)
-    pm, dm = _ptr_and_device(M_dev)
-    if not (dv and dc and dm):
-        raise ValueError("Uv, Uc and M_dev must be device tensors")
+    nbox = int(np.prod(f))
+    cur = torch.cuda.current_device()
+    for name, t, n in (("Uv", Uv, nv * 2 * nbox), ("Uc", Uc, nc * 2 * nbox), ("M_dev", M_dev, nv * nc * len(g))):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.complex128 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous complex128 tensor")
+        if t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} elements, the call needs {n}")
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    pv, _ = _ptr_and_device(Uv)
+    pc, _ = _ptr_and_device(Uc)
+    pm, _ = _ptr_and_device(M_dev)
     return _check(_lib.bgw_mtxel_spinor_noalloc(_host_ptr(f), pv, pc, nv, nc, _host_ptr(g0), len(g),
                                                 _host_ptr(g), pm, _stream_handle(stream)), None)
 

@@ -20,6 +20,9 @@
 #include "../../include/bgw_chi.h"
 #include "bgw_internal.h"
 
+// Defined in bgw_api.cu: the message bgw_last_error(NULL) returns.
+void bgw_set_global_error(const std::string &msg);
+
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[BGW_NOALLOC_SCRATCH_BYTES];
@@ -78,10 +81,19 @@ bgw_status setup_device(int dev, void **scratch, std::string &err) {
     return BGW_OK;
 }
 
-}  // namespace
+// A device pointer of the current device (or managed memory it can reach);
+// cudaPointerGetAttributes allocates nothing.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
 
-// Defined in bgw_api.cu: the message bgw_last_error(NULL) returns.
-void bgw_set_global_error(const std::string &msg);
+}  // namespace
 
 extern "C" bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv, const void *Uc,
                                                int nv, int nc, const int G0[3], int ng,
@@ -117,20 +129,39 @@ extern "C" bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv,
     const bool scatter = bgw::mtxel_scatter_mode(ax, 16);
     const long nmap = ng + (scatter ? cube : 0);
     const long P = (long)nv * nc;
-    const long PB = (long)bgw::mtxel_v_batch(nv, nc, ax, 16) * nc;   // pairs per kernel batch
+    // Scratch of one block of vb valence bands: the sphere map, then the
+    // kernels' z-pass (where used) and y-pass buffers for vb * nc pairs.  The
+    // call runs in blocks of whole valence bands sized to the array.
     const size_t gbytes = round_up(sizeof(int) * (size_t)nmap);
-    const size_t abytes = bgw::mtxel_uses_a(ax) ? round_up((size_t)PB * fft[0] * fft[1] * ax.w[2] * 16) : 0;
-    const size_t bbytes = round_up((size_t)PB * fft[0] * ax.w[1] * ax.w[2] * 16);
-    const size_t need = gbytes + abytes + bbytes;
-    if (need > (size_t)BGW_NOALLOC_SCRATCH_BYTES)
-        return fail(BGW_E_ARG, "mtxel_noalloc: " + std::to_string(P) + " pairs need " +
-                                   std::to_string(need) + " bytes of scratch, more than the " +
-                                   std::to_string((size_t)BGW_NOALLOC_SCRATCH_BYTES) +
-                                   "-byte maximum; split the band range");
+    const size_t a_pair = bgw::mtxel_uses_a(ax) ? (size_t)fft[0] * fft[1] * ax.w[2] * 16 : 0;
+    const size_t b_pair = (size_t)fft[0] * ax.w[1] * ax.w[2] * 16;
+    auto need = [&](long vb) {
+        const long pb = (long)std::min(vb, (long)bgw::mtxel_v_batch((int)vb, nc, ax, 16)) * nc;
+        return gbytes + round_up((size_t)pb * a_pair) + round_up((size_t)pb * b_pair);
+    };
+    const size_t cap = (size_t)BGW_NOALLOC_SCRATCH_BYTES;
+    if (P > 0 && need(1) > cap)
+        return fail(BGW_E_ARG, "mtxel_noalloc: one valence band with " + std::to_string(nc) +
+                                   " conduction bands needs " + std::to_string(need(1)) +
+                                   " bytes of scratch, more than the " + std::to_string(cap) +
+                                   "-byte maximum; split the conduction range");
     if (P == 0) return BGW_OK;
+    long vb = nv;
+    while (vb > 1 && need(vb) > cap) vb = std::max(1L, std::min(vb - 1, vb * (long)cap / (long)need(vb)));
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(BGW_E_CUDA, std::string("mtxel_noalloc: ") + cudaGetErrorString(e));
+    if (!on_device(Uv, dev) || !on_device(Uc, dev) || !on_device(M_dev, dev))
+        return fail(BGW_E_ARG, "mtxel_noalloc: Uv, Uc and M_dev must be device memory of the current device " +
+                                   std::to_string(dev));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // The sphere map goes through a static host array: a captured copy would
+    // read it at replay time, after later calls have rewritten it.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return fail(BGW_E_CUDA, std::string("mtxel_noalloc: ") + cudaGetErrorString(e));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(BGW_E_ARG, "mtxel_noalloc: the stream is being captured; this call cannot be captured");
     void *scratch = nullptr;
     const bgw_status s = setup_device(dev, &scratch, err);
     if (s != BGW_OK) return fail(s, err);
@@ -147,14 +178,21 @@ extern "C" bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv,
             g_gmap_host[ng + cell] = (int)g;
         }
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(scratch);
     int *gmap = reinterpret_cast<int *>(base);
-    // pageable source: the copy has read g_gmap_host when this call returns
+    const long pb = (long)std::min(vb, (long)bgw::mtxel_v_batch((int)vb, nc, ax, 16)) * nc;
+    char *abuf = base + gbytes;
+    char *bbuf = abuf + round_up((size_t)pb * a_pair);
+    // pageable source: the copy waits for earlier work on the stream and has
+    // read g_gmap_host when this call returns
     e = cudaMemcpyAsync(gmap, g_gmap_host, sizeof(int) * (size_t)nmap, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, ng, base + gbytes, base + gbytes + abytes, M_dev,
-                           ng, st);
+    const long nbox = (long)fft[0] * fft[1] * fft[2];
+    for (long v0 = 0; e == cudaSuccess && v0 < nv; v0 += vb) {
+        const int n = (int)std::min(vb, (long)nv - v0);
+        const void *uv = static_cast<const char *>(Uv) + (size_t)v0 * 2 * nbox * 16;
+        void *m = static_cast<char *>(M_dev) + (size_t)v0 * nc * ng * 16;
+        e = bgw::mtxel_f64(uv, Uc, n, nc, ax, gmap, ng, abuf, bbuf, m, ng, st);
+    }
     if (e != cudaSuccess) return fail(BGW_E_CUDA, std::string("mtxel_noalloc: ") + cudaGetErrorString(e));
     return BGW_OK;
 }

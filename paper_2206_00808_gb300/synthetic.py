@@ -38,7 +38,7 @@ __all__ = [
     "wfn_sphere", "eps_sphere", "spinor_coefficients", "band_energies",
     "make_problem", "make_batched_problem", "make_bi2se3_problem", "spinor_coefficients_device",
     "CONFIGS", "spinless_to_spinor", "rotate_spin",
-    "plane_wave_bands",
+    "plane_wave_bands", "fill_coefficients",
 ]
 
 
@@ -167,6 +167,7 @@ class Problem:
     qs: list                    # list of (q crystal (3,), eps sphere (N_G,3) int32, nc(q))
     freq: np.ndarray            # (N_omega,) eV, imaginary-axis magnitudes
     precision: str = "fp64"
+    config_id: int = -1         # seed of the coefficient generator (fill_coefficients)
 
     @property
     def nk(self) -> int:
@@ -180,8 +181,26 @@ class Problem:
         return self.nk * self.nv * self.qs[iq][2]
 
 
+def _coefficients(config_id, ik, ngw, nbands, on):
+    """Coefficients of one k: numpy ("host"), torch on a CUDA device ("cuda"),
+    or None (generated later by fill_coefficients)."""
+    if on is None:
+        return None
+    if on == "host":
+        return spinor_coefficients(config_id, ik, ngw, nbands)
+    return spinor_coefficients_device(config_id, ik, ngw, nbands, on)
+
+
+def fill_coefficients(p: "Problem", ks, on="host"):
+    """Generate the coefficients of k-points `ks` of a problem made with
+    coeff_on=None (or replace them), on the host or a CUDA device."""
+    for ik in ks:
+        p.coeff[ik] = _coefficients(p.config_id, ik, len(p.gvec[ik]), p.nbands, on)
+    return p
+
+
 def _fcc_problem(name, config_id, a, box, ecut_wfn, ng, kgrid, nv, nc, q, nfreq,
-                 precision):
+                 precision, coeff_on="host"):
     avec = fcc_cell(a)
     bvec = reciprocal(avec)
     kc = kgrid_points(kgrid)
@@ -189,13 +208,13 @@ def _fcc_problem(name, config_id, a, box, ecut_wfn, ng, kgrid, nv, nc, q, nfreq,
     for ik in range(len(kc)):
         g = wfn_sphere(bvec, kc[ik], ecut_wfn)
         gvec.append(g)
-        coeff.append(spinor_coefficients(config_id, ik, len(g), nv + nc))
+        coeff.append(_coefficients(config_id, ik, len(g), nv + nc, coeff_on))
         energy.append(band_energies(config_id, ik, nv, nc))
     q = np.asarray(q, float)
     qs = [(q, eps_sphere(bvec, q, ng), nc)]
     freq = np.linspace(0.0, 40.0, nfreq) if nfreq > 1 else np.zeros(1)
     return Problem(name, avec, tuple(box), tuple(kgrid), kc, nv, nc, gvec, coeff, energy,
-                   qs, freq, precision)
+                   qs, freq, precision, config_id)
 
 
 # Workloads: Si-like (FCC 10.26 bohr) and GaSb-like (FCC 11.53 bohr) cells from
@@ -253,7 +272,8 @@ def make_bi2se3_problem(config_id: int = 4, box=(64, 64, 64), ecut_wfn: float = 
                         nfreq: int = 8, device="cuda") -> Problem:
     """Bi2Se3-like rhombohedral cell (hexagonal a = 4.143 A, c = 28.636 A),
     64^3 box, ~9000 plane waves per spinor component, N_G = 2000; the
-    coefficients are generated on the device (torch tensors)."""
+    coefficients are generated on the device (torch tensors), or not at all
+    with device=None (fill_coefficients makes them per k)."""
     avec = rhombohedral_cell(4.143 * BOHR_PER_ANGSTROM, 28.636 * BOHR_PER_ANGSTROM)
     bvec = reciprocal(avec)
     kc = kgrid_points(kgrid)
@@ -261,16 +281,21 @@ def make_bi2se3_problem(config_id: int = 4, box=(64, 64, 64), ecut_wfn: float = 
     for ik in range(len(kc)):
         gk = wfn_sphere(bvec, kc[ik], ecut_wfn)
         gvec.append(gk)
-        coeff.append(spinor_coefficients_device(config_id, ik, len(gk), nv + nc, device))
+        coeff.append(None if device is None else spinor_coefficients_device(config_id, ik, len(gk), nv + nc,
+                                                                            device))
         energy.append(band_energies(config_id, ik, nv, nc))
     qv = np.asarray(q, float)
     freq = np.linspace(0.0, 40.0, nfreq) if nfreq > 1 else np.zeros(1)
-    return Problem("bi2se3", avec, tuple(box), tuple(kgrid), kc, nv, nc, gvec, coeff, energy,
-                   [(qv, eps_sphere(bvec, qv, ng), nc)], freq, "mixed")
+    p = Problem("bi2se3", avec, tuple(box), tuple(kgrid), kc, nv, nc, gvec, coeff, energy,
+                [(qv, eps_sphere(bvec, qv, ng), nc)], freq, "mixed", config_id)
+    return p
 
 
 def make_problem(name: str, **overrides) -> Problem:
-    """Build a named workload; `overrides` change any of its sizes."""
+    """Build a named workload; `overrides` change any of its sizes, and
+    coeff_on = "host" (default, numpy), "cuda" (torch on the device) or None
+    (no coefficients yet: fill_coefficients) says where the coefficients are
+    made."""
     spec = dict(CONFIGS[name])
     spec.update(overrides)
     return _fcc_problem(name, **spec)

@@ -31,3 +31,30 @@ def test_flop_model_scales_with_pairs_and_frequencies():
 
 def test_measured_hbm_rate_is_positive():
     assert bench.measured_hbm_gbs() > 1000.0
+
+
+def test_umklapp_and_partner_bookkeeping():
+    p = syn.make_problem("gasb32", coeff_on=None)
+    umk = bench.umklapp_ks(p)
+    # k1 = 5/6 (indices 180..215) is where k + q = k' + (1, 0, 0) on the 6x6x6 grid
+    assert umk == list(range(180, 216))
+    assert bench.with_partners(p, [0, 3, 180]) == [0, 3, 36, 39, 180]
+    assert bench.k_runs([0, 1, 2, 3, 180, 181, 183]) == [(0, 4), (180, 182), (183, 184)]
+
+
+def test_error_stats_of_a_known_perturbation():
+    rng = np.random.default_rng(3)
+    ref = rng.standard_normal((2, 4, 4)) + 1j * rng.standard_normal((2, 4, 4))
+    got = ref.copy()
+    got[1, 0, 1] += 1e-3
+    e = bench.error_stats(got, ref)
+    assert e["rel_fro_per_freq"][0] == 0.0
+    assert np.isclose(e["rel_fro_per_freq"][1], 1e-3 / np.linalg.norm(ref[1]))
+    assert np.isclose(e["max_entry_err_rel_to_max"], 1e-3 / np.abs(ref).max())
+    assert e["offdiag_rel_fro_max"] > 0 and np.isclose(e["rel_fro"], 1e-3 / np.linalg.norm(ref))
+
+
+def test_oracle_sample_sizes():
+    p = syn.make_problem("gasb32", coeff_on=None)
+    assert 1 <= bench.sample_nc(p) < p.nc
+    assert bench.sample_nc(syn.make_problem("si18_qx")) == 24

@@ -445,3 +445,37 @@ def test_epsinv_head_row_is_identity_when_v_is_zero():
     e, w = oracle.epsinv(chi, v)
     assert np.allclose(e[0][0], np.eye(n)[0], atol=1e-15)
     assert np.abs(w[0][:, 0]).max() == 0.0
+
+
+# ------------------------------------------- large-case forms of the oracle --
+
+def test_matmul_contraction_equals_the_loop_and_bruteforce():
+    """The library-product form of the chi0 sum (used for the full-size
+    parity cases) equals the plain loop, and both the real-space brute force."""
+    rng = np.random.default_rng(11)
+    p = tiny_problem(rng, nv=3, nc=4, freq=(0.0, 2.5, 9.0))
+    loop = oracle.chi0(p)
+    mm = oracle.chi0(p, contraction="matmul")
+    assert np.linalg.norm(mm - loop) <= 1e-13 * np.linalg.norm(loop)
+    # brute force of one k-point's share: real-space M, the bracket in complex form
+    ik = 1
+    kp, G0 = oracle.umklapp(p.kcrys, ik, p.qs[0][0])
+    uv = realspace_u(p.box, p.gvec[ik], p.coeff[ik][:p.nv])
+    uc = realspace_u(p.box, p.gvec[kp], p.coeff[kp][p.nv:], shift=G0)
+    M = realspace_M(p.box, uv, uc, p.qs[0][1]).reshape(-1, len(p.qs[0][1]))
+    d = (p.energy[ik][:p.nv, None] - p.energy[kp][None, p.nv:]).reshape(-1)
+    share = oracle.chi0(p, k_indices=[ik], contraction="matmul")
+    for j, f in enumerate(p.freq):
+        w = (1.0 / (d - 1j * f) + 1.0 / (d + 1j * f)).real
+        want = (M.conj().T * w) @ M / p.nk
+        assert np.abs(share[j] - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_g_subset_is_the_block_of_the_full_chi0():
+    """chi0 over a subset of the dielectric sphere is exactly that block of the
+    full chi0 (every M(G) is its own convolution sum)."""
+    p = syn.make_problem("si18_qx", nv=2, nc=3, nfreq=2)
+    full = oracle.chi0(p)
+    S = [0, 3, 40, 99, 136]
+    sub = oracle.chi0(p, g_indices=S)
+    assert np.array_equal(sub, full[:, S][:, :, S])

@@ -31,14 +31,14 @@ def grids(torch, p, ik, bands):
     return torch.from_numpy(np.ascontiguousarray(u.reshape(len(c), 2, -1))).cuda()
 
 
-def test_noalloc_matches_context_mtxel_on_two_calls(gpu_lib):
-    torch = pytest.importorskip("torch")
-    p = syn.make_problem("si18_qx")
+def compare_with_context(gpu_lib, torch, p, iks):
+    """Two (or more) calls in a row of the allocation-free entry point against
+    bgw_mtxel_spinor of a context on the same k-points."""
     q, geps, nc = p.qs[0]
     ng = len(geps)
     ctx = gpu_lib.Chi0Context(p, "fp64")
     ctx.upload()
-    for ik in (4, 0):          # an umklapp k first, then a plain one
+    for ik in iks:
         kp, G0 = oracle.umklapp(p.kcrys, ik, q)
         ref = torch.zeros((p.nv, nc, ng), dtype=torch.complex128, device="cuda")
         gpu_lib.bgw_mtxel_spinor(ctx.ctx, q, geps, ik, 0, p.nv, 0, nc, ref)
@@ -54,11 +54,47 @@ def test_noalloc_matches_context_mtxel_on_two_calls(gpu_lib):
     ctx.close()
 
 
+def test_noalloc_matches_context_mtxel_on_two_calls(gpu_lib):
+    torch = pytest.importorskip("torch")
+    # an umklapp k first, then a plain one
+    compare_with_context(gpu_lib, torch, syn.make_problem("si18_qx"), (4, 0))
+
+
+@pytest.mark.parametrize("box", [(48, 48, 48), (48, 64, 64)])
+def test_noalloc_large_boxes(gpu_lib, box):
+    """48^3: the eight-lane kernels with the scatter through the inverse map
+    and no z-pass scratch; 48x64x64: the four-lane kernels of non-cubic boxes."""
+    torch = pytest.importorskip("torch")
+    p = syn.make_problem("si18_qx", box=box, ng=137, nv=3, nc=5, nfreq=1)
+    compare_with_context(gpu_lib, torch, p, (4, 0))
+
+
+def test_noalloc_runs_in_valence_blocks(gpu_lib):
+    """8 x 200 pairs need about 77 MiB of kernel scratch on the 18^3 box, more
+    than the static array: the call runs in blocks of valence bands."""
+    torch = pytest.importorskip("torch")
+    p = syn.make_problem("si18_qx", nc=200)
+    compare_with_context(gpu_lib, torch, p, (4, 0))
+
+
 def test_noalloc_rejects_calls_beyond_its_scratch(gpu_lib):
     torch = pytest.importorskip("torch")
     p = syn.make_problem("si18_qx")
     geps = p.qs[0][1]
-    dummy = torch.zeros(2, dtype=torch.complex128, device="cuda")
+    nbox = int(np.prod(p.box))
+    nc = 1400        # one valence band with 1400 conduction bands: about 67 MiB of scratch
+    Uv = torch.zeros((1, 2, nbox), dtype=torch.complex128, device="cuda")
+    Uc = torch.zeros((nc, 2, nbox), dtype=torch.complex128, device="cuda")
+    M = torch.zeros((1, nc, len(geps)), dtype=torch.complex128, device="cuda")
     with pytest.raises(gpu_lib.BgwError) as e:
-        gpu_lib.bgw_mtxel_spinor_noalloc(p.box, dummy, dummy, 100, 1000, (0, 0, 0), geps, dummy)
+        gpu_lib.bgw_mtxel_spinor_noalloc(p.box, Uv, Uc, 1, nc, (0, 0, 0), geps, M)
     assert e.value.status == gpu_lib.BGW_E_ARG and "maximum" in str(e.value)
+
+
+def test_noalloc_binding_checks_shapes(gpu_lib):
+    torch = pytest.importorskip("torch")
+    p = syn.make_problem("si18_qx")
+    geps = p.qs[0][1]
+    small = torch.zeros(2, dtype=torch.complex128, device="cuda")
+    with pytest.raises(ValueError):
+        gpu_lib.bgw_mtxel_spinor_noalloc(p.box, small, small, 2, 3, (0, 0, 0), geps, small)
