@@ -466,6 +466,75 @@ BGW_API bgw_status bgw_mtxel_spinor_noalloc(const int fft[3], const void *Uv, co
                                             int nv, int nc, const int G0[3], int ng,
                                             const int *gvec, void *M_dev, void *stream);
 
+/*
+ * Matrix elements of any two band ranges (Eq. matrix_el with free band
+ * indices): M[n][m][g] = M_{n0+n, m0+m}(k, q, G_g) for bands n0..n0+nn-1 at
+ * k = kcrys[ik] and m0..m0+nm-1 at k+q, band indices counted over the whole
+ * upload (0..nv+nc_max-1: occupied then empty).  This is what the self-energy
+ * and the BSE kernel need beyond the polarizability's occupied-empty pairs:
+ * the paper's M_{n''n}(k, -q, -G) of Eqs. sigma_sx and sigma_coh equals
+ * M_{n''n}(k', q, G) here with k' = k - q (first band at k - q, second at
+ * k), and the spin-traced M of the BSE kernel section is the same element.
+ *   q      : q->q and its sphere q->gvec (q->nc is not used)
+ *   M_dev  : caller-owned DEVICE buffer [nn][nm][q->ng], complex128 (FP64
+ *            context) or complex64 (mixed)
+ * The k-point ik and its partner must have been uploaded.  BGW_W_ALIAS as for
+ * bgw_mtxel_spinor.  Asynchronous.
+ */
+BGW_API bgw_status bgw_mtxel_bands(bgw_ctx ctx, const bgw_q *q, int ik, int n0, int nn, int m0, int nm,
+                                   void *M_dev);
+
+/*
+ * Screened-exchange and Coulomb-hole diagonal elements of the self-energy,
+ * Eqs. sigma_sx and sigma_coh, in the static limit (COHSEX: the screened
+ * interaction at zero frequency, W_GG'(q) = eps^-1_GG'(q, 0) v(q+G'); the
+ * frequency integral of the Coulomb-hole term then reduces to half the
+ * induced interaction W - v summed over every band n'').  The contribution of
+ * one q-point to bands n0..n0+nn-1 at k = kcrys[ik] is ADDED to sx[] and
+ * coh[] (host, caller-owned, eV):
+ *   sx[n]  += -(1/N_k) sum_{n'' occupied} sum_{G,G'} conj(M_{n''n}(G)) W_GG' M_{n''n}(G')
+ *   coh[n] += (1/2)(1/N_k) sum_{n'' all bands} sum_{G,G'} conj(M_{n''n}(G)) (W_GG' - delta_GG' v(q+G)) M_{n''n}(G')
+ * with M_{n''n}(G) = M_{n''n}(k - q, q, G) (bgw_mtxel_bands at the k-point
+ * k - q, which must be on the k list and uploaded, as must k).  Occupied
+ * bands are 0..nv-1; "all bands" are the nv + nc_max bands of the upload.
+ * Summing the calls over every q of the k-grid gives the Brillouin-zone
+ * average (the 1/N_k; the paper prints the q sum without it).
+ *   W_dev : DEVICE complex128 [q->ng][q->ng], row G, column G' (eV), e.g.
+ *           bgw_epsinv mode 1 applied to the static chi0 of this q
+ *   vq    : host [q->ng], v(q+G) in eV (the square of bgw_coulomb_sqrt)
+ * Needs a BGW_FP64 context; uses context-owned scratch of about
+ * 32 (nv+nc_max) nn q->ng bytes.  Waits for the stream (the sums are read
+ * back); not capturable (BGW_E_STATE during a capture).
+ */
+BGW_API bgw_status bgw_sigma_cohsex(bgw_ctx ctx, const bgw_q *q, int ik, int n0, int nn, const void *W_dev,
+                                    const double *vq, double *sx, double *coh);
+
+/*
+ * One (k_i, k_j) block of the exchange and direct BSE kernels in the
+ * Tamm-Dancoff approximation (the K^X and K^D integrals of the BSE section),
+ * for valence bands v0..v0+nv-1 and conduction bands c0..c0+nc-1 (counted
+ * within the occupied and the empty bands) at both k-points; rows are (v c)
+ * at k_i = kcrys[ik], columns (v' c') at k_j = kcrys[jk], index v*nc + c:
+ *   KX[(v c)][(v' c')] =  (1/N_k) sum_G v(G) M_vc(k_i, 0, G) conj(M_v'c'(k_j, 0, G))
+ *   KD[(v c)][(v' c')] = -(1/N_k) sum_{G,G'} conj(M_cc'(k_i, q, G)) W_GG'(q) M_vv'(k_i, q, G')
+ * with q = k_j - k_i, M as in bgw_mtxel_bands (spin traced) and W the static
+ * screened interaction of q.  The printed kernels carry -i and +i from the
+ * time integration; the factor i that turns them into energies gives the
+ * usual repulsive exchange and attractive direct terms above.
+ *   q0, v0_coul : the exchange sphere at q = 0 (q0->q a reciprocal lattice
+ *                 vector) and v(G) there, host [q0->ng] eV (0 where G = 0:
+ *                 the long-range term is left out, as bgw_coulomb_sqrt does)
+ *   qd, W_dev   : q = k_j - k_i (mod a reciprocal vector) with its sphere, and
+ *                 DEVICE complex128 W [qd->ng][qd->ng] (eV)
+ *   KX_dev, KD_dev : caller-owned DEVICE complex128 [nv*nc][nv*nc]; either
+ *                 may be NULL to skip that kernel
+ * Needs a BGW_FP64 context with both k-points uploaded; context-owned
+ * scratch.  Asynchronous (the host v0_coul is read before the call returns).
+ */
+BGW_API bgw_status bgw_bse_kernel(bgw_ctx ctx, int ik, int jk, const bgw_q *q0, const double *v0_coul,
+                                  const bgw_q *qd, const void *W_dev, int v0, int nv, int c0, int nc,
+                                  void *KX_dev, void *KD_dev);
+
 /* Release every device buffer of the context (synchronizes its stream). */
 BGW_API void bgw_destroy(bgw_ctx ctx);
 

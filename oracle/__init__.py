@@ -15,7 +15,11 @@ What the functions follow (arXiv:2206.00808, Sec. II):
                     the paper is silent on it);
   * `coulomb`    -- v(q+G) = 4 pi e^2 / (Omega |q+G|^2) in eV;
   * `epsinv`     -- eps = delta - v(q+G) P and W = eps^-1 v(q+G') (the two
-                    equations before the P formula), eps^-1 by a plain LU.
+                    equations before the P formula), eps^-1 by a plain LU;
+  * `sigma_cohsex` -- the screened-exchange and Coulomb-hole diagonal
+                    elements, Eqs. sigma_sx and sigma_coh, with the static W;
+  * `bse_kernel` -- the exchange and direct BSE kernel blocks (the K^X and
+                    K^D integrals of the BSE section, spin traced).
 All are pinned by tests/test_oracle_pins.py; none is "parity unpinned".
 """
 from __future__ import annotations
@@ -67,6 +71,14 @@ def _load():
             lib.oracle_coulomb.restype = None
             lib.oracle_epsinv.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P]
             lib.oracle_epsinv.restype = ctypes.c_int
+            lib.oracle_quad.argtypes = [ctypes.c_long, ctypes.c_int, P, P, P]
+            lib.oracle_quad.restype = None
+            lib.oracle_bse_exchange.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P,
+                                                ctypes.c_double, P]
+            lib.oracle_bse_exchange.restype = None
+            lib.oracle_bse_direct.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P,
+                                              ctypes.c_double, P]
+            lib.oracle_bse_direct.restype = None
             _lib = lib
     return _lib
 
@@ -193,3 +205,83 @@ def epsinv(chi, v) -> tuple[np.ndarray, np.ndarray]:
     if lib.oracle_epsinv(ng, nf, _ptr(chi), _ptr(vv), _ptr(e), _ptr(w)) != 0:
         raise ArithmeticError("oracle_epsinv: singular matrix or allocation failure")
     return e, w
+
+
+def quad(M, A) -> np.ndarray:
+    """Re sum_GG' conj(M[p][G]) A[G][G'] M[p][G'] for every row p of M (np, ng)."""
+    lib = _load()
+    M, A = _c128(M), _c128(A)
+    np_, ng = M.shape
+    out = np.zeros(np_, dtype=np.float64)
+    lib.oracle_quad(np_, ng, _ptr(M), _ptr(A), _ptr(out))
+    return out
+
+
+def k_minus_q(kcrys, ik, q) -> int:
+    """Grid index j with kcrys[j] + q = kcrys[ik] + G0 (G0 integer)."""
+    for j in range(len(kcrys)):
+        kp, _ = umklapp_or_none(kcrys, j, q)
+        if kp == ik:
+            return j
+    raise ValueError(f"k - q is not on the k-grid (k index {ik}, q = {q})")
+
+
+def umklapp_or_none(kcrys, ik, q):
+    try:
+        return umklapp(kcrys, ik, q)
+    except ValueError:
+        return None, None
+
+
+def sigma_cohsex(problem, ik, q, geps, W, vq, n0, nn):
+    """(sx, coh) [nn] in eV: one q-point's share of the static screened-exchange
+    and Coulomb-hole diagonal elements (Eqs. sigma_sx, sigma_coh with
+    W = eps^-1(q, 0) v(q+G')) for bands n0..n0+nn-1 at k = kcrys[ik]:
+        sx[n]  = -(1/N_k) sum_{n'' occupied} conj(M)^T W M
+        coh[n] = (1/2)(1/N_k) sum_{n'' all} conj(M)^T (W - diag v) M
+    with M = M_{n''n}(k - q, q, G): band n'' at k - q, band n at k (the
+    paper's M_{n''n}(k, -q, -G))."""
+    jk = k_minus_q(problem.kcrys, ik, q)
+    kp, G0 = umklapp(problem.kcrys, jk, q)
+    nb = problem.nbands
+    M = mtxel(problem.box, problem.gvec[jk], problem.coeff[jk], problem.gvec[kp],
+              problem.coeff[kp][n0:n0 + nn], G0, geps)            # [nb][nn][ng]
+    ng = len(geps)
+    sw = quad(M.reshape(nb * nn, ng), W).reshape(nb, nn)
+    sv = quad(M.reshape(nb * nn, ng), np.diag(np.asarray(vq, np.float64)).astype(np.complex128)).reshape(nb, nn)
+    sx = np.zeros(nn)
+    coh = np.zeros(nn)
+    for n in range(nn):
+        for m in range(nb):
+            if m < problem.nv:
+                sx[n] -= sw[m, n] / problem.nk
+            coh[n] += 0.5 * (sw[m, n] - sv[m, n]) / problem.nk
+    return sx, coh
+
+
+def bse_kernel(problem, ik, jk, geps0, v0, qd, gepsd, W, vb, cb):
+    """(KX, KD) [(v c)][(v' c')] in eV for bands vb = (v0, nv) of the occupied
+    and cb = (c0, nc) of the empty bands at k_i = kcrys[ik] (rows) and
+    k_j = kcrys[jk] (columns), q = k_j - k_i = qd:
+        KX = (1/N_k) sum_G v(G) M_vc(k_i, 0, G) conj(M_v'c'(k_j, 0, G))
+        KD = -(1/N_k) sum_GG' conj(M_cc'(k_i, q, G)) W_GG' M_vv'(k_i, q, G')
+    (the K^X and K^D integrals of the BSE section times the factor i of the
+    time integration)."""
+    p = problem
+    (va, nv), (ca, nc) = vb, cb
+    ca += p.nv
+    box = p.box
+    zero = np.zeros(3, np.int32)
+    Mi = mtxel(box, p.gvec[ik], p.coeff[ik][va:va + nv], p.gvec[ik], p.coeff[ik][ca:ca + nc], zero, geps0)
+    Mj = mtxel(box, p.gvec[jk], p.coeff[jk][va:va + nv], p.gvec[jk], p.coeff[jk][ca:ca + nc], zero, geps0)
+    lib = _load()
+    P = nv * nc
+    KX = np.zeros((P, P), dtype=np.complex128)
+    lib.oracle_bse_exchange(nv, nc, len(geps0), _ptr(Mi), _ptr(Mj), _ptr(_f64(v0)), 1.0 / p.nk, _ptr(KX))
+    kp, G0 = umklapp(p.kcrys, ik, qd)
+    assert kp == jk, "k_i + q must land on k_j"
+    Mcc = mtxel(box, p.gvec[ik], p.coeff[ik][ca:ca + nc], p.gvec[jk], p.coeff[jk][ca:ca + nc], G0, gepsd)
+    Mvv = mtxel(box, p.gvec[ik], p.coeff[ik][va:va + nv], p.gvec[jk], p.coeff[jk][va:va + nv], G0, gepsd)
+    KD = np.zeros((P, P), dtype=np.complex128)
+    lib.oracle_bse_direct(nv, nc, len(gepsd), _ptr(Mcc), _ptr(Mvv), _ptr(_c128(W)), 1.0 / p.nk, _ptr(KD))
+    return KX, KD

@@ -355,3 +355,99 @@ int oracle_epsinv(int ng, int nfreq, const double *chi, const double *v, double 
     free(piv);
     return failed ? -1 : 0;
 }
+
+/*
+ * ---------------------------------------------------------------------------
+ * Self-energy terms (Sec. II, Eqs. sigma_sx and sigma_coh) in the static
+ * limit, and the BSE kernels (the K^X and K^D integrals of the BSE section).
+ * Both are sums of spin-traced matrix elements, computed by oracle_mtxel with
+ * free band ranges, against an interaction matrix.
+ * ---------------------------------------------------------------------------
+ */
+
+/*
+ * out[p] = Re sum_G sum_G' conj(M[p][G]) A[G][G'] M[p][G'] for np rows M[p]
+ * of ng complex values and a complex ng x ng matrix A (row G, column G').
+ * For a Hermitian A the sum is real; its real part is returned.
+ */
+void oracle_quad(long np, int ng, const double *M, const double *A, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < np; ++p) {
+        const double *m = M + 2 * p * ng;
+        double sr = 0.0;
+        for (int g = 0; g < ng; ++g) {
+            /* y = sum_G' A[g][G'] M[G'] */
+            double yr = 0.0, yi = 0.0;
+            const double *row = A + 2 * (long)g * ng;
+            for (int h = 0; h < ng; ++h) {
+                yr += row[2 * h] * m[2 * h] - row[2 * h + 1] * m[2 * h + 1];
+                yi += row[2 * h] * m[2 * h + 1] + row[2 * h + 1] * m[2 * h];
+            }
+            /* conj(M[g]) y, real part */
+            sr += m[2 * g] * yr + m[2 * g + 1] * yi;
+        }
+        out[p] = sr;
+    }
+}
+
+/*
+ * Exchange kernel block:
+ *   K[(v c)][(v' c')] = scale sum_G v[G] Mi[v][c][G] conj(Mj[v'][c'][G])
+ * Mi, Mj: [nv][nc][ng] complex (M_vc at k_i and at k_j, q = 0), v: [ng].
+ */
+void oracle_bse_exchange(int nv, int nc, int ng, const double *Mi, const double *Mj, const double *v,
+                         double scale, double *K)
+{
+    const long P = (long)nv * nc;
+#pragma omp parallel for schedule(static)
+    for (long I = 0; I < P; ++I) {
+        const double *a = Mi + 2 * I * ng;
+        for (long J = 0; J < P; ++J) {
+            const double *b = Mj + 2 * J * ng;
+            double sr = 0.0, si = 0.0;
+            for (int g = 0; g < ng; ++g) {
+                /* a * conj(b) */
+                sr += v[g] * (a[2 * g] * b[2 * g] + a[2 * g + 1] * b[2 * g + 1]);
+                si += v[g] * (a[2 * g + 1] * b[2 * g] - a[2 * g] * b[2 * g + 1]);
+            }
+            K[2 * (I * P + J)] = scale * sr;
+            K[2 * (I * P + J) + 1] = scale * si;
+        }
+    }
+}
+
+/*
+ * Direct kernel block:
+ *   K[(v c)][(v' c')] = -scale sum_G sum_G' conj(Mcc[c][c'][G]) W[G][G'] Mvv[v][v'][G']
+ * Mcc: [nc][nc][ng] (M_cc' with c at k_i, c' at k_j), Mvv: [nv][nv][ng],
+ * W: [ng][ng] complex.
+ */
+void oracle_bse_direct(int nv, int nc, int ng, const double *Mcc, const double *Mvv, const double *W,
+                       double scale, double *K)
+{
+    const long P = (long)nv * nc;
+#pragma omp parallel for schedule(static)
+    for (long I = 0; I < P; ++I) {
+        const int v = (int)(I / nc), c = (int)(I % nc);
+        for (long J = 0; J < P; ++J) {
+            const int v2 = (int)(J / nc), c2 = (int)(J % nc);
+            const double *a = Mcc + 2 * (((long)c * nc + c2) * ng);
+            const double *b = Mvv + 2 * (((long)v * nv + v2) * ng);
+            double sr = 0.0, si = 0.0;
+            for (int g = 0; g < ng; ++g) {
+                double yr = 0.0, yi = 0.0;   /* sum_G' W[g][G'] b[G'] */
+                const double *row = W + 2 * (long)g * ng;
+                for (int h = 0; h < ng; ++h) {
+                    yr += row[2 * h] * b[2 * h] - row[2 * h + 1] * b[2 * h + 1];
+                    yi += row[2 * h] * b[2 * h + 1] + row[2 * h + 1] * b[2 * h];
+                }
+                /* conj(a[g]) y */
+                sr += a[2 * g] * yr + a[2 * g + 1] * yi;
+                si += a[2 * g] * yi - a[2 * g + 1] * yr;
+            }
+            K[2 * (I * P + J)] = -scale * sr;
+            K[2 * (I * P + J) + 1] = -scale * si;
+        }
+    }
+}

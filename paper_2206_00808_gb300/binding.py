@@ -30,7 +30,7 @@ EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "
             "bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch", "bgw_chi0_progress",
             "bgw_chi0_checkpoint_bytes", "bgw_chi0_checkpoint", "bgw_chi0_resume", "bgw_coulomb_sqrt",
             "bgw_epsinv_workspace_bytes", "bgw_epsinv", "bgw_symmetry_su2", "bgw_unfold_spinor",
-            "bgw_destroy", "bgw_last_error"]
+            "bgw_mtxel_bands", "bgw_sigma_cohsex", "bgw_bse_kernel", "bgw_destroy", "bgw_last_error"]
 BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C, BGW_OPT_GRID_SLOTS = 1, 2, 3, 4
 BGW_OPT_TEST_DROP_LOAD, BGW_OPT_TEST_FAIL_ALLOC, BGW_OPT_K1_PATH, BGW_OPT_MTXEL_LANES = 5, 6, 7, 8
 BGW_OPT_DEFER_K1, BGW_OPT_COPY_AHEAD, BGW_OPT_OVERLAP = 9, 10, 11
@@ -72,6 +72,12 @@ _lib.bgw_epsinv.restype = ctypes.c_int
 _lib.bgw_symmetry_su2.argtypes, _lib.bgw_symmetry_su2.restype = [_P, _P, _P, _P], ctypes.c_int
 _lib.bgw_unfold_spinor.argtypes = [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]
 _lib.bgw_unfold_spinor.restype = ctypes.c_int
+_lib.bgw_mtxel_bands.argtypes = [_P, ctypes.POINTER(bgw_q), _I, _I, _I, _I, _I, _P]
+_lib.bgw_sigma_cohsex.argtypes = [_P, ctypes.POINTER(bgw_q), _I, _I, _I, _P, _P, _P, _P]
+_lib.bgw_bse_kernel.argtypes = [_P, _I, _I, ctypes.POINTER(bgw_q), _P, ctypes.POINTER(bgw_q), _P, _I, _I, _I, _I,
+                                _P, _P]
+for _f in ["bgw_mtxel_bands", "bgw_sigma_cohsex", "bgw_bse_kernel"]:
+    getattr(_lib, _f).restype = ctypes.c_int
 _lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
 _lib.bgw_last_error.argtypes, _lib.bgw_last_error.restype = [_P], ctypes.c_char_p
 for _f in ["bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
@@ -307,6 +313,52 @@ def bgw_mtxel_spinor_noalloc(fft, Uv, Uc, nv: int, nc: int, G0, gvec, M_dev, str
     pm, _ = _ptr_and_device(M_dev)
     return _check(_lib.bgw_mtxel_spinor_noalloc(_host_ptr(f), pv, pc, nv, nc, _host_ptr(g0), len(g),
                                                 _host_ptr(g), pm, _stream_handle(stream)), None)
+
+
+def bgw_mtxel_bands(ctx, q, gvec, ik: int, n0: int, nn: int, m0: int, nm: int, M_dev) -> int:
+    """M_{n m}(k, q, G) for bands n0..n0+nn-1 at k and m0..m0+nm-1 at k+q
+    (indices over all uploaded bands) into the device tensor M_dev [nn][nm][ng]."""
+    s, keep = make_q(q, gvec, 1)
+    pm, dm = _ptr_and_device(M_dev)
+    if not dm:
+        raise ValueError("M_dev must be a device tensor")
+    st = _lib.bgw_mtxel_bands(ctx, ctypes.byref(s), ik, n0, nn, m0, nm, pm)
+    del keep
+    return _check(st, ctx)
+
+
+def bgw_sigma_cohsex(ctx, q, gvec, ik: int, n0: int, nn: int, W_dev, vq, sx=None, coh=None):
+    """Adds one q-point's static screened-exchange and Coulomb-hole shares to
+    sx, coh (float64 [nn], zeros when not given) for bands n0.. at k; returns
+    (sx, coh)."""
+    s, keep = make_q(q, gvec, 1)
+    v = np.ascontiguousarray(vq, dtype=np.float64)
+    sx = np.zeros(nn) if sx is None else sx
+    coh = np.zeros(nn) if coh is None else coh
+    assert sx.dtype == np.float64 and coh.dtype == np.float64 and len(sx) >= nn and len(coh) >= nn
+    pw, dw = _ptr_and_device(W_dev)
+    if not dw:
+        raise ValueError("W_dev must be a device tensor")
+    _check(_lib.bgw_sigma_cohsex(ctx, ctypes.byref(s), ik, n0, nn, pw, _host_ptr(v), _host_ptr(sx), _host_ptr(coh)),
+           ctx)
+    del keep
+    return sx, coh
+
+
+def bgw_bse_kernel(ctx, ik: int, jk: int, q0, gvec0, v0_coul, qd, gvecd, W_dev, v0: int, nv: int, c0: int, nc: int,
+                   KX_dev=None, KD_dev=None) -> int:
+    """One (k_i, k_j) block of the exchange (KX_dev) and direct (KD_dev) BSE
+    kernels, device complex128 [nv*nc][nv*nc] tensors (either may be None)."""
+    s0, k0 = make_q(q0, gvec0, 1)
+    sd, kd = make_q(qd, gvecd, 1)
+    v = np.ascontiguousarray(v0_coul, dtype=np.float64)
+    pw = ctypes.c_void_p(W_dev.data_ptr()) if W_dev is not None else None
+    px = ctypes.c_void_p(KX_dev.data_ptr()) if KX_dev is not None else None
+    pd = ctypes.c_void_p(KD_dev.data_ptr()) if KD_dev is not None else None
+    st = _lib.bgw_bse_kernel(ctx, ik, jk, ctypes.byref(s0), _host_ptr(v), ctypes.byref(sd), pw, v0, nv, c0, nc, px,
+                             pd)
+    del k0, kd
+    return _check(st, ctx)
 
 
 def bgw_set_option(ctx, option: int, value: int) -> int:

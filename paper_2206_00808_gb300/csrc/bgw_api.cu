@@ -166,6 +166,9 @@ struct bgw_ctx_s {
     DevBuf out_stage;    // finalize to host
     DevBuf gmap_tmp;     // dielectric-sphere map of a bgw_mtxel_spinor call
     DevBuf errflag;      // device int: non-zero after a bounded device wait gave up
+    // scratch of the self-energy and BSE kernel calls (matrix-element blocks,
+    // products, per-pair sums, a copy of the interaction's diagonal)
+    DevBuf nx_m1, nx_m2, nx_y, nx_t, nx_s, nx_v;
     // real-space grid slots: every k resident (nslots == nk), or a
     // least-recently-used cache of nslots grids (streaming)
     int grid_slots_opt = 0;
@@ -438,10 +441,10 @@ bool find_umklapp(const bgw_ctx_s *c, int ik, const double q[3], int &kp, int G0
 void compute_kmap(const bgw_ctx_s *c, QState &s);
 
 // Geometry of one dielectric sphere: extents, kept widths, cube positions.
-bgw_status prepare_q(bgw_ctx_s *c, const bgw_q *q, QState &s) {
+bgw_status prepare_q(bgw_ctx_s *c, const bgw_q *q, QState &s, bool check_nc = true) {
     if (!q) return c->fail(BGW_E_ARG, "null q");
     if (q->ng < 1 || !q->gvec) return c->fail(BGW_E_ARG, "q: ng must be >= 1 with a gvec list");
-    if (q->nc < 1 || q->nc > c->nc_max)
+    if (check_nc && (q->nc < 1 || q->nc > c->nc_max))
         return c->fail(BGW_E_ARG, "q: nc=%d outside 1..nc_max=%d", q->nc, c->nc_max);
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(q->q[a])) return c->fail(BGW_E_ARG, "q: non-finite component");
@@ -835,6 +838,71 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
     cudaError_t ej = join();
     return e != cudaSuccess ? e : ej;
 }
+}  // namespace
+
+// ---- matrix elements of any band ranges (self-energy, BSE kernel) ----------
+namespace {
+
+// Scratch of the matrix-element kernels for na x nb2 pairs of sphere s.
+cudaError_t ensure_mtxel_scratch_pairs(bgw_ctx_s *c, const QState &s, int na, int nb2) {
+    const long n01 = (long)c->box[0] * c->box[1];
+    const int G0z[3] = {0, 0, 0};
+    const bgw::Axes ax = mtxel_axes(c, s, G0z);
+    const long P = (long)bgw::mtxel_v_batch(na, nb2, ax, c->csize) * nb2;
+    const long PA = bgw::mtxel_uses_a(ax) ? P : 0;
+    cudaError_t e = c->A.ensure((size_t)(PA * n01 * s.w[2]) * c->csize, c->st);
+    if (e == cudaSuccess) e = c->Bs.ensure((size_t)(P * c->box[0] * s.w[1] * s.w[2]) * c->csize, c->st);
+    return e;
+}
+
+// M[a][b][g] = M_{a0+a, b0+b}(k, q, G_g) for bands a0.. at k = kcrys[ik] and
+// b0.. at k + q (absolute band indices of the uploads) into the device
+// buffer M (row stride ng).  `clean` is cleared when the box aliases.
+bgw_status mtxel_into(bgw_ctx_s *c, const char *who, QState &s, int ik, int a0, int na, int b0, int nb2,
+                      void *M, bool &clean) {
+    int kp, G0[3];
+    if (!find_umklapp(c, ik, s.q, kp, G0)) return c->fail(BGW_E_ARG, "%s: k + q is not on the k list (k %d)", who, ik);
+    if (!c->k[ik].uploaded || !c->k[kp].uploaded)
+        return c->fail(BGW_E_STATE, "%s: k %d or its partner %d not uploaded", who, ik, kp);
+    if (na == 0 || nb2 == 0) return BGW_OK;
+    clean = clean && alias_free(c, ik, kp, G0, s);
+    cudaError_t e = flush_k1(c);
+    if (e != cudaSuccess) return c->cuda_fail(e, "deferred sphere-to-grid kernels");
+    e = ensure_mtxel_scratch_pairs(c, s, na, nb2);
+    if (e != cudaSuccess) return c->cuda_fail(e, "matrix-element scratch");
+    e = c->gmap_tmp.ensure(sizeof(int) * s.gmap.size(), c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "map buffer");
+    // pageable source: the copy is stream-ordered and has read the host
+    // vector when it returns, so the buffer can be refilled by a later call
+    e = cudaMemcpyAsync(c->gmap_tmp.p, s.gmap.data(), sizeof(int) * s.gmap.size(), cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "map copy");
+    const bgw::Axes ax = mtxel_axes(c, s, G0);
+    cudaError_t ge;
+    const int sa = ensure_grid(c, ik, ge);
+    if (ge != cudaSuccess) return c->cuda_fail(ge, "grid");
+    const int sb = ensure_grid(c, kp, ge);
+    if (ge != cudaSuccess) return c->cuda_fail(ge, "grid");
+    const int *gmap = static_cast<const int *>(c->gmap_tmp.p);
+    const int rec = c->stage_begin(1);
+    e = (c->prec == BGW_FP64)
+            ? bgw::mtxel_f64(c->slot_ptr(sa, a0), c->slot_ptr(sb, b0), na, nb2, ax, gmap, s.ng, c->A.p, c->Bs.p, M,
+                             s.ng, c->st, 0, 0, c->mtxel_lanes)
+            : bgw::mtxel_f32(c->slot_ptr(sa, a0), c->slot_ptr(sb, b0), na, nb2, ax, gmap, s.ng, c->A.p, c->Bs.p, M,
+                             s.ng, c->st, 0, 0, c->mtxel_lanes);
+    c->stage_end(rec, 3);
+    if (e != cudaSuccess) return c->cuda_fail(e, "matrix-element kernels");
+    return BGW_OK;
+}
+
+// Grid index j of k - q: the k-point whose k + q lands on kcrys[ik].
+int k_minus_q(const bgw_ctx_s *c, int ik, const double q[3]) {
+    for (int j = 0; j < c->nk; ++j) {
+        int kp, G0[3];
+        if (find_umklapp(c, j, q, kp, G0) && kp == ik) return j;
+    }
+    return -1;
+}
+
 }  // namespace
 
 // ---- checkpoint / resume ----------------------------------------------------
@@ -1668,10 +1736,155 @@ void bgw_destroy(bgw_ctx c) {
         }
         DevBuf *bufs[] = {&c->grids, &c->energy, &c->stage, &c->S,  &c->R,        &c->A,
                           &c->Bs,    &c->M,      &c->W,     &c->mixed_ws, &c->freq_dev, &c->out_stage, &c->gmap_tmp,
-                          &c->errflag};
+                          &c->errflag, &c->nx_m1, &c->nx_m2, &c->nx_y, &c->nx_t, &c->nx_s, &c->nx_v};
         for (DevBuf *b : bufs) b->release();
     }
     delete c;
+}
+
+bgw_status bgw_mtxel_bands(bgw_ctx c, const bgw_q *q, int ik, int n0, int nn, int m0, int nm, void *M_dev) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (!M_dev) return c->fail(BGW_E_ARG, "mtxel_bands: null output");
+    if (ik < 0 || ik >= c->nk) return c->fail(BGW_E_ARG, "mtxel_bands: ik=%d out of range", ik);
+    if (nn < 0 || n0 < 0 || n0 + nn > c->nb || nm < 0 || m0 < 0 || m0 + nm > c->nb)
+        return c->fail(BGW_E_ARG, "mtxel_bands: band ranges [%d,%d) and [%d,%d) must lie in [0,%d)", n0, n0 + nn,
+                       m0, m0 + nm, c->nb);
+    QState s;
+    bgw_status st = prepare_q(c, q, s, false);
+    if (st != BGW_OK) return st;
+    bool clean = true;
+    st = mtxel_into(c, "mtxel_bands", s, ik, n0, nn, m0, nm, M_dev, clean);
+    if (st != BGW_OK) return st;
+    return clean ? BGW_OK : BGW_W_ALIAS;
+}
+
+bgw_status bgw_sigma_cohsex(bgw_ctx c, const bgw_q *q, int ik, int n0, int nn, const void *W_dev,
+                            const double *vq, double *sx, double *coh) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (c->prec != BGW_FP64) return c->fail(BGW_E_STATE, "sigma_cohsex: needs a BGW_FP64 context");
+    if (!W_dev || !vq || !sx || !coh) return c->fail(BGW_E_ARG, "sigma_cohsex: null pointer argument");
+    if (ik < 0 || ik >= c->nk) return c->fail(BGW_E_ARG, "sigma_cohsex: ik=%d out of range", ik);
+    if (nn < 1 || n0 < 0 || n0 + nn > c->nb)
+        return c->fail(BGW_E_ARG, "sigma_cohsex: band range [%d,%d) outside [0,%d)", n0, n0 + nn, c->nb);
+    if (st_capturing(c)) return c->fail(BGW_E_STATE, "sigma_cohsex: blocks on its result, cannot be captured");
+    QState s;
+    bgw_status st = prepare_q(c, q, s, false);
+    if (st != BGW_OK) return st;
+    for (int g = 0; g < s.ng; ++g)
+        if (!std::isfinite(vq[g]) || vq[g] < 0) return c->fail(BGW_E_ARG, "sigma_cohsex: v(q+G) must be finite, >= 0");
+    const int jk = k_minus_q(c, ik, s.q);
+    if (jk < 0) return c->fail(BGW_E_ARG, "sigma_cohsex: k - q is not on the k list (k %d)", ik);
+    const long P = (long)c->nb * nn;
+    const size_t mb = 16 * (size_t)P * s.ng;
+    cudaError_t e = c->nx_m1.ensure(mb, c->st);
+    if (e == cudaSuccess) e = c->nx_y.ensure(mb, c->st);
+    if (e == cudaSuccess) e = c->nx_s.ensure(sizeof(double) * (2 * (size_t)P + 3 * (size_t)nn), c->st);
+    if (e == cudaSuccess) e = c->nx_v.ensure(sizeof(double) * (size_t)s.ng, c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sigma_cohsex: scratch");
+    // M_{n'' n}(k - q, q, G): every band n'' at k - q, bands n0.. at k
+    bool clean = true;
+    st = mtxel_into(c, "sigma_cohsex", s, jk, 0, c->nb, n0, nn, c->nx_m1.p, clean);
+    if (st != BGW_OK) return st;
+    double *sw = static_cast<double *>(c->nx_s.p), *tv = sw + P, *out = tv + P;
+    e = cudaMemcpyAsync(c->nx_v.p, vq, sizeof(double) * s.ng, cudaMemcpyHostToDevice, c->st);
+    // Y[p][G] = sum_G' W[G][G'] M[p][G']
+    if (e == cudaSuccess)
+        e = bgw::zgemm_f64((int)P, s.ng, s.ng, c->nx_m1.p, s.ng, 1, false, W_dev, 1, s.ng, false, nullptr, c->nx_y.p,
+                           s.ng, 1, 1.0, 0.0, false, c->st);
+    if (e == cudaSuccess)
+        e = bgw::rowdot_f64(c->nx_m1.p, c->nx_y.p, static_cast<const double *>(c->nx_v.p), P, s.ng, sw, tv, c->st);
+    if (e == cudaSuccess) e = bgw::band_sum_f64(sw, c->nv, nn, out, c->st);              // occupied n''
+    if (e == cudaSuccess) e = bgw::band_sum_f64(sw, c->nb, nn, out + nn, c->st);         // every n''
+    if (e == cudaSuccess) e = bgw::band_sum_f64(tv, c->nb, nn, out + 2 * nn, c->st);
+    std::vector<double> h(3 * (size_t)nn);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sigma_cohsex: kernels");
+    const double scale = 1.0 / c->nk;
+    for (int n = 0; n < nn; ++n) {
+        sx[n] += -scale * h[n];
+        coh[n] += 0.5 * scale * (h[nn + n] - h[2 * nn + n]);
+    }
+    return clean ? BGW_OK : BGW_W_ALIAS;
+}
+
+bgw_status bgw_bse_kernel(bgw_ctx c, int ik, int jk, const bgw_q *q0, const double *v0_coul, const bgw_q *qd,
+                          const void *W_dev, int v0, int nv, int c0, int nc, void *KX_dev, void *KD_dev) {
+    if (!c) return BGW_E_ARG;
+    DeviceGuard dg(c->device);
+    c->err.clear();
+    if (c->prec != BGW_FP64) return c->fail(BGW_E_STATE, "bse_kernel: needs a BGW_FP64 context");
+    if (ik < 0 || ik >= c->nk || jk < 0 || jk >= c->nk)
+        return c->fail(BGW_E_ARG, "bse_kernel: k indices %d, %d out of range", ik, jk);
+    if (nv < 1 || v0 < 0 || v0 + nv > c->nv || nc < 1 || c0 < 0 || c0 + nc > c->nc_max)
+        return c->fail(BGW_E_ARG, "bse_kernel: band ranges outside the context's valence/conduction bands");
+    if (KX_dev && (!q0 || !v0_coul)) return c->fail(BGW_E_ARG, "bse_kernel: K^X needs q0 and v(G)");
+    if (KD_dev && (!qd || !W_dev)) return c->fail(BGW_E_ARG, "bse_kernel: K^D needs qd and W");
+    const long P = (long)nv * nc;
+    const double scale = 1.0 / c->nk;
+    bool clean = true;
+    cudaError_t e = cudaSuccess;
+    if (KX_dev) {
+        QState s;
+        bgw_status st = prepare_q(c, q0, s, false);
+        if (st != BGW_OK) return st;
+        for (int g = 0; g < s.ng; ++g)
+            if (!std::isfinite(v0_coul[g]) || v0_coul[g] < 0)
+                return c->fail(BGW_E_ARG, "bse_kernel: v(G) must be finite and >= 0");
+        int kp, G0[3];
+        if (!find_umklapp(c, ik, s.q, kp, G0) || kp != ik || !find_umklapp(c, jk, s.q, kp, G0) || kp != jk)
+            return c->fail(BGW_E_ARG, "bse_kernel: q0 must be a reciprocal lattice vector (k + q0 = k)");
+        const size_t mb = 16 * (size_t)P * s.ng;
+        e = c->nx_m1.ensure(mb, c->st);
+        if (e == cudaSuccess) e = c->nx_m2.ensure(mb, c->st);
+        if (e == cudaSuccess) e = c->nx_v.ensure(sizeof(double) * (size_t)s.ng, c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "bse_kernel: scratch");
+        const int va = v0, ca = c->nv + c0;   // absolute band indices
+        st = mtxel_into(c, "bse_kernel", s, ik, va, nv, ca, nc, c->nx_m1.p, clean);
+        if (st == BGW_OK) st = mtxel_into(c, "bse_kernel", s, jk, va, nv, ca, nc, c->nx_m2.p, clean);
+        if (st != BGW_OK) return st;
+        e = cudaMemcpyAsync(c->nx_v.p, v0_coul, sizeof(double) * s.ng, cudaMemcpyHostToDevice, c->st);
+        // KX[I][J] = (1/N_k) sum_G v(G) M_I(k_i, G) conj(M_J(k_j, G))
+        if (e == cudaSuccess)
+            e = bgw::zgemm_f64((int)P, (int)P, s.ng, c->nx_m1.p, s.ng, 1, false, c->nx_m2.p, 1, s.ng, true,
+                               static_cast<const double *>(c->nx_v.p), KX_dev, P, 1, scale, 0.0, false, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);   // the host copy of v(G) has been read
+        if (e != cudaSuccess) return c->cuda_fail(e, "bse_kernel: exchange");
+    }
+    if (KD_dev) {
+        QState s;
+        bgw_status st = prepare_q(c, qd, s, false);
+        if (st != BGW_OK) return st;
+        int kp, G0[3];
+        if (!find_umklapp(c, ik, s.q, kp, G0) || kp != jk)
+            return c->fail(BGW_E_ARG, "bse_kernel: k_i + qd must land on k_j");
+        const size_t mcc = 16 * (size_t)nc * nc * s.ng, mvv = 16 * (size_t)nv * nv * s.ng;
+        e = c->nx_m1.ensure(mcc, c->st);
+        if (e == cudaSuccess) e = c->nx_m2.ensure(mvv, c->st);
+        if (e == cudaSuccess) e = c->nx_y.ensure(mvv, c->st);
+        if (e == cudaSuccess) e = c->nx_t.ensure(16 * (size_t)P * P, c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "bse_kernel: scratch");
+        // M_cc'(k_i, qd, G) and M_vv'(k_i, qd, G): bands at k_i and at k_j
+        st = mtxel_into(c, "bse_kernel", s, ik, c->nv + c0, nc, c->nv + c0, nc, c->nx_m1.p, clean);
+        if (st == BGW_OK) st = mtxel_into(c, "bse_kernel", s, ik, v0, nv, v0, nv, c->nx_m2.p, clean);
+        if (st != BGW_OK) return st;
+        const int nv2 = nv * nv, nc2 = nc * nc;
+        // Y[(v v')][G] = sum_G' W[G][G'] M_vv'(G')
+        e = bgw::zgemm_f64(nv2, s.ng, s.ng, c->nx_m2.p, s.ng, 1, false, W_dev, 1, s.ng, false, nullptr, c->nx_y.p,
+                           s.ng, 1, 1.0, 0.0, false, c->st);
+        // T[(c c')][(v v')] = -(1/N_k) sum_G conj(M_cc'(G)) Y[(v v')][G]
+        if (e == cudaSuccess)
+            e = bgw::zgemm_f64(nc2, nv2, s.ng, c->nx_m1.p, s.ng, 1, true, c->nx_y.p, 1, s.ng, false, nullptr,
+                               c->nx_t.p, nv2, 1, -scale, 0.0, false, c->st);
+        if (e == cudaSuccess) e = bgw::bse_permute_f64(c->nx_t.p, nv, nc, KD_dev, c->st);
+        if (e != cudaSuccess) return c->cuda_fail(e, "bse_kernel: direct");
+    }
+    return clean ? BGW_OK : BGW_W_ALIAS;
 }
 
 }  // extern "C"

@@ -125,4 +125,21 @@ cudaError_t herk_f64(const void *M, int P, int ng, const double *w, int nfreq, v
 cudaError_t chi0_finalize(const void *acc, int ng, int nfreq, double scale, void *out,
                           cudaStream_t st);
 
+// ---- bgw_zgemm.cu (FP64, for the self-energy and BSE kernel steps) -------
+// C(m, n) = [C(m, n) if accumulate] + alpha sum_k opA(m, k) wk[k] opB(k, n),
+// opA(m, k) = A[m*sam + k*sak] (conjugated if conjA), opB(k, n) = B[k*sbk +
+// n*sbn] (conjugated if conjB), C(m, n) at C[m*scm + n*scn]; complex128
+// throughout, wk (device, may be null) a real weight per k.
+cudaError_t zgemm_f64(int M, int N, int K, const void *A, long sam, long sak, bool conjA, const void *B, long sbk,
+                      long sbn, bool conjB, const double *wk, void *C, long scm, long scn, double alpha_re,
+                      double alpha_im, bool accumulate, cudaStream_t st);
+// s[p] = Re sum_g conj(M[p][g]) Y[p][g]; t[p] = sum_g v[g] |M[p][g]|^2 (when v
+// and t are given); M, Y complex128 [P][ng].
+cudaError_t rowdot_f64(const void *M, const void *Y, const double *v, long P, int ng, double *s, double *t,
+                       cudaStream_t st);
+// out[n] = sum_{i < n_first} x[i*nn + n], summed in order of i.
+cudaError_t band_sum_f64(const double *x, int n_first, int nn, double *out, cudaStream_t st);
+// K[(v*nc + c)][(v'*nc + c')] = T[(c*nc + c')][(v*nv + v')], complex128.
+cudaError_t bse_permute_f64(const void *T, int nv, int nc, void *K, cudaStream_t st);
+
 }  // namespace bgw
