@@ -77,7 +77,9 @@ typedef enum {
 } bgw_status;
 
 typedef enum {
-    BGW_FP64 = 0,          /* FP64 throughout: grids, FFTs, M, contraction */
+    BGW_FP64 = 0,          /* FP64 grids, FFTs and M; the contraction to FP64
+                              accuracy on tensor cores (exact BF16 digit
+                              slices) or, by option, on the FP64 pipe */
     BGW_MIXED_BF16X3 = 1   /* FP32 grids/FFTs, complex64 M, contraction as
                               split-BF16 (3 products) on tensor cores with FP32
                               accumulation per k, FP64 weights and FP64
@@ -375,6 +377,14 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        bitwise the same; work queued on the context stream
  *                        after the call waits for all of it.  Not changeable
  *                        during a graph capture.
+ *   BGW_OPT_FP64_CONTRACTION  FP64 contexts only.  0 (default): the pair sum
+ *                        runs on tcgen05 tensor cores from exact BF16 digit
+ *                        slices (per row a power-of-two exponent, five signed
+ *                        base-256 digits, the 15 products of total order <= 4
+ *                        with exact integer sums; about 2e-11 relative error,
+ *                        inside the FP64 path's 1e-10).  1: the FP64 FMA kernel
+ *                        (FP64 pipe only, rounding of plain FP64 sums).  Not
+ *                        changeable during a graph capture.
  *   BGW_OPT_TEST_FAIL_ALLOC for failure-handling tests only: when n > 0, the
  *                        n-th device allocation made by the library from now on
  *                        (by any context of the process) fails as if the device
@@ -391,7 +401,7 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
 enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
        BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7,
        BGW_OPT_MTXEL_LANES = 8, BGW_OPT_DEFER_K1 = 9, BGW_OPT_COPY_AHEAD = 10,
-       BGW_OPT_OVERLAP = 11 };
+       BGW_OPT_OVERLAP = 11, BGW_OPT_FP64_CONTRACTION = 12 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

@@ -25,6 +25,7 @@
 #include "../../include/bgw_chi.h"
 #include "bgw_internal.h"
 #include "bgw_mixed.h"
+#include "bgw_f64tc.h"
 
 namespace {
 
@@ -191,6 +192,7 @@ struct bgw_ctx_s {
     int copy_ahead = 0;           // BGW_OPT_COPY_AHEAD
     cudaStream_t cst = nullptr;   // copy stream of copy-ahead host uploads
     int overlap = 0;              // BGW_OPT_OVERLAP
+    int f64_dfma = 0;             // BGW_OPT_FP64_CONTRACTION: 1 = FP64 FMA kernel, 0 = digit slices on tcgen05
     cudaStream_t gst = nullptr;   // contraction stream of the overlapped mixed path
     cudaEvent_t ov_fork = nullptr, ov_join = nullptr, ov_free[2] = {nullptr, nullptr};
     int npending = 0;             // uploads whose grid is not built yet
@@ -596,6 +598,12 @@ size_t mixed_q_bytes(const bgw_ctx_s *c, const QState &s, int nfreq, int kchunk)
     return align256(bgw::mixed_workspace_bytes((long)kchunk * c->nv * s.nc, s.ng, nfreq));
 }
 
+// Workspace of the FP64 contraction of P pairs (either kernel).
+size_t f64_ws_bytes(const bgw_ctx_s *c, long P, int ng, int nfreq) {
+    return c->f64_dfma ? bgw::herk_f64_workspace_bytes((int)P, ng, nfreq, c->sm_count)
+                       : bgw::f64tc_workspace_bytes(P, ng, nfreq);
+}
+
 // Consecutive q-points contracted by one grouped launch (mixed path): at
 // most mixed_max_group() of them and, past the first, no more than
 // kGroupBytes of split operands.  FP64: one q per group.
@@ -651,8 +659,7 @@ cudaError_t ensure_chunk_scratch(bgw_ctx_s *c, const std::vector<QState> &qs, in
             if (c->prec != BGW_FP64)
                 sum += mixed_q_bytes(c, s, nfreq, kchunk);
             else
-                sum = std::max(sum, bgw::herk_f64_workspace_bytes((int)(kchunk * c->nv * s.nc), s.ng,
-                                                                  nfreq, c->sm_count));
+                sum = std::max(sum, f64_ws_bytes(c, (long)kchunk * c->nv * s.nc, s.ng, nfreq));
         }
         ws = std::max(ws, sum);
     }
@@ -807,9 +814,13 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
                 }
                 if (c->prec == BGW_FP64) {
                     const int rec = c->stage_begin(3);
-                    e = bgw::herk_f64(M, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
-                                      s.acc.p, c->mixed_ws.p, c->sm_count, c->st);
-                    c->stage_end(rec, 2);
+                    if (c->f64_dfma)
+                        e = bgw::herk_f64(M, PT, s.ng, static_cast<const double *>(c->W.p), nfreq,
+                                          s.acc.p, c->mixed_ws.p, c->sm_count, c->st);
+                    else
+                        e = bgw::f64tc_contract(M, PT, s.ng, static_cast<const double *>(c->W.p), nfreq, s.acc.p,
+                                                c->mixed_ws.p, c->sm_count, c->st, static_cast<int *>(c->errflag.p));
+                    c->stage_end(rec, c->f64_dfma ? 2 : 3);
                     if (e != cudaSuccess) return join(), e;
                 } else {
                     void *ws = static_cast<char *>(c->mixed_ws.p) + off;
@@ -1285,6 +1296,12 @@ bgw_status bgw_chi0_finalize(bgw_ctx c, int iq, void *chi0, int on_device) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return c->cuda_fail(e, "finalize: copy to host");
+    if (flag == bgw::F64TC_ERR_SIGN) {
+        cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st);
+        return c->fail(BGW_E_ARG, "finalize: a pair weight was positive (an occupied band above an empty one); "
+                                  "the tensor-core FP64 contraction needs every e_v < e_c: set "
+                                  "BGW_OPT_FP64_CONTRACTION to 1 for such inputs");
+    }
     if (flag != 0) {
         cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st);
         return c->fail(BGW_E_TIMEOUT, "finalize: a device-side wait gave up (code %d); the result is invalid",
@@ -1352,6 +1369,9 @@ bgw_status bgw_chi0_checkpoint(bgw_ctx c, void *buf, size_t bytes) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return c->cuda_fail(e, "checkpoint: copy to host");
+    if (flag == bgw::F64TC_ERR_SIGN)
+        return c->fail(BGW_E_ARG, "checkpoint: a pair weight was positive; the tensor-core FP64 contraction "
+                                  "left it out (set BGW_OPT_FP64_CONTRACTION to 1 for such inputs)");
     if (flag != 0)
         return c->fail(BGW_E_TIMEOUT, "checkpoint: a device-side wait gave up (code %d); the sum is invalid", flag);
     return BGW_OK;
@@ -1437,6 +1457,11 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
             if (c->capturing) return c->fail(BGW_E_STATE, "set_option: overlap cannot change during a capture");
             c->overlap = (int)value;
             return BGW_OK;
+        case BGW_OPT_FP64_CONTRACTION:
+            if (value != 0 && value != 1) return c->fail(BGW_E_ARG, "set_option: FP64 contraction must be 0 or 1");
+            if (c->capturing) return c->fail(BGW_E_STATE, "set_option: contraction kernel cannot change during a capture");
+            c->f64_dfma = (int)value;
+            return BGW_OK;
         case BGW_OPT_TEST_FAIL_ALLOC:
             if (value < 0) return c->fail(BGW_E_ARG, "set_option: allocation count must be >= 0");
             g_fail_alloc.store(value);
@@ -1466,6 +1491,7 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_DEFER_K1: *value = c->defer_k1; return BGW_OK;
         case BGW_OPT_COPY_AHEAD: *value = c->copy_ahead; return BGW_OK;
         case BGW_OPT_OVERLAP: *value = c->overlap; return BGW_OK;
+        case BGW_OPT_FP64_CONTRACTION: *value = c->f64_dfma; return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }
@@ -1570,8 +1596,7 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
                 if (c->prec != BGW_FP64)
                     ws = std::max(ws, bgw::mixed_workspace_bytes((long)kc * c->nv * s.nc, s.ng, nfreq));
                 else
-                    ws = std::max(ws, bgw::herk_f64_workspace_bytes(kc * c->nv * s.nc, s.ng, nfreq,
-                                                                    c->sm_count));
+                    ws = std::max(ws, f64_ws_bytes(c, (long)kc * c->nv * s.nc, s.ng, nfreq));
             }
             if (ws + mb > ((size_t)2 << 30)) break;
             float ms = 0;

@@ -39,9 +39,12 @@
 #include <mutex>
 
 #include "bgw_mixed.h"
+#include "bgw_tc_common.cuh"
 
 namespace bgw {
 namespace {
+
+using namespace tc;
 
 constexpr int kTileM = 128;           // rows of D per CTA (A rows)
 constexpr int kTileN = 128;           // columns of D per CTA (B rows)
@@ -51,8 +54,6 @@ constexpr int kTileBytes = kTileM * kBlockK * 2;                 // 16 KB per op
 constexpr int kStageBytes = 4 * kTileBytes;                      // A_hi, A_lo, B_hi, B_lo
 constexpr int kAccCols = 4 * kTileN;                             // 3 hi.hi + 1 cross accumulator
 constexpr int kMaxGroup = 48;                                    // q-points per grouped launch
-constexpr uint32_t kSpinLimit = 1u << 26;          // backstop; the time limit ends waits first
-constexpr uint64_t kWaitNs = 2000000000ull;          // a device-side wait gives up after ~2 s
 constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
 
 // ------------------------------------------------------------ split kernel --
@@ -135,50 +136,6 @@ k5_split(const float2 *__restrict__ M, int P, int ng, const double *__restrict__
     }
 }
 
-// --------------------------------------------------------- PTX helpers --
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait: false once ~kWaitNs of wall time (or kSpinLimit polls) pass.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t i = 1; i < kSpinLimit; ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if (i > 32) __nanosleep(64);
-        if ((i & 255) == 0 && global_ns() - t0 > kWaitNs) return false;
-    }
-    return false;
-}
-
 // One 128 x 64 tile (k-block kb, row tile rt, plane) of the tiled operand
 // layout: coordinates {0, 0, kb, rt, plane} of the 5-D map.
 __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap *map, uint32_t bar, int kb,
@@ -218,25 +175,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void lower_tile(int t, int &bi, int &bj) {
     int i = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
     while ((i + 1) * (i + 2) / 2 <= t) ++i;
@@ -271,10 +209,6 @@ struct GroupParams {
     int nq, nfreq;
     int drop_first_load;          // test hook: block 0 never issues its first stage
 };
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 struct Item {
     int q, ti, tj, j, nkb;
@@ -541,23 +475,8 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
 
 // ---------------------------------------------------------- tensor map --
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-std::once_flag g_encode_once;
-cudaError_t g_encode_status = cudaSuccess;
 
-cudaError_t get_encoder() {
-    std::call_once(g_encode_once, [] {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                         cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
-            g_encode_status = (e != cudaSuccess) ? e : cudaErrorNotSupported;
-            return;
-        }
-        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    });
-    return g_encode_status;
-}
+cudaError_t get_encoder() { return tc::tensor_map_encoder(&g_encode); }
 
 long round_up(long x, long m) { return (x + m - 1) / m * m; }
 
