@@ -87,6 +87,8 @@ def parse_args():
     ap.add_argument("--fp64-ks", type=int, default=4, metavar="N",
                     help="FP64 leg of a mixed headline: k-points 0..N-1 and the first N k-points with an "
                          "umklapp (k+q = k'+G0, G0 != 0)")
+    ap.add_argument("--fp64-dfma", action="store_true",
+                    help="FP64 path: contract on the FP64 pipe (FMA kernel) instead of the tensor cores")
     ap.add_argument("--no-autotune", action="store_true", help="default tiles and k-chunk")
     ap.add_argument("--grid-slots", type=int, default=-1,
                     help="real-space grid slots (0 = all k resident; default 8 for bi2se3, else 0)")
@@ -546,6 +548,8 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_COPY_AHEAD, 1)
     if args.overlap and precision == "mixed":
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_OVERLAP, 1)
+    if precision == "fp64" and args.fp64_dfma:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_FP64_CONTRACTION, 1)
     ctx.upload(device_inputs=dev_in)
     tune_span = min(p.nk, 16)
     if fixed_fp64:
@@ -610,7 +614,8 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     fl = flop_model(p)
     burst, sustained, _ = bf16_peaks()
     f64 = (args.fp64_peak, "FP64 DGEMM (measured in this run)")
-    peaks = ({"wfn_to_grid": f64, "mtxel": f64, "contraction": f64}
+    f64c = f64 if args.fp64_dfma else (sustained / 15, "BF16 sustained / 15 digit products")
+    peaks = ({"wfn_to_grid": f64, "mtxel": f64, "contraction": f64c}
              if precision == "fp64" else
              {"wfn_to_grid": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
               "mtxel": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
@@ -809,6 +814,8 @@ def fp64_leg(B, torch, p, args, stream, dev_in, ks, reps=2):
     if len(need) + 2 < p.nk:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_GRID_SLOTS, len(need) + 2)
     B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk if args.kchunk > 0 else 4)
+    if args.fp64_dfma:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_FP64_CONTRACTION, 1)
     ctx.upload(device_inputs=dev_in)
     q, geps, nc = p.qs[0]
     ng, nf = len(geps), len(p.freq)
@@ -832,7 +839,12 @@ def fp64_leg(B, torch, p, args, stream, dev_in, ks, reps=2):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = statistics.median(times)
-    return ctx, out.cpu().numpy(), ms / len(ks)
+    B.bgw_profile(ctx.ctx, True)
+    run()
+    prof = B.bgw_profile_read(ctx.ctx)
+    B.bgw_profile(ctx.ctx, False)
+    stages = {k: v[0] / len(ks) for k, v in prof.items() if v[1]}
+    return ctx, out.cpu().numpy(), ms / len(ks), stages
 
 
 def head_roofline(p, res, precision, args, steps):
@@ -849,11 +861,15 @@ def head_roofline(p, res, precision, args, steps):
                                  "and these sources (pass --traffic-bytes); none is taken by the timed run")
     if ct >= mt:
         ach = fl["contraction"] / (ct * 1e-3) / 1e12
-        if precision == "fp64":
+        if precision == "fp64" and args.fp64_dfma:
             r = {"bound": "alu", "kernel": "k4_herk_f64", "achieved": ach, "peak": args.fp64_peak,
                  "unit": "TFLOP/s", "frac": ach / args.fp64_peak,
                  "peak_source": "FP64 DGEMM measured in this run (torch.matmul 8192^3)",
                  "derived_fp64_peak_tflops": FP64_PEAK_DERIVED_TFLOPS}
+        elif precision == "fp64":
+            r = {"bound": "tensor", "kernel": "k5z_gemm (with its exponent and digit-split passes)",
+                 "achieved": ach, "peak": sustained / 15, "unit": "TFLOP/s", "frac": ach / (sustained / 15),
+                 "peak_source": f"{src} BF16 sustained {sustained} TFLOP/s / 15 digit products"}
         else:
             r = {"bound": "tensor", "kernel": "k5_gemm", "achieved": ach, "peak": sustained / 3,
                  "unit": "TFLOP/s", "frac": ach / (sustained / 3),
@@ -937,13 +953,16 @@ def run_ours(args, world, rank, local):
             n = min(args.fp64_ks, p.nk)
             umk = umklapp_ks(p)
             ks = sorted(set(range(n)) | set(umk[:n]))
-            octx, chi64, per_k = fp64_leg(B, torch, p, args, stream, dev_in, ks)
+            octx, chi64, per_k, st64 = fp64_leg(B, torch, p, args, stream, dev_in, ks)
             chimx = chi0_on(B, head["ctx"], [(q, geps, nc)], p.freq, ks)
             ms64 = per_k * p.nk
             other = {"precision": "fp64 (FP64 grids, FFTs, M and contraction)",
                      "k_subset": ks, "k_subset_note": f"k = 0..{n - 1} and the first {n} k-points with an "
                                                       "umklapp; per-k time x N_k",
+                     "contraction": "FP64 FMA kernel" if args.fp64_dfma else
+                                    "tensor cores, exact BF16 digit slices (FP64 accuracy)",
                      "ms_per_k": per_k, "ms_per_q_extrapolated": ms64,
+                     "stage_ms_per_k": st64,
                      "value": world * 1e3 / ms64, "unit": "q-points/s (extrapolated from the k-subset)",
                      "speedup_mixed_vs_fp64": ms64 / ms,
                      "mixed_vs_fp64_on_subset": error_stats(chimx, chi64),
