@@ -93,6 +93,11 @@ def parse_args():
     ap.add_argument("--grid-slots", type=int, default=-1,
                     help="real-space grid slots (0 = all k resident; default 8 for bi2se3, else 0)")
     ap.add_argument("--kchunk", type=int, default=0, help="k-chunk when not autotuning")
+    ap.add_argument("--pair-tile", type=int, nargs=2, default=None, metavar=("TV", "TC"),
+                    help="pair tile of the FP32 matrix-element kernel when not autotuning")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the hot path only: no eps^-1/W, unfolding, e2e, other precision, CPU baseline or "
+                         "secondary workload (for profiler launch lists)")
     ap.add_argument("--k1-path", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="sphere -> grid kernels: 0 automatic, 1 per axis, 2 one kernel per band component, "
                          "3 eight lanes per line (cubic 32/40/48/64), 4 one kernel without the shared cube")
@@ -452,6 +457,8 @@ def make_workload(name, coeff_on="cuda"):
         p.coeff = [c.numpy() for c in p.coeff]
         return p, desc
     over = dict(over)
+    if name.endswith("_small") and coeff_on is not None:
+        coeff_on = "host"      # profilers run these; the device QR's lazily loaded library is not found under them
     return syn.make_problem(over.pop("config"), coeff_on=coeff_on, **over), desc
 
 
@@ -538,6 +545,9 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     fixed_fp64 = precision == "fp64" and not args.no_autotune and args.kchunk == 0
     if args.kchunk > 0 or fixed_fp64:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk if args.kchunk > 0 else min(4, p.nk))
+    if args.pair_tile:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_PAIR_TILE_V, args.pair_tile[0])
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_PAIR_TILE_C, args.pair_tile[1])
     if args.k1_path > 0:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_K1_PATH, args.k1_path)
     if args.mtxel_lanes > 0:
@@ -613,7 +623,7 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     # achieved algorithmic rate and roofline fraction of each stage with a FLOP model
     fl = flop_model(p)
     burst, sustained, _ = bf16_peaks()
-    f64 = (args.fp64_peak, "FP64 DGEMM (measured in this run)")
+    f64 = (args.fp64_peak, args.fp64_peak_label)
     f64c = f64 if args.fp64_dfma else (sustained / 15, "BF16 sustained / 15 digit products")
     peaks = ({"wfn_to_grid": f64, "mtxel": f64, "contraction": f64c}
              if precision == "fp64" else
@@ -864,7 +874,7 @@ def head_roofline(p, res, precision, args, steps):
         if precision == "fp64" and args.fp64_dfma:
             r = {"bound": "alu", "kernel": "k4_herk_f64", "achieved": ach, "peak": args.fp64_peak,
                  "unit": "TFLOP/s", "frac": ach / args.fp64_peak,
-                 "peak_source": "FP64 DGEMM measured in this run (torch.matmul 8192^3)",
+                 "peak_source": args.fp64_peak_label,
                  "derived_fp64_peak_tflops": FP64_PEAK_DERIVED_TFLOPS}
         elif precision == "fp64":
             r = {"bound": "tensor", "kernel": "k5z_gemm (with its exponent and digit-split passes)",
@@ -879,7 +889,7 @@ def head_roofline(p, res, precision, args, steps):
         pk = args.fp64_peak if precision == "fp64" else FP32_PEAK_TFLOPS
         r = {"bound": "alu", "kernel": "matrix elements (pair density + pruned FFT + gather)",
              "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-             "peak_source": ("FP64 DGEMM measured in this run" if precision == "fp64" else
+             "peak_source": (args.fp64_peak_label if precision == "fp64" else
                              "FP32 FFMA from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz")}
     r["traffic"] = traffic
     if note:
@@ -920,7 +930,11 @@ def run_ours(args, world, rank, local):
     build.build()
     from paper_2206_00808_gb300 import binding as B
 
-    args.fp64_peak = dgemm_tflops()
+    if args.no_extras:
+        args.no_e2e = args.no_other = args.no_cpu_baseline = args.no_secondary = True
+    args.fp64_peak = dgemm_tflops() if not args.no_extras else FP64_PEAK_DERIVED_TFLOPS
+    args.fp64_peak_label = ("FP64 DGEMM (measured in this run)" if not args.no_extras else
+                            "FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz")
     p, desc = make_workload(args.workload, coeff_on="cuda")
     if args.grid_slots < 0:
         args.grid_slots = 8 if args.workload == "bi2se3" else 0
@@ -941,8 +955,8 @@ def run_ours(args, world, rank, local):
     ms = head["ms"]
     value = world * nq * 1e3 / ms
     roofline = head_roofline(p, head, args.precision, args, steps)
-    epsinv = epsinv_measure(B, torch, p, head, stream, args.fp64_peak)
-    unfold = unfold_measure(B, torch, p, dev_in, stream)
+    epsinv = None if args.no_extras else epsinv_measure(B, torch, p, head, stream, args.fp64_peak)
+    unfold = None if args.no_extras else unfold_measure(B, torch, p, dev_in, stream)
     e2e = None if args.no_e2e else e2e_measure(B, torch, p, head, args, dist, stream)
 
     # the other precision: FP64 on a labelled k-subset (mixed headline), or
