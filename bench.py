@@ -51,6 +51,10 @@ WORKLOADS = {
     "bi2se3": ("bi2se3", "Bi2Se3-like rhombohedral cell (hex a=4.143 A, c=28.636 A), 64^3 box, "
                          "N_w~9000 per spinor component, N_G=2000, N_k=216 (6x6x6), N_v=48, N_c=1000, "
                          "8 imaginary freqs, q=(1/6,0,0); real-space grids streamed through 8 slots"),
+    "bi2se3_48": ("bi2se3_48", "Bi2Se3-like rhombohedral cell, literal 48^3 box with the largest alias-free "
+                               "wavefunction sphere (32.5 Ry, N_w~3000 per spinor component), N_G=2000, "
+                               "N_k=216 (6x6x6), N_v=48, N_c=1000, 8 imaginary freqs, q=(1/6,0,0); grids "
+                               "streamed through 8 slots"),
     # profiling case: the 64^3 box and N_G = 2000 on a 2x2x2 k-grid with 8 + 40 bands (~1.5 GB)
     "bi2se3_small": ("bi2se3_small", "Bi2Se3-like cell, 64^3 box, N_G=2000, 2x2x2 k-grid, N_v=8, N_c=40, "
                                      "2 freqs, q=(1/2,0,0)"),
@@ -450,6 +454,8 @@ def make_workload(name, coeff_on="cuda"):
         return syn.make_batched_problem(), desc
     if over == "bi2se3":
         return syn.make_bi2se3_problem(device=coeff_on), desc
+    if over == "bi2se3_48":
+        return syn.make_bi2se3_problem(box=(48, 48, 48), ecut_wfn=32.5, device=coeff_on), desc
     if over == "bi2se3_small":
         # generated on the host (torch CPU QR): profilers run this case, and the
         # device QR's lazily loaded library is not found under them
@@ -937,7 +943,7 @@ def run_ours(args, world, rank, local):
                             "FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz")
     p, desc = make_workload(args.workload, coeff_on="cuda")
     if args.grid_slots < 0:
-        args.grid_slots = 8 if args.workload == "bi2se3" else 0
+        args.grid_slots = 8 if args.workload in ("bi2se3", "bi2se3_48") else 0
     q, geps, nc = p.qs[0]
     ng, nf = len(geps), len(p.freq)
     stream = torch.cuda.Stream()      # graph capture needs a non-default stream

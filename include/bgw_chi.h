@@ -545,6 +545,20 @@ BGW_API bgw_status bgw_bse_kernel(bgw_ctx ctx, int ik, int jk, const bgw_q *q0, 
                                   const bgw_q *qd, const void *W_dev, int v0, int nv, int c0, int nc,
                                   void *KX_dev, void *KD_dev);
 
+/*
+ * Index checks (a development aid; the paper has no counterpart).  The
+ * library built with -DBGW_BOUNDS=1 (libbgwchi_bounds.so) tests every index
+ * its kernels read from a device map against the range it must lie in: the
+ * cube, inverse, gather and scatter maps of the FFT passes and the k + q map
+ * of the pair weights.  An index out of range skips that access and sets bit
+ * `site` in a device status word (0 cube map, 1 inverse map, 2 gather map,
+ * 3 scatter map, 4 k + q map); nothing traps.  bgw_bounds_check waits for the
+ * device, returns the OR of the words in *word and clears them.  In the
+ * default build it returns BGW_E_STATE with *word = 0.  Errors go to
+ * bgw_last_error(NULL).
+ */
+BGW_API bgw_status bgw_bounds_check(unsigned *word);
+
 /* Release every device buffer of the context (synchronizes its stream). */
 BGW_API void bgw_destroy(bgw_ctx ctx);
 

@@ -14,7 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-LIB_PATH = _build.LIB
+# BGW_LIBRARY=bounds loads the index-checking build (libbgwchi_bounds.so)
+LIB_PATH = _build.LIB_BOUNDS if os.environ.get("BGW_LIBRARY") == "bounds" else _build.LIB
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_2206_00808_gb300.build.build()")
 _lib = ctypes.CDLL(LIB_PATH)
@@ -30,7 +31,8 @@ EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "
             "bgw_graph_begin", "bgw_graph_end", "bgw_graph_launch", "bgw_chi0_progress",
             "bgw_chi0_checkpoint_bytes", "bgw_chi0_checkpoint", "bgw_chi0_resume", "bgw_coulomb_sqrt",
             "bgw_epsinv_workspace_bytes", "bgw_epsinv", "bgw_symmetry_su2", "bgw_unfold_spinor",
-            "bgw_mtxel_bands", "bgw_sigma_cohsex", "bgw_bse_kernel", "bgw_destroy", "bgw_last_error"]
+            "bgw_mtxel_bands", "bgw_sigma_cohsex", "bgw_bse_kernel", "bgw_bounds_check", "bgw_destroy",
+            "bgw_last_error"]
 BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C, BGW_OPT_GRID_SLOTS = 1, 2, 3, 4
 BGW_OPT_TEST_DROP_LOAD, BGW_OPT_TEST_FAIL_ALLOC, BGW_OPT_K1_PATH, BGW_OPT_MTXEL_LANES = 5, 6, 7, 8
 BGW_OPT_DEFER_K1, BGW_OPT_COPY_AHEAD, BGW_OPT_OVERLAP, BGW_OPT_FP64_CONTRACTION = 9, 10, 11, 12
@@ -76,6 +78,7 @@ _lib.bgw_mtxel_bands.argtypes = [_P, ctypes.POINTER(bgw_q), _I, _I, _I, _I, _I, 
 _lib.bgw_sigma_cohsex.argtypes = [_P, ctypes.POINTER(bgw_q), _I, _I, _I, _P, _P, _P, _P]
 _lib.bgw_bse_kernel.argtypes = [_P, _I, _I, ctypes.POINTER(bgw_q), _P, ctypes.POINTER(bgw_q), _P, _I, _I, _I, _I,
                                 _P, _P]
+_lib.bgw_bounds_check.argtypes, _lib.bgw_bounds_check.restype = [ctypes.POINTER(ctypes.c_uint)], ctypes.c_int
 for _f in ["bgw_mtxel_bands", "bgw_sigma_cohsex", "bgw_bse_kernel"]:
     getattr(_lib, _f).restype = ctypes.c_int
 _lib.bgw_destroy.argtypes, _lib.bgw_destroy.restype = [_P], None
@@ -359,6 +362,14 @@ def bgw_bse_kernel(ctx, ik: int, jk: int, q0, gvec0, v0_coul, qd, gvecd, W_dev, 
                              pd)
     del k0, kd
     return _check(st, ctx)
+
+
+def bgw_bounds_check():
+    """(status, word): the index-check status word of the bounds-checking
+    build, read and cleared (status BGW_E_STATE in the default build)."""
+    w = ctypes.c_uint(0)
+    st = _lib.bgw_bounds_check(ctypes.byref(w))
+    return st, w.value
 
 
 def bgw_set_option(ctx, option: int, value: int) -> int:

@@ -1767,6 +1767,29 @@ void bgw_destroy(bgw_ctx c) {
     delete c;
 }
 
+bgw_status bgw_bounds_check(unsigned *word) {
+    if (!word) {
+        bgw_set_global_error("bounds_check: null pointer argument");
+        return BGW_E_ARG;
+    }
+    *word = 0u;
+    if (!bgw::kBoundsBuild) {
+        bgw_set_global_error("bounds_check: this library was built without BGW_BOUNDS (no index checks)");
+        return BGW_E_STATE;
+    }
+    unsigned a = 0u, b = 0u, d = 0u;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = bgw::bounds_take_grid_f64(&a);
+    if (e == cudaSuccess) e = bgw::bounds_take_grid_f32(&b);
+    if (e == cudaSuccess) e = bgw::bounds_take_chi0(&d);
+    if (e != cudaSuccess) {
+        bgw_set_global_error(std::string("bounds_check: ") + cudaGetErrorString(e));
+        return BGW_E_CUDA;
+    }
+    *word = a | b | d;
+    return BGW_OK;
+}
+
 bgw_status bgw_mtxel_bands(bgw_ctx c, const bgw_q *q, int ik, int n0, int nn, int m0, int nm, void *M_dev) {
     if (!c) return BGW_E_ARG;
     DeviceGuard dg(c->device);

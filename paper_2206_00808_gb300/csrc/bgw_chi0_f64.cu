@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "bgw_bounds.cuh"
 #include "bgw_internal.h"
 
 namespace bgw {
@@ -30,8 +31,13 @@ __global__ void k3_pair_weights(const double *__restrict__ energy, int nb, int n
     const int kl = (int)(pt / P);
     const long p = pt % P;
     const int k = k0 + kl;
+    const int kq = kmap[k];
+    if (!BGW_IN_BOUNDS(kq >= 0, kBoundsKMap)) {
+        w[t] = 0.0;
+        return;
+    }
     const double ev = energy[(long)k * nb + p / nc];
-    const double ec = energy[(long)kmap[k] * nb + nv + p % nc];
+    const double ec = energy[(long)kq * nb + nv + p % nc];
     const double d = ev - ec;
     const double f = freq[j];
     w[t] = 2.0 * d / (d * d + f * f);
@@ -231,6 +237,8 @@ cudaError_t herk_f64(const void *M, int P, int ng, const double *w, int nfreq, v
                                                                static_cast<double2 *>(acc));
     return cudaGetLastError();
 }
+
+cudaError_t bounds_take_chi0(unsigned *word) { return bgw_bounds_take(word); }
 
 cudaError_t chi0_finalize(const void *acc, int ng, int nfreq, double scale, void *out,
                           cudaStream_t st) {

@@ -21,4 +21,5 @@ cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes
 int plane_tile_candidates(int nv, int nc, const Axes &a, int *tv, int *tc, int max) {
     return f32::plane_tile_list(nv, nc, a, tv, tc, max);
 }
+cudaError_t bounds_take_grid_f32(unsigned *word) { return bgw_bounds_take(word); }
 }  // namespace bgw

@@ -17,4 +17,5 @@ cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes
                       cudaStream_t st, int tv, int tc, int lanes) {
     return f64::mtxel(Uv, Uc, nv, nc, a, gmap, ng, A, Bs, M, ldm, st, tv, tc, lanes);
 }
+cudaError_t bounds_take_grid_f64(unsigned *word) { return bgw_bounds_take(word); }
 }  // namespace bgw

@@ -22,6 +22,7 @@
 #pragma once
 #include <cmath>
 
+#include "bgw_bounds.cuh"
 #include "bgw_fft.cuh"
 #include "bgw_internal.h"
 
@@ -92,7 +93,7 @@ k1_xpass(const double2 *__restrict__ coeff, int ngw, long B, const int *__restri
         C v = {T(0), T(0)};
         if (j < w0) {
             const int idx = __ldg(cube_map + j * yzs + yz);
-            if (idx >= 0) {
+            if (idx >= 0 && BGW_IN_BOUNDS(idx < ngw, kBoundsCubeMap)) {
                 const double2 c = __ldg(coeff + b * ngw + idx);
                 v = {(T)c.x, (T)c.y};
             }
@@ -223,7 +224,8 @@ k2_xpass_gather(const C *__restrict__ Bs, long P, int PP, int w0, int w1, int w2
     __syncthreads();
     for (int i = threadIdx.x; i < np * ng; i += kGatherThreads) {
         const int pp = i / ng, g = i % ng;
-        const C v = cube[pp * csz + __ldg(gmap + g)];
+        const int cell = __ldg(gmap + g);
+        const C v = BGW_IN_BOUNDS(cell >= 0 && cell < csz, kBoundsGatherMap) ? cube[pp * csz + cell] : C{T(0), T(0)};
         M[(p0 + pp) * ldm + g] = C{v.x * scale, v.y * scale};
     }
 }
@@ -261,7 +263,7 @@ k2_xpass_scatter(const C *__restrict__ Bs, long P, int w0, int w1, int w2, int s
         const int j = rot<N>(f, ns);
         if (j < w0) {
             const int g = __ldg(imap + j * lines + l);
-            if (g >= 0) M[p * ldm + g] = C{a[f].x * scale, a[f].y * scale};
+            if (g >= 0 && BGW_IN_BOUNDS(g < ldm, kBoundsScatterMap)) M[p * ldm + g] = C{a[f].x * scale, a[f].y * scale};
         }
     }
 }
@@ -410,7 +412,7 @@ k2_xpass_scatter_oct(const C *__restrict__ Bs, long P, int w0, int w1, int w2, i
         const int jj = rot<N>(t + M * k1, ns);
         if (jj < w0) {
             const int g = __ldg(imap + jj * lines + l);
-            if (g >= 0) Mo[p * ldm + g] = C{out[k1].x * scale, out[k1].y * scale};
+            if (g >= 0 && BGW_IN_BOUNDS(g < ldm, kBoundsScatterMap)) Mo[p * ldm + g] = C{out[k1].x * scale, out[k1].y * scale};
         }
     }
 }
@@ -442,7 +444,7 @@ k1_xpass_oct(const double2 *__restrict__ coeff, int ngw, long B, const int *__re
         C v = {T(0), T(0)};
         if (j < w0) {
             const int idx = __ldg(cube_map + j * yzs + yz);
-            if (idx >= 0) {
+            if (idx >= 0 && BGW_IN_BOUNDS(idx < ngw, kBoundsCubeMap)) {
                 const double2 c = __ldg(coeff + b * ngw + idx);
                 v = {(T)c.x, (T)c.y};
             }
@@ -560,7 +562,8 @@ k2_xpass_scatter_c4(const C *__restrict__ Bs, long P, int w0, int w1, int w2, in
             const int jj = rot<N>(t * Q + j + MM * k1, ns);
             if (jj < w0) {
                 const int g = __ldg(imap + jj * lines + l);
-                if (g >= 0) M[p * ldm + g] = C{out[k1][j].x * scale, out[k1][j].y * scale};
+                if (g >= 0 && BGW_IN_BOUNDS(g < ldm, kBoundsScatterMap))
+                    M[p * ldm + g] = C{out[k1][j].x * scale, out[k1][j].y * scale};
             }
         }
 }
@@ -595,7 +598,8 @@ __device__ __forceinline__ void k1_fused_body(const double2 *__restrict__ cb, in
         __syncthreads();
         for (int i = threadIdx.x; i < ngw; i += kFusedThreads) {
             const double2 c = __ldg(cb + i);
-            cube[__ldg(inv + i)] = C{(T)c.x, (T)c.y};
+            const int cell = __ldg(inv + i);
+            if (BGW_IN_BOUNDS(cell >= 0 && cell < ncube, kBoundsInverseMap)) cube[cell] = C{(T)c.x, (T)c.y};
         }
         __syncthreads();
     }
@@ -611,7 +615,7 @@ __device__ __forceinline__ void k1_fused_body(const double2 *__restrict__ cb, in
                 C v = {T(0), T(0)};
                 if (j < w0) {
                     const int idx = __ldg(cmap + j * yzs + l);
-                    if (idx >= 0) {
+                    if (idx >= 0 && BGW_IN_BOUNDS(idx < ngw, kBoundsCubeMap)) {
                         const double2 c = __ldg(cb + idx);
                         v = {(T)c.x, (T)c.y};
                     }

@@ -3,6 +3,12 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#ifdef BGW_BOUNDS
+#define BGW_BOUNDS_BUILD (BGW_BOUNDS != 0)
+#else
+#define BGW_BOUNDS_BUILD false
+#endif
+
 namespace bgw {
 
 // Extents of a pruned transform along the three box axes.
@@ -124,6 +130,14 @@ cudaError_t herk_f64(const void *M, int P, int ng, const double *w, int nfreq, v
 // out[j][g][g'] = scale * (g >= g' ? acc[j][g][g'] : conj(acc[j][g'][g])).
 cudaError_t chi0_finalize(const void *acc, int ng, int nfreq, double scale, void *out,
                           cudaStream_t st);
+
+// ---- bounds-checking build (bgw_bounds.cuh) ------------------------------
+// Each translation unit's index-check status word, read and cleared; always
+// 0 in the default build.
+cudaError_t bounds_take_grid_f64(unsigned *word);
+cudaError_t bounds_take_grid_f32(unsigned *word);
+cudaError_t bounds_take_chi0(unsigned *word);
+constexpr bool kBoundsBuild = BGW_BOUNDS_BUILD;
 
 // ---- bgw_zgemm.cu (FP64, for the self-energy and BSE kernel steps) -------
 // C(m, n) = [C(m, n) if accumulate] + alpha sum_k opA(m, k) wk[k] opB(k, n),

@@ -119,3 +119,10 @@ def test_symmetry_rejects_non_rotations():
         B.bgw_symmetry_su2(avec, np.array([[2, 0, 0], [0, 1, 0], [0, 0, 1]]))   # not unimodular
     with pytest.raises(B.BgwError):
         B.bgw_symmetry_su2(avec, np.array([[1, 1, 0], [0, 1, 0], [0, 0, 1]]))   # shear: not a rotation
+
+
+def test_default_build_has_no_index_checks():
+    from paper_2206_00808_gb300 import binding as B
+    st, word = B.bgw_bounds_check()
+    assert st == B.BGW_E_STATE and word == 0
+    assert "BGW_BOUNDS" in B.bgw_last_error(None)
