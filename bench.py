@@ -105,6 +105,8 @@ def parse_args():
     ap.add_argument("--k1-path", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="sphere -> grid kernels: 0 automatic, 1 per axis, 2 one kernel per band component, "
                          "3 eight lanes per line (cubic 32/40/48/64), 4 one kernel without the shared cube")
+    ap.add_argument("--mtxel-zy", type=int, default=0, choices=[0, 1, 2],
+                    help="FP32 pair density + z + y kernel: 0 automatic, 1 plane kernel, 2 streamed")
     ap.add_argument("--mtxel-lanes", type=int, default=0, choices=[0, 1, 8],
                     help="FFT lanes per line of the matrix-element kernels (0 automatic)")
     ap.add_argument("--defer-k1", type=int, default=1, choices=[0, 1],
@@ -558,6 +560,8 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_K1_PATH, args.k1_path)
     if args.mtxel_lanes > 0:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_MTXEL_LANES, args.mtxel_lanes)
+    if args.mtxel_zy > 0:
+        B.bgw_set_option(ctx.ctx, B.BGW_OPT_MTXEL_ZY, args.mtxel_zy)
     if args.defer_k1:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_DEFER_K1, 1)
     if args.copy_ahead:

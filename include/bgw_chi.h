@@ -334,6 +334,16 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        one elsewhere), 1 one, 8 eight where the box is cubic
  *                        with N = 32, 40, 48 or 64.  Same results up to
  *                        rounding.
+ *   BGW_OPT_MTXEL_ZY     pair density + z and y passes of the FP32 matrix-
+ *                        element kernels on boxes with N2 = N3 <= 40: 0
+ *                        automatic (default: the streamed kernel where it
+ *                        applies, even N2 <= 32), 1 the plane kernel with the
+ *                        pair tile of BGW_OPT_PAIR_TILE_V/C (or the autotuner's),
+ *                        2 the streamed kernel where it applies: a CTA keeps
+ *                        four valence x-planes in shared memory and streams the
+ *                        conduction x-planes in groups of four, copying the next
+ *                        group while the current one is transformed.  Same
+ *                        results up to rounding.
  *   BGW_OPT_DEFER_K1     0 (default): bgw_wfn_upload builds the k-point's
  *                        real-space grid before it returns (on the stream).
  *                        1: the build is deferred to the next call that reads
@@ -401,7 +411,7 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
 enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
        BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7,
        BGW_OPT_MTXEL_LANES = 8, BGW_OPT_DEFER_K1 = 9, BGW_OPT_COPY_AHEAD = 10,
-       BGW_OPT_OVERLAP = 11, BGW_OPT_FP64_CONTRACTION = 12 };
+       BGW_OPT_OVERLAP = 11, BGW_OPT_FP64_CONTRACTION = 12, BGW_OPT_MTXEL_ZY = 13 };
 BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 

@@ -188,6 +188,7 @@ struct bgw_ctx_s {
     int test_drop_load = 0;       // BGW_OPT_TEST_DROP_LOAD
     int k1_path = 0;              // BGW_OPT_K1_PATH
     int mtxel_lanes = 0;          // BGW_OPT_MTXEL_LANES
+    int mtxel_zy = 0;             // BGW_OPT_MTXEL_ZY
     int defer_k1 = 0;             // BGW_OPT_DEFER_K1
     int copy_ahead = 0;           // BGW_OPT_COPY_AHEAD
     cudaStream_t cst = nullptr;   // copy stream of copy-ahead host uploads
@@ -552,7 +553,8 @@ cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const in
     const int rec = c->stage_begin(1);
     cudaError_t e = (c->prec == BGW_FP64)
         ? bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, 0, 0, c->mtxel_lanes)
-        : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, tv, tc, c->mtxel_lanes);
+        : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, tv, tc, c->mtxel_lanes,
+                         c->mtxel_zy);
     c->stage_end(rec, 3);
     return e;
 }
@@ -899,7 +901,7 @@ bgw_status mtxel_into(bgw_ctx_s *c, const char *who, QState &s, int ik, int a0, 
             ? bgw::mtxel_f64(c->slot_ptr(sa, a0), c->slot_ptr(sb, b0), na, nb2, ax, gmap, s.ng, c->A.p, c->Bs.p, M,
                              s.ng, c->st, 0, 0, c->mtxel_lanes)
             : bgw::mtxel_f32(c->slot_ptr(sa, a0), c->slot_ptr(sb, b0), na, nb2, ax, gmap, s.ng, c->A.p, c->Bs.p, M,
-                             s.ng, c->st, 0, 0, c->mtxel_lanes);
+                             s.ng, c->st, 0, 0, c->mtxel_lanes, c->mtxel_zy);
     c->stage_end(rec, 3);
     if (e != cudaSuccess) return c->cuda_fail(e, "matrix-element kernels");
     return BGW_OK;
@@ -1457,6 +1459,10 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
             if (c->capturing) return c->fail(BGW_E_STATE, "set_option: overlap cannot change during a capture");
             c->overlap = (int)value;
             return BGW_OK;
+        case BGW_OPT_MTXEL_ZY:
+            if (value < 0 || value > 2) return c->fail(BGW_E_ARG, "set_option: matrix-element z+y kernel must be 0, 1 or 2");
+            c->mtxel_zy = (int)value;
+            return BGW_OK;
         case BGW_OPT_FP64_CONTRACTION:
             if (value != 0 && value != 1) return c->fail(BGW_E_ARG, "set_option: FP64 contraction must be 0 or 1");
             if (c->capturing) return c->fail(BGW_E_STATE, "set_option: contraction kernel cannot change during a capture");
@@ -1492,6 +1498,7 @@ bgw_status bgw_get_option(bgw_ctx c, int option, long *value) {
         case BGW_OPT_COPY_AHEAD: *value = c->copy_ahead; return BGW_OK;
         case BGW_OPT_OVERLAP: *value = c->overlap; return BGW_OK;
         case BGW_OPT_FP64_CONTRACTION: *value = c->f64_dfma; return BGW_OK;
+        case BGW_OPT_MTXEL_ZY: *value = c->mtxel_zy; return BGW_OK;
         default: return c->fail(BGW_E_ARG, "get_option: unknown option %d", option);
     }
 }

@@ -20,6 +20,8 @@
 // (f - s) mod N and the forward transform stores output f to slot
 // (f - s) mod N (see rot<N>).  Register indices stay compile-time.
 #pragma once
+#include <cuda_pipeline.h>
+
 #include <cmath>
 
 #include "bgw_bounds.cuh"
@@ -848,6 +850,116 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
     }
 }
 
+// Streamed form of the pair density + z + y passes (FP32, even N): one CTA
+// per (x-plane, group of up to SV valence bands, range of conduction bands).
+// The valence x-planes stay in shared memory for the whole item; the
+// conduction x-planes come in groups of SC bands through two buffers filled
+// by cp.async, so the copies of group g+1 run while group g is transformed.
+// After the z pass has read its conduction buffer (the kept outputs wait in
+// registers across a barrier), that buffer holds the z outputs for the y pass.
+// Shared: V[SV][2][N][RS], Cb[2][SC][2][N][RS]; Z[SV*SC][N][w2] inside Cb[g&1].
+constexpr int kStreamV = 4, kStreamC = 4, kStreamThreads = 512;
+
+template <int N>
+__host__ __device__ constexpr size_t stream_smem() {
+    return sizeof(cpx<float>) * (size_t)(kStreamV + 2 * kStreamC) * 2 * N * plane_row<N>();
+}
+
+template <int N>
+__global__ void __launch_bounds__(kStreamThreads, 1)
+k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int CC, int w1, int w2, int s1,
+             int s2, C *__restrict__ Bs) {
+    static_assert(N % 2 == 0, "16-byte copies need even rows");
+    extern __shared__ unsigned char smem_raw[];
+    constexpr int RS = plane_row<N>();
+    constexpr int PS = N * RS;                   // one spin component of a plane
+    constexpr int NN = N * N;
+    constexpr int CH = NN / 2;                   // 16-byte chunks per plane component
+    C *V = reinterpret_cast<C *>(smem_raw);
+    C *Cb0 = V + kStreamV * 2 * PS;
+    const int x = blockIdx.x, n0 = gridDim.x;
+    const int v0 = blockIdx.y * kStreamV, cbeg = blockIdx.z * CC;
+    const int tv = min(kStreamV, nv - v0), cend = min(nc, cbeg + CC);
+    const long vol = (long)n0 * NN;
+    const int ns1 = N - s1, ns2 = N - s2;
+    // copies of band planes (both spin components of x-plane x) into rows of RS
+    auto copy_planes = [&](C *dst, const C *src, long band0, int nb) {
+        const int total = nb * 2 * CH;
+        for (int i = threadIdx.x; i < total; i += kStreamThreads) {
+            const int ba = i / CH, ch = i % CH;           // ba = band * 2 + alpha
+            const int yz = 2 * ch;
+            const C *g = src + ((band0 + (ba >> 1)) * 2 + (ba & 1)) * vol + (long)x * NN + yz;
+            C *d = dst + ba * PS + (yz / N) * RS + (yz % N);
+            __pipeline_memcpy_async(d, g, 16);
+        }
+    };
+    copy_planes(V, Uv, v0, tv);
+    const int ng = (cend - cbeg + kStreamC - 1) / kStreamC;
+    if (ng > 0) copy_planes(Cb0, Uc, cbeg, min(kStreamC, cend - cbeg));
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+    __syncthreads();
+    for (int g = 0; g < ng; ++g) {
+        C *cur = Cb0 + (g & 1) * (kStreamC * 2 * PS);
+        const int c0 = cbeg + g * kStreamC;
+        const int tc = min(kStreamC, cend - c0);
+        if (g + 1 < ng) {
+            const int c1 = c0 + kStreamC;
+            copy_planes(Cb0 + ((g + 1) & 1) * (kStreamC * 2 * PS), Uc, c1, min(kStreamC, cend - c1));
+        }
+        __pipeline_commit();
+        // z lines: thread l = (pair, y), pair = v * tc + c
+        const int npair = tv * tc;
+        const int l = threadIdx.x;
+        const bool zl = l < npair * N;
+        const int pr = l / N, y = l % N;
+        C a[N];
+        if (zl) {
+            const int v = pr / tc, c = pr % tc;
+            const float4 *v4 = reinterpret_cast<const float4 *>(V + (v * 2) * PS + y * RS);
+            const float4 *c4 = reinterpret_cast<const float4 *>(cur + (c * 2) * PS + y * RS);
+            constexpr int P4 = PS / 2;
+#pragma unroll
+            for (int z = 0; z < N / 2; ++z) {
+                const float4 va = v4[z], vb = v4[P4 + z], ca = c4[z], cb = c4[P4 + z];
+                a[2 * z] = rho2(C{va.x, va.y}, C{ca.x, ca.y}, C{vb.x, vb.y}, C{cb.x, cb.y});
+                a[2 * z + 1] = rho2(C{va.z, va.w}, C{ca.z, ca.w}, C{vb.z, vb.w}, C{cb.z, cb.w});
+            }
+            fft_line<T, -1, N>(a);
+        }
+        __syncthreads();                 // every z line has read `cur`: it now holds Z
+        C *Z = cur;
+        if (zl) {
+            C *zo = Z + ((long)pr * N + y) * w2;
+#pragma unroll
+            for (int f = 0; f < N; ++f) {
+                const int j = rot<N>(f, ns2);
+                if (j < w2) zo[j] = a[f];
+            }
+        }
+        __syncthreads();
+        // y lines over the kept z outputs; keep w1 outputs -> Bs[p][x][jy][jz]
+        for (int t = threadIdx.x; t < npair * w2; t += kStreamThreads) {
+            const int q = t / w2, jz = t % w2;
+            const int v = q / tc, c = q % tc;
+            const C *zi = Z + (long)q * N * w2 + jz;
+            C b[N];
+#pragma unroll
+            for (int yy = 0; yy < N; ++yy) b[yy] = zi[yy * w2];
+            fft_line<T, -1, N>(b);
+            const long p = (long)(v0 + v) * nc + (c0 + c);
+            C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
+#pragma unroll
+            for (int f = 0; f < N; ++f) {
+                const int j = rot<N>(f, ns1);
+                if (j < w1) bo[j * w2] = b[f];
+            }
+        }
+        __pipeline_wait_prior(0);        // group g+1 has landed
+        __syncthreads();                 // and every y line has read Z
+    }
+}
+
 // Sphere -> grid y and z passes for one x-plane of TB band components:
 // S[b][x][w1][w2] -> U[b][x][N][N].  Shared: in[TB][w1][w2], P[TB][N][w2+1],
 // out[TB][N][N+1].
@@ -1184,9 +1296,55 @@ static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int 
     return n;
 }
 
+// The x pass of the one-lane-per-line paths: gather through shared memory
+// when the kept cube is small, else scatter through the inverse map.
+static cudaError_t xpass(const C *Bp, long P, const Axes &a, const int *gmap, int ng, C *Mp, long ldm,
+                         cudaStream_t st) {
+    const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
+    const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
+    cudaError_t e = cudaSuccess;
+    if (mtxel_scatter_mode(a, sizeof(C))) {
+        const long lines = (long)a.w[1] * a.w[2];
+        BGW_FOR_EACH_LEN(a.n[0], (k2_xpass_scatter<N><<<blocks_for(P * lines), kLineThreads, 0, st>>>(
+                                     Bp, P, a.w[0], a.w[1], a.w[2], a.s[0], gmap + ng, scale, Mp, ldm)));
+        return cudaGetLastError();
+    }
+    BGW_FOR_EACH_LEN(a.n[0], {
+        const int PP = gather_pairs(a, P);
+        if (smem * PP > 48 * 1024) {
+            e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(smem * PP));
+            if (e != cudaSuccess) return e;
+        }
+        k2_xpass_gather<N><<<(unsigned)((P + PP - 1) / PP), kGatherThreads, smem * PP, st>>>(
+            Bp, P, PP, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
+    });
+    return cudaGetLastError();
+}
+
+// The streamed z + y kernel applies to FP32 boxes of the plane kernels with an
+// even N <= 32 whose kept z outputs of 16 pairs fit in one conduction buffer.
+#define BGW_FOR_EACH_STREAM_LEN(n, ...)                                                \
+    switch (n) {                                                                       \
+        case 16: { constexpr int N = 16; __VA_ARGS__; } break;                         \
+        case 18: { constexpr int N = 18; __VA_ARGS__; } break;                         \
+        case 20: { constexpr int N = 20; __VA_ARGS__; } break;                         \
+        case 24: { constexpr int N = 24; __VA_ARGS__; } break;                         \
+        case 30: { constexpr int N = 30; __VA_ARGS__; } break;                         \
+        case 32: { constexpr int N = 32; __VA_ARGS__; } break;                         \
+        default: return cudaErrorInvalidValue;                                         \
+    }
+
+static bool use_stream(const Axes &a) {
+    const int n = a.n[1];
+    if (!use_plane_kernels(a) || n % 2 != 0 || n > 32 || n == 28 || n == 26 || n == 22) return false;
+    const int rs = n + 2;
+    return a.w[2] * kStreamV <= 2 * rs;
+}
+
 static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const Axes &a,
                                const int *gmap, int ng, C *Ap, C *Bp, C *Mp, long ldm,
-                               cudaStream_t st, int tv_req, int tc_req, int lanes) {
+                               cudaStream_t st, int tv_req, int tc_req, int lanes, int zy) {
     const long P = (long)nv * nc;
     if (oct_len(a) && (lanes == 8 || (lanes == 0 && use_coop(a) && use_oct(a)))) {
         // eight lanes per line: fused z+y, then the x pass
@@ -1222,6 +1380,35 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
                 Bp, P, PP, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
         });
         return cudaGetLastError();
+    }
+    if (zy != 1 && use_stream(a)) {
+        // streamed pair density + z + y: conduction ranges sized for about four
+        // waves of one CTA per SM
+        const int nvg = (nv + kStreamV - 1) / kStreamV;
+        static int sms = 0;
+        if (sms == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+                sms = 148;
+        }
+        const long want = 4L * sms;
+        const long per = (long)a.n[0] * nvg;
+        const int chunks = (int)((want + per - 1) / per);
+        int CC = (nc + chunks - 1) / chunks;
+        CC = (CC + kStreamC - 1) / kStreamC * kStreamC;
+        if (CC < kStreamC) CC = kStreamC;
+        dim3 grid((unsigned)a.n[0], (unsigned)nvg, (unsigned)((nc + CC - 1) / CC));
+        cudaError_t e = cudaSuccess;
+        BGW_FOR_EACH_STREAM_LEN(a.n[1], {
+            const size_t ss = stream_smem<N>();
+            e = cudaFuncSetAttribute(k2_zy_stream<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+            if (e != cudaSuccess) return e;
+            k2_zy_stream<N><<<grid, kStreamThreads, ss, st>>>(uv, uc, nv, nc, CC, a.w[1], a.w[2], a.s[1], a.s[2], Bp);
+        });
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return xpass(Bp, P, a, gmap, ng, Mp, ldm, st);
     }
     int TV = 0, TC = 0;
     if (use_plane_kernels(a)) {
@@ -1271,31 +1458,12 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         BGW_FOR_EACH_LEN(a.n[1], (k2_ypass<N><<<blocks_for(npx * a.w[2]), kLineThreads, 0, st>>>(
                                      Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
     }
-    const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
-    const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
-    cudaError_t e = cudaSuccess;
-    if (mtxel_scatter_mode(a, sizeof(C))) {
-        const long lines = (long)a.w[1] * a.w[2];
-        BGW_FOR_EACH_LEN(a.n[0], (k2_xpass_scatter<N><<<blocks_for(P * lines), kLineThreads, 0, st>>>(
-                                     Bp, P, a.w[0], a.w[1], a.w[2], a.s[0], gmap + ng, scale, Mp, ldm)));
-        return cudaGetLastError();
-    }
-    BGW_FOR_EACH_LEN(a.n[0], {
-        const int PP = gather_pairs(a, P);
-        if (smem * PP > 48 * 1024) {
-            e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(smem * PP));
-            if (e != cudaSuccess) return e;
-        }
-        k2_xpass_gather<N><<<(unsigned)((P + PP - 1) / PP), kGatherThreads, smem * PP, st>>>(
-            Bp, P, PP, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
-    });
-    return cudaGetLastError();
+    return xpass(Bp, P, a, gmap, ng, Mp, ldm, st);
 }
 
 static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                          const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                         cudaStream_t st, int tv_req, int tc_req, int lanes) {
+                         cudaStream_t st, int tv_req, int tc_req, int lanes, int zy) {
     if ((long)nv * nc == 0) return cudaSuccess;
     const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
     C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
@@ -1304,7 +1472,7 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
     for (int vb0 = 0; vb0 < nv; vb0 += VB) {
         const int nvb = nv - vb0 < VB ? nv - vb0 : VB;
         cudaError_t e = mtxel_batch(uv + (long)vb0 * 2 * vol, uc, nvb, nc, a, gmap, ng, Ap, Bp,
-                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req, lanes);
+                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req, lanes, zy);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1313,6 +1481,7 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
 #undef BGW_FOR_EACH_LEN
 #undef BGW_FOR_EACH_COOP_LEN
 #undef BGW_FOR_EACH_OCT_LEN
+#undef BGW_FOR_EACH_STREAM_LEN
 
 }  // namespace BGW_SUFFIX
 }  // namespace bgw

@@ -62,12 +62,14 @@ cudaError_t wfn_to_grid_batch_f32(const K1Job *jobs, int n, int B, cudaStream_t 
 // N = 32, 40, 48 or 64 (automatic choice uses them for 48 and 64 only).
 // Pairs are processed in batches of mtxel_v_batch(...) valence bands x nc, so
 // A and Bs need room for that many pairs only.
+// zy (FP32): 0 automatic (the streamed z + y kernel where it applies), 1 the
+// plane kernel with the pair tile tv x tc, 2 streamed where it applies.
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0);
+                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0);
 cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0);
+                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0);
 // The last forward pass gathers the kept w0*w1*w2 cube through shared memory
 // when it is small; a larger cube is written straight to M through an
 // inverse map (cube cell -> G index or -1) stored in the map buffer right

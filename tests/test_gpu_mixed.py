@@ -88,3 +88,22 @@ def test_chi0_mixed_si24_k_subset(gpu_lib):
     got = ctx.finalize()
     ctx.close()
     assert rel_fro(got, ref) <= TOL_CHI_MIXED
+
+
+@pytest.mark.parametrize("zy", [1, 2])
+@pytest.mark.parametrize("over", [{}, dict(box=(24, 24, 24), nv=9, nc=30, ng=113, nfreq=2),
+                                  dict(box=(32, 32, 32), nv=5, nc=13, ng=181, nfreq=2)])
+def test_both_zy_kernels_match_oracle(gpu_lib, zy, over):
+    """The FP32 pair density + z + y passes as the plane kernel (pair tiles)
+    and as the streamed kernel (resident valence planes, conduction planes in
+    double-buffered groups of four; ragged last groups here) against the
+    oracle."""
+    p = syn.make_problem("si18_qx", **over)
+    ref = oracle.chi0(p)
+    ctx = gpu_lib.Chi0Context(p, "mixed")
+    gpu_lib.bgw_set_option(ctx.ctx, gpu_lib.BGW_OPT_MTXEL_ZY, zy)
+    ctx.upload()
+    ctx.accumulate()
+    got = ctx.finalize()
+    ctx.close()
+    assert rel_fro(got, ref) <= TOL_CHI_MIXED
