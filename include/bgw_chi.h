@@ -337,7 +337,8 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *   BGW_OPT_MTXEL_ZY     pair density + z and y passes of the FP32 matrix-
  *                        element kernels on boxes with N2 = N3 <= 40: 0
  *                        automatic (default: the streamed kernel where it
- *                        applies, even N2 <= 32), 1 the plane kernel with the
+ *                        applies, even N2 <= 32, unless a pair tile is set),
+ *                        1 the plane kernel with the
  *                        pair tile of BGW_OPT_PAIR_TILE_V/C (or the autotuner's),
  *                        2 the streamed kernel where it applies: a CTA keeps
  *                        four valence x-planes in shared memory and streams the
@@ -416,13 +417,16 @@ BGW_API bgw_status bgw_set_option(bgw_ctx ctx, int option, long value);
 BGW_API bgw_status bgw_get_option(bgw_ctx ctx, int option, long *value);
 
 /*
- * Autotuner: times candidate pair tiles and k-chunks on k-points
- * k_begin..k_end-1 of the given q-set and frequencies (CUDA events on the
- * context stream, one warm-up and one timed run each) and sets the fastest.
+ * Autotuner: times the candidate matrix-element kernels (mixed precision:
+ * the streamed z + y kernel and the plane kernel's best pair tiles) and then
+ * the k-chunks on k-points k_begin..k_end-1 of the given q-set and frequencies
+ * (CUDA events on the context stream, one warm-up and the median of three
+ * timed runs each) and sets the fastest (BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V/C,
+ * BGW_OPT_MTXEL_ZY).
  * The running chi0 sums are not touched.  Chunks whose M block and split
  * operands would exceed 2 GiB are not tried.  cache_path (may
- * be NULL): a text file of "key|kchunk tile_v tile_c" lines; a hit skips the
- * timing, a miss appends the result.  Blocks until done.
+ * be NULL): a text file of "key|kchunk tile_v tile_c zy" lines; a hit skips
+ * the timing, a miss appends the result.  Blocks until done.
  */
 BGW_API bgw_status bgw_autotune(bgw_ctx ctx, int nq, const bgw_q *qs, int nfreq,
                                 const double *freq_eV, int k_begin, int k_end,

@@ -395,7 +395,8 @@ def bgw_autotune(ctx, qs, freq, k_begin: int, k_end: int, cache_path=None) -> di
     cp = cache_path.encode() if cache_path else None
     _check(_lib.bgw_autotune(ctx, len(structs), arr, len(f), _host_ptr(f), k_begin, k_end, cp), ctx)
     return {"kchunk": bgw_get_option(ctx, BGW_OPT_KCHUNK),
-            "pair_tile": (bgw_get_option(ctx, BGW_OPT_PAIR_TILE_V), bgw_get_option(ctx, BGW_OPT_PAIR_TILE_C))}
+            "pair_tile": (bgw_get_option(ctx, BGW_OPT_PAIR_TILE_V), bgw_get_option(ctx, BGW_OPT_PAIR_TILE_C)),
+            "mtxel_zy": bgw_get_option(ctx, BGW_OPT_MTXEL_ZY)}
 
 
 def bgw_graph_begin(ctx) -> int:

@@ -1524,11 +1524,13 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
             while (fgets(line, sizeof line, f)) {
                 const char *bar = strchr(line, '|');
                 if (!bar || std::string(line, bar - line) != key) continue;
-                int kc, tv, tcc;
-                if (sscanf(bar + 1, "%d %d %d", &kc, &tv, &tcc) == 3) {
+                int kc, tv, tcc, zy = 0;
+                const int got = sscanf(bar + 1, "%d %d %d %d", &kc, &tv, &tcc, &zy);
+                if (got >= 3) {
                     c->kchunk = kc;
                     c->tile_v = tv;
                     c->tile_c = tcc;
+                    if (got == 4) c->mtxel_zy = zy;
                     fclose(f);
                     return BGW_OK;
                 }
@@ -1559,39 +1561,53 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     long Pmax = 0;
     for (auto &s : tq) Pmax = std::max(Pmax, (long)c->nv * s.nc);
+    // one warm-up run, then the median of three timed runs
     auto time_one = [&](int kc, int tv, int tcc, float &ms) -> cudaError_t {
         cudaError_t r = ensure_chunk_scratch(c, tq, nfreq, kc);
         bool clean = true;
         const double *fq = static_cast<const double *>(tfreq.p);
         if (r == cudaSuccess) r = run_range(c, tq, nfreq, fq, k_begin, k_end, kc, tv, tcc, clean);   // warm
-        if (r == cudaSuccess) r = cudaEventRecord(e0, c->st);
-        if (r == cudaSuccess) r = run_range(c, tq, nfreq, fq, k_begin, k_end, kc, tv, tcc, clean);
-        if (r == cudaSuccess) r = cudaEventRecord(e1, c->st);
-        if (r == cudaSuccess) r = cudaEventSynchronize(e1);
-        if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+        float t[3] = {0, 0, 0};
+        for (int i = 0; i < 3 && r == cudaSuccess; ++i) {
+            r = cudaEventRecord(e0, c->st);
+            if (r == cudaSuccess) r = run_range(c, tq, nfreq, fq, k_begin, k_end, kc, tv, tcc, clean);
+            if (r == cudaSuccess) r = cudaEventRecord(e1, c->st);
+            if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+            if (r == cudaSuccess) r = cudaEventElapsedTime(&t[i], e0, e1);
+        }
+        std::sort(t, t + 3);
+        ms = t[1];
         return r;
     };
-    int best_kc = c->kchunk, best_tv = c->tile_v, best_tc = c->tile_c;
+    const int zy_in = c->mtxel_zy;
+    int best_kc = c->kchunk, best_tv = c->tile_v, best_tc = c->tile_c, best_zy = zy_in;
     float best_ms = 1e30f;
     if (e == cudaSuccess) {
-        // pair tile first (FP32 plane kernel), at k-chunk 1
-        int tvs[8] = {0}, tcs[8] = {0};
+        // matrix-element kernel first (FP32: the streamed z + y kernel and the
+        // plane kernel's best pair tiles), at k-chunk 1
+        int tvs[8] = {0}, tcs[8] = {0}, zys[8] = {zy_in};
         int ncand = 1;
         if (c->prec != BGW_FP64) {
             const int zero3[3] = {0, 0, 0};
             bgw::Axes ax = mtxel_axes(c, tq[0], zero3);
-            ncand += bgw::plane_tile_candidates(c->nv, tq[0].nc, ax, tvs + 1, tcs + 1, 4);
+            zys[0] = 2;
+            const int nt = bgw::plane_tile_candidates(c->nv, tq[0].nc, ax, tvs + 1, tcs + 1, 4);
+            for (int i = 1; i <= nt; ++i) zys[i] = 1;
+            ncand += nt;
         }
         for (int i = 0; i < ncand && e == cudaSuccess; ++i) {
             float ms = 0;
+            c->mtxel_zy = zys[i];
             e = time_one(1, tvs[i], tcs[i], ms);
             if (e == cudaSuccess && ms < best_ms) {
                 best_ms = ms;
                 best_tv = tvs[i];
                 best_tc = tcs[i];
+                best_zy = zys[i];
                 best_kc = 1;
             }
         }
+        c->mtxel_zy = best_zy;
         // then the k-chunk, within a workspace cap (the split operands of the
         // mixed path grow with the chunk)
         const int kcands[] = {2, 4, 8, 16, 32, 64};
@@ -1624,13 +1640,17 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
         s.acc.release();
     }
     c->prof = prof;
-    if (e != cudaSuccess) return c->cuda_fail(e, "autotune");
+    if (e != cudaSuccess) {
+        c->mtxel_zy = zy_in;
+        return c->cuda_fail(e, "autotune");
+    }
     c->kchunk = best_kc;
     c->tile_v = best_tv;
     c->tile_c = best_tc;
+    c->mtxel_zy = best_zy;
     if (cache_path) {
         if (FILE *f = fopen(cache_path, "a")) {
-            fprintf(f, "%s|%d %d %d\n", key.c_str(), best_kc, best_tv, best_tc);
+            fprintf(f, "%s|%d %d %d %d\n", key.c_str(), best_kc, best_tv, best_tc, best_zy);
             fclose(f);
         }
     }

@@ -850,33 +850,49 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
     }
 }
 
-// Streamed form of the pair density + z + y passes (FP32, even N): one CTA
-// per (x-plane, group of up to SV valence bands, range of conduction bands).
-// The valence x-planes stay in shared memory for the whole item; the
+// Streamed form of the pair density + z + y passes (FP32, even N <= 32): one
+// CTA per (x-plane, group of up to SV valence bands, range of conduction
+// bands).  The valence x-planes stay in shared memory for the whole item; the
 // conduction x-planes come in groups of SC bands through two buffers filled
-// by cp.async, so the copies of group g+1 run while group g is transformed.
-// After the z pass has read its conduction buffer (the kept outputs wait in
-// registers across a barrier), that buffer holds the z outputs for the y pass.
-// Shared: V[SV][2][N][RS], Cb[2][SC][2][N][RS]; Z[SV*SC][N][w2] inside Cb[g&1].
-constexpr int kStreamV = 4, kStreamC = 4, kStreamThreads = 512;
+// by cp.async.  Each phase k, after which the CTA synchronises once:
+//   threads 0..kZThreads-1  z lines of group k (pair density, FFT, kept outputs
+//                           into Z[k & 1]),
+//   the other threads       y lines of group k - 1 (from Z[(k - 1) & 1] to Bs),
+//   copies                  of group k + 1 into the buffer group k - 1 used,
+// so copies, z lines and y lines of consecutive groups run together.
+// Shared: V[SV][2][N][RS], Cb[2][SC][2][N][RS], Z[2][SV*SC][N][kZW].
+constexpr int kZThreads = 256, kYThreads = 128, kStreamThreads = kZThreads + kYThreads;
+constexpr int kZW = 17;   // largest kept z width the Z buffers hold
+
+// Valence and conduction group sizes per box length: as many z lines
+// (SV * SC * N) as z threads, or nearly.
+template <int N>
+struct StreamTile {
+    static constexpr int V = N == 24 ? 5 : 4;
+    static constexpr int C = N >= 24 ? 2 : (N >= 18 ? 3 : 4);
+};
 
 template <int N>
 __host__ __device__ constexpr size_t stream_smem() {
-    return sizeof(cpx<float>) * (size_t)(kStreamV + 2 * kStreamC) * 2 * N * plane_row<N>();
+    constexpr int SV = StreamTile<N>::V, SC = StreamTile<N>::C;
+    return sizeof(cpx<float>) * ((size_t)(SV + 2 * SC) * 2 * N * plane_row<N>() + (size_t)2 * SV * SC * N * kZW);
 }
 
 template <int N>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int CC, int w1, int w2, int s1,
              int s2, C *__restrict__ Bs) {
-    static_assert(N % 2 == 0, "16-byte copies need even rows");
+    constexpr int kStreamV = StreamTile<N>::V, kStreamC = StreamTile<N>::C;
+    static_assert(N % 2 == 0 && kStreamV * kStreamC * N <= kZThreads, "one z line per z thread");
     extern __shared__ unsigned char smem_raw[];
     constexpr int RS = plane_row<N>();
     constexpr int PS = N * RS;                   // one spin component of a plane
     constexpr int NN = N * N;
     constexpr int CH = NN / 2;                   // 16-byte chunks per plane component
+    constexpr int ZS = kStreamV * kStreamC * N * kZW;
     C *V = reinterpret_cast<C *>(smem_raw);
     C *Cb0 = V + kStreamV * 2 * PS;
+    C *Z0 = Cb0 + 2 * kStreamC * 2 * PS;
     const int x = blockIdx.x, n0 = gridDim.x;
     const int v0 = blockIdx.y * kStreamV, cbeg = blockIdx.z * CC;
     const int tv = min(kStreamV, nv - v0), cend = min(nc, cbeg + CC);
@@ -893,70 +909,68 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
             __pipeline_memcpy_async(d, g, 16);
         }
     };
-    copy_planes(V, Uv, v0, tv);
     const int ng = (cend - cbeg + kStreamC - 1) / kStreamC;
+    copy_planes(V, Uv, v0, tv);
     if (ng > 0) copy_planes(Cb0, Uc, cbeg, min(kStreamC, cend - cbeg));
     __pipeline_commit();
     __pipeline_wait_prior(0);
     __syncthreads();
-    for (int g = 0; g < ng; ++g) {
-        C *cur = Cb0 + (g & 1) * (kStreamC * 2 * PS);
-        const int c0 = cbeg + g * kStreamC;
-        const int tc = min(kStreamC, cend - c0);
-        if (g + 1 < ng) {
-            const int c1 = c0 + kStreamC;
-            copy_planes(Cb0 + ((g + 1) & 1) * (kStreamC * 2 * PS), Uc, c1, min(kStreamC, cend - c1));
+    for (int k = 0; k <= ng; ++k) {
+        if (k + 1 < ng) {
+            const int c1 = cbeg + (k + 1) * kStreamC;
+            copy_planes(Cb0 + ((k + 1) & 1) * (kStreamC * 2 * PS), Uc, c1, min(kStreamC, cend - c1));
         }
         __pipeline_commit();
-        // z lines: thread l = (pair, y), pair = v * tc + c
-        const int npair = tv * tc;
-        const int l = threadIdx.x;
-        const bool zl = l < npair * N;
-        const int pr = l / N, y = l % N;
-        C a[N];
-        if (zl) {
-            const int v = pr / tc, c = pr % tc;
-            const float4 *v4 = reinterpret_cast<const float4 *>(V + (v * 2) * PS + y * RS);
-            const float4 *c4 = reinterpret_cast<const float4 *>(cur + (c * 2) * PS + y * RS);
-            constexpr int P4 = PS / 2;
+        if (threadIdx.x < kZThreads) {
+            // z line (pair, y) of group k, pair = v * tc + c
+            const int tc = k < ng ? min(kStreamC, cend - (cbeg + k * kStreamC)) : 0;
+            const int l = threadIdx.x;
+            if (l < tv * tc * N) {
+                const int pr = l / N, y = l % N;
+                const int v = pr / tc, c = pr % tc;
+                const C *cur = Cb0 + (k & 1) * (kStreamC * 2 * PS);
+                const float4 *v4 = reinterpret_cast<const float4 *>(V + (v * 2) * PS + y * RS);
+                const float4 *c4 = reinterpret_cast<const float4 *>(cur + (c * 2) * PS + y * RS);
+                constexpr int P4 = PS / 2;
+                C a[N];
 #pragma unroll
-            for (int z = 0; z < N / 2; ++z) {
-                const float4 va = v4[z], vb = v4[P4 + z], ca = c4[z], cb = c4[P4 + z];
-                a[2 * z] = rho2(C{va.x, va.y}, C{ca.x, ca.y}, C{vb.x, vb.y}, C{cb.x, cb.y});
-                a[2 * z + 1] = rho2(C{va.z, va.w}, C{ca.z, ca.w}, C{vb.z, vb.w}, C{cb.z, cb.w});
+                for (int z = 0; z < N / 2; ++z) {
+                    const float4 va = v4[z], vb = v4[P4 + z], ca = c4[z], cb = c4[P4 + z];
+                    a[2 * z] = rho2(C{va.x, va.y}, C{ca.x, ca.y}, C{vb.x, vb.y}, C{cb.x, cb.y});
+                    a[2 * z + 1] = rho2(C{va.z, va.w}, C{ca.z, ca.w}, C{vb.z, vb.w}, C{cb.z, cb.w});
+                }
+                fft_line<T, -1, N>(a);
+                C *zo = Z0 + (k & 1) * ZS + ((long)pr * N + y) * w2;
+#pragma unroll
+                for (int f = 0; f < N; ++f) {
+                    const int j = rot<N>(f, ns2);
+                    if (j < w2) zo[j] = a[f];
+                }
             }
-            fft_line<T, -1, N>(a);
-        }
-        __syncthreads();                 // every z line has read `cur`: it now holds Z
-        C *Z = cur;
-        if (zl) {
-            C *zo = Z + ((long)pr * N + y) * w2;
+        } else if (k >= 1) {
+            // y lines of group k - 1; keep w1 outputs -> Bs[p][x][jy][jz]
+            const int c0 = cbeg + (k - 1) * kStreamC;
+            const int tc = min(kStreamC, cend - c0);
+            const C *Z = Z0 + ((k - 1) & 1) * ZS;
+            for (int t = threadIdx.x - kZThreads; t < tv * tc * w2; t += kYThreads) {
+                const int q = t / w2, jz = t % w2;
+                const int v = q / tc, c = q % tc;
+                const C *zi = Z + (long)q * N * w2 + jz;
+                C b[N];
 #pragma unroll
-            for (int f = 0; f < N; ++f) {
-                const int j = rot<N>(f, ns2);
-                if (j < w2) zo[j] = a[f];
+                for (int yy = 0; yy < N; ++yy) b[yy] = zi[yy * w2];
+                fft_line<T, -1, N>(b);
+                const long p = (long)(v0 + v) * nc + (c0 + c);
+                C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
+#pragma unroll
+                for (int f = 0; f < N; ++f) {
+                    const int j = rot<N>(f, ns1);
+                    if (j < w1) bo[j * w2] = b[f];
+                }
             }
         }
-        __syncthreads();
-        // y lines over the kept z outputs; keep w1 outputs -> Bs[p][x][jy][jz]
-        for (int t = threadIdx.x; t < npair * w2; t += kStreamThreads) {
-            const int q = t / w2, jz = t % w2;
-            const int v = q / tc, c = q % tc;
-            const C *zi = Z + (long)q * N * w2 + jz;
-            C b[N];
-#pragma unroll
-            for (int yy = 0; yy < N; ++yy) b[yy] = zi[yy * w2];
-            fft_line<T, -1, N>(b);
-            const long p = (long)(v0 + v) * nc + (c0 + c);
-            C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
-#pragma unroll
-            for (int f = 0; f < N; ++f) {
-                const int j = rot<N>(f, ns1);
-                if (j < w1) bo[j * w2] = b[f];
-            }
-        }
-        __pipeline_wait_prior(0);        // group g+1 has landed
-        __syncthreads();                 // and every y line has read Z
+        __pipeline_wait_prior(0);        // group k + 1 has landed
+        __syncthreads();                 // Z[k & 1] written, Z[(k - 1) & 1] and Cb[k & 1] read
     }
 }
 
@@ -1338,8 +1352,7 @@ static cudaError_t xpass(const C *Bp, long P, const Axes &a, const int *gmap, in
 static bool use_stream(const Axes &a) {
     const int n = a.n[1];
     if (!use_plane_kernels(a) || n % 2 != 0 || n > 32 || n == 28 || n == 26 || n == 22) return false;
-    const int rs = n + 2;
-    return a.w[2] * kStreamV <= 2 * rs;
+    return a.w[2] <= kZW;
 }
 
 static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const Axes &a,
@@ -1381,9 +1394,14 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         });
         return cudaGetLastError();
     }
-    if (zy != 1 && use_stream(a)) {
+    if ((zy == 2 || (zy == 0 && tv_req <= 0)) && use_stream(a)) {
         // streamed pair density + z + y: conduction ranges sized for about four
         // waves of one CTA per SM
+        int kStreamV = 4, kStreamC = 2;
+        BGW_FOR_EACH_STREAM_LEN(a.n[1], {
+            kStreamV = StreamTile<N>::V;
+            kStreamC = StreamTile<N>::C;
+        });
         const int nvg = (nv + kStreamV - 1) / kStreamV;
         static int sms = 0;
         if (sms == 0) {

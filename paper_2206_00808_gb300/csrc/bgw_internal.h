@@ -62,8 +62,9 @@ cudaError_t wfn_to_grid_batch_f32(const K1Job *jobs, int n, int B, cudaStream_t 
 // N = 32, 40, 48 or 64 (automatic choice uses them for 48 and 64 only).
 // Pairs are processed in batches of mtxel_v_batch(...) valence bands x nc, so
 // A and Bs need room for that many pairs only.
-// zy (FP32): 0 automatic (the streamed z + y kernel where it applies), 1 the
-// plane kernel with the pair tile tv x tc, 2 streamed where it applies.
+// zy (FP32): 0 automatic (the streamed z + y kernel where it applies, unless a
+// pair tile tv x tc is given), 1 the plane kernel with the pair tile tv x tc,
+// 2 streamed where it applies.
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
                       cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0);

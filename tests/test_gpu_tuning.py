@@ -54,7 +54,7 @@ def test_kchunk_aligned_splits_are_bitwise_identical(gpu_lib, case, prec):
 @pytest.mark.parametrize("tile", [(1, 1), (2, 3), (8, 2), (2, 2), (8, 8)])
 def test_pair_tiles_give_identical_results(gpu_lib, case, tile):
     p, _ = case
-    auto = run(gpu_lib, p, "mixed")
+    auto = run(gpu_lib, p, "mixed", [(gpu_lib.BGW_OPT_MTXEL_ZY, 1)])      # plane kernel, automatic tile
     got = run(gpu_lib, p, "mixed", [(gpu_lib.BGW_OPT_PAIR_TILE_V, tile[0]),
                                     (gpu_lib.BGW_OPT_PAIR_TILE_C, tile[1])])
     assert np.array_equal(got, auto)
@@ -68,7 +68,7 @@ def test_autotune_keeps_results_and_uses_cache(gpu_lib, case, tmp_path):
         ctx.upload()
         ctx.accumulate(0, 3)                     # a running sum the autotuner must not touch
         choice = ctx.autotune(cache_path=cache)
-        assert choice["kchunk"] >= 1
+        assert choice["kchunk"] >= 1 and choice["mtxel_zy"] in (0, 1, 2)
         ctx.accumulate(3, 8)                     # the sum continues with the tuned settings
         got = ctx.finalize()
         ctx.close()
