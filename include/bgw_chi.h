@@ -320,7 +320,10 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        alive and unchanged until the k-point is uploaded
  *                        again or the context is destroyed.
  *   BGW_OPT_K1_PATH      kernels of the sphere -> real-space transform of
- *                        bgw_wfn_upload: 0 automatic (default), 1 one kernel
+ *                        bgw_wfn_upload: 0 automatic (default: the one-kernel
+ *                        transform where it fits, else eight lanes per line on
+ *                        cubic boxes of 32, 40 (FP32), 48 and 64, else one
+ *                        kernel per axis), 1 one kernel
  *                        per axis, 2 one kernel for the whole transform of a
  *                        band component where the box fits in shared memory
  *                        (else as 1), 3 eight lanes per FFT line where the box
@@ -360,10 +363,12 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        are built on demand already.  Same grids, bitwise.
  *   BGW_OPT_COPY_AHEAD   0 (default): a host upload (on_device = 0) copies
  *                        the coefficients on the context stream, after the
- *                        work queued there before it.  1: the copy runs on a
- *                        second stream of the context into a device buffer of
- *                        the k-point's own, so the copies of later k-points
- *                        overlap the transforms of earlier ones; work queued
+ *                        work queued there before it.  1: the copy runs on
+ *                        one of four copy streams of the context (k-point ik
+ *                        on stream ik mod 4, so several copy engines share the
+ *                        transfer) into a device buffer of the k-point's own,
+ *                        so the copies of later k-points overlap the
+ *                        transforms of earlier ones; work queued
  *                        on the context stream after the call still waits for
  *                        the copy.  The host buffer must hold its data when
  *                        the call is made (the copy is not ordered after

@@ -87,10 +87,12 @@ struct KPoint {
     const double *coeff_src = nullptr;          // streaming mode: coefficients the grid is built from
     int slot = -1;                              // grid slot holding this k (-1: none)
     const double *pending = nullptr;            // BGW_OPT_DEFER_K1: grid not built yet, from these
-    // BGW_OPT_COPY_AHEAD: `coeff` is written on the copy stream; `copied`
-    // marks that copy complete, `consumed` the last transform that read it
+    // BGW_OPT_COPY_AHEAD: `coeff` is written on a copy stream; `copied`
+    // marks that copy complete, `consumed` the last transform that read it;
+    // copy_wait: a deferred build must make the context stream wait for it
     cudaEvent_t copied = nullptr, consumed = nullptr;
     bool consumed_set = false;
+    bool copy_wait = false;
 };
 
 struct QState {
@@ -191,7 +193,8 @@ struct bgw_ctx_s {
     int mtxel_zy = 0;             // BGW_OPT_MTXEL_ZY
     int defer_k1 = 0;             // BGW_OPT_DEFER_K1
     int copy_ahead = 0;           // BGW_OPT_COPY_AHEAD
-    cudaStream_t cst = nullptr;   // copy stream of copy-ahead host uploads
+    static constexpr int kCopyStreams = 4;
+    cudaStream_t cst[kCopyStreams] = {};   // copy streams of copy-ahead host uploads (k-point ik uses ik % 4)
     int overlap = 0;              // BGW_OPT_OVERLAP
     int f64_dfma = 0;             // BGW_OPT_FP64_CONTRACTION: 1 = FP64 FMA kernel, 0 = digit slices on tcgen05
     cudaStream_t gst = nullptr;   // contraction stream of the overlapped mixed path
@@ -361,7 +364,8 @@ bool st_capturing(const bgw_ctx_s *c) {
 // Copy-ahead host uploads: the copy stream and the k-point's two events.
 cudaError_t ensure_copy_events(bgw_ctx_s *c, KPoint &kp) {
     cudaError_t e = cudaSuccess;
-    if (!c->cst) e = cudaStreamCreateWithFlags(&c->cst, cudaStreamNonBlocking);
+    for (int i = 0; i < bgw_ctx_s::kCopyStreams && e == cudaSuccess; ++i)
+        if (!c->cst[i]) e = cudaStreamCreateWithFlags(&c->cst[i], cudaStreamNonBlocking);
     if (e == cudaSuccess && !kp.copied) e = cudaEventCreateWithFlags(&kp.copied, cudaEventDisableTiming);
     if (e == cudaSuccess && !kp.consumed) e = cudaEventCreateWithFlags(&kp.consumed, cudaEventDisableTiming);
     return e;
@@ -401,6 +405,13 @@ cudaError_t flush_k1(bgw_ctx_s *c) {
         jobs.push_back(j);
         ks.push_back(ik);
     }
+    // copy-ahead uploads of these k-points: the builds wait for their copies
+    for (int ik : ks) {
+        KPoint &kp = c->k[ik];
+        if (kp.copy_wait && e == cudaSuccess) e = cudaStreamWaitEvent(c->st, kp.copied, 0);
+        kp.copy_wait = false;
+    }
+    if (e != cudaSuccess) return e;
     bool batched = false;
     if (c->k1_path == 0) {
         const int rec = c->stage_begin(0);
@@ -1132,13 +1143,19 @@ bgw_status bgw_wfn_upload(bgw_ctx c, int ik, int ngw, const int *gvec, const dou
             e = cudaEventRecord(kp.consumed, c->st);
             kp.consumed_set = true;
         }
-        if (e == cudaSuccess && cbytes > kp.coeff.cap) e = cudaStreamSynchronize(c->cst);
+        cudaStream_t cs = c->cst[ik % bgw_ctx_s::kCopyStreams];
+        if (e == cudaSuccess && cbytes > kp.coeff.cap) e = cudaStreamSynchronize(cs);
         if (e == cudaSuccess) e = kp.coeff.ensure(cbytes, c->st);
-        if (e == cudaSuccess && kp.consumed_set) e = cudaStreamWaitEvent(c->cst, kp.consumed, 0);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(kp.coeff.p, coeff, cbytes, cudaMemcpyHostToDevice, c->cst);
-        if (e == cudaSuccess) e = cudaEventRecord(kp.copied, c->cst);
-        // later work on the context stream (this k's transform first) waits for the copy
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, kp.copied, 0);
+        if (e == cudaSuccess && kp.consumed_set) e = cudaStreamWaitEvent(cs, kp.consumed, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(kp.coeff.p, coeff, cbytes, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(kp.copied, cs);
+        // the k's transform waits for the copy: a deferred build (flush_k1)
+        // adds that wait just before it, so the copy can run beside the work
+        // already queued on the context stream; an immediate build waits here
+        if (c->defer_k1)
+            kp.copy_wait = true;
+        else if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(c->st, kp.copied, 0);
         if (e != cudaSuccess) return c->cuda_fail(e, "wfn_upload: copy-ahead coefficient copy");
         src = static_cast<const double *>(kp.coeff.p);
     } else if (c->defer_k1) {
@@ -1665,7 +1682,8 @@ bgw_status bgw_graph_begin(bgw_ctx c) {
     if (c->capturing) return c->fail(BGW_E_STATE, "graph_begin: already capturing");
     cudaError_t e = flush_k1(c);   // uploads made before the capture are not part of it
     if (e == cudaSuccess) e = c->drain();
-    if (e == cudaSuccess && c->cst) e = cudaStreamSynchronize(c->cst);
+    for (int i = 0; i < bgw_ctx_s::kCopyStreams && e == cudaSuccess; ++i)
+        if (c->cst[i]) e = cudaStreamSynchronize(c->cst[i]);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return c->cuda_fail(e, "graph_begin");
     c->capturing = true;
@@ -1757,10 +1775,11 @@ void bgw_destroy(bgw_ctx c) {
             cudaGetLastError();
         }
         cudaStreamSynchronize(c->st);
-        if (c->cst) {
-            cudaStreamSynchronize(c->cst);
-            cudaStreamDestroy(c->cst);
-        }
+        for (cudaStream_t cs : c->cst)
+            if (cs) {
+                cudaStreamSynchronize(cs);
+                cudaStreamDestroy(cs);
+            }
         if (c->gst) {
             cudaStreamSynchronize(c->gst);
             cudaStreamDestroy(c->gst);

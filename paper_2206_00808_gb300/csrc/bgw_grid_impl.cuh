@@ -1103,7 +1103,7 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
     C *Sp = static_cast<C *>(S), *Rp = static_cast<C *>(R), *Up = static_cast<C *>(U);
     const double2 *cf = reinterpret_cast<const double2 *>(coeff);
     const int *inv = cube_map + (long)a.w[0] * a.w[1] * a.w[2];
-    const bool oct = oct_len(a) && (path == 3 || (use_coop(a) && use_oct(a)));
+    bool oct = oct_len(a) && (path == 3 || (use_coop(a) && use_oct(a)));
     if (path == 4 && sizeof(T) == 4 && a.n[0] == a.n[1] && a.n[1] == a.n[2] && a.n[0] < kCoopMinN) {
         // cube-less one-kernel transform, three CTAs per SM, where it fits
         int KP = 0;
@@ -1128,7 +1128,12 @@ static cudaError_t wfn_to_grid(const double *coeff, int ngw, int B, const int *c
             return cudaGetLastError();
         }
     }
-    if (const int KP = (path == 1 || oct) ? 0 : fused_planes(a, path == 2 ? kFusedSmemMax : kFusedSmemAuto)) {
+    const int KP = (path == 1 || oct) ? 0 : fused_planes(a, path == 2 ? kFusedSmemMax : kFusedSmemAuto);
+    // automatic choice for cubic FP32 boxes of 32 and 40 whose x-transformed
+    // cube does not fit the one-kernel transform: the eight-lane kernels
+    // (GaSb-like 32^3: 48.8 -> 41.4 ms per q-point against the one-lane passes)
+    if (path == 0 && !KP && sizeof(T) == 4 && oct_len(a)) oct = true;
+    if (KP) {
         const size_t smem = fused_smem(a, KP);
         cudaError_t e = cudaSuccess;
         BGW_FOR_EACH_LEN(a.n[0], {
