@@ -79,8 +79,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="gasb32")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
-                    help="precision of the headline value (default mixed)")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "tf32x3", "tf32"], default="mixed",
+                    help="precision of the headline value (default mixed = split-BF16 x3)")
+    ap.add_argument("--no-formats", action="store_true",
+                    help="skip the TF32 contraction forms on the FP64 leg's k-subset (mixed headline)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -566,7 +568,7 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_DEFER_K1, 1)
     if args.copy_ahead:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_COPY_AHEAD, 1)
-    if args.overlap and precision == "mixed":
+    if args.overlap and precision != "fp64":
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_OVERLAP, 1)
     if precision == "fp64" and args.fp64_dfma:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_FP64_CONTRACTION, 1)
@@ -602,7 +604,7 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
         step()
     # eager, profiled: stage breakdown and per-kernel times, on one stream so
     # that each kernel's events bracket it alone
-    ovl = args.overlap and precision == "mixed"
+    ovl = args.overlap and precision != "fp64"
     if ovl:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_OVERLAP, 0)
     B.bgw_profile(ctx.ctx, True)
@@ -639,7 +641,7 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
              if precision == "fp64" else
              {"wfn_to_grid": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
               "mtxel": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
-              "contraction": (sustained / 3, "BF16 sustained / 3 products")})
+              "contraction": contraction_peak(precision, sustained, "")})
     bm = byte_model(p, 16 if precision == "fp64" else 8)
     hbm = measured_hbm_gbs()
     for name, st in res["stages"].items():
@@ -828,18 +830,18 @@ def chi0_on(B, ctx, qlist, freq, ks):
     return out
 
 
-def fp64_leg(B, torch, p, args, stream, dev_in, ks, reps=2):
-    """The FP64 path on k-points ks of the workload: every run re-uploads the
-    k-points it reads (so each includes the sphere-to-grid transforms of ks
-    and of their k + q partners), accumulates ks and finalises to the device.
-    Grids live in a few streaming slots, not all N_k.  CUDA events on the
-    stream, one warm-up run, median of `reps`."""
+def subset_leg(B, torch, p, args, stream, dev_in, ks, prec="fp64", kchunk=None, reps=2):
+    """One precision (FP64 by default) on k-points ks of the workload: every
+    run re-uploads the k-points it reads (so each includes the sphere-to-grid
+    transforms of ks and of their k + q partners), accumulates ks and
+    finalises to the device.  Grids live in a few streaming slots, not all
+    N_k.  CUDA events on the stream, one warm-up run, median of `reps`."""
     need = with_partners(p, ks)
-    ctx = B.Chi0Context(p, "fp64", stream)
+    ctx = B.Chi0Context(p, prec, stream)
     if len(need) + 2 < p.nk:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_GRID_SLOTS, len(need) + 2)
-    B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, args.kchunk if args.kchunk > 0 else 4)
-    if args.fp64_dfma:
+    B.bgw_set_option(ctx.ctx, B.BGW_OPT_KCHUNK, kchunk or (args.kchunk if args.kchunk > 0 else 4))
+    if prec == "fp64" and args.fp64_dfma:
         B.bgw_set_option(ctx.ctx, B.BGW_OPT_FP64_CONTRACTION, 1)
     ctx.upload(device_inputs=dev_in)
     q, geps, nc = p.qs[0]
@@ -872,6 +874,47 @@ def fp64_leg(B, torch, p, args, stream, dev_in, ks, reps=2):
     return ctx, out.cpu().numpy(), ms / len(ks), stages
 
 
+TF32_PER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor rates of GB300
+
+
+def contraction_peak(precision, sustained, src):
+    """Ceiling of the mixed contraction in algorithmic FLOP/s: the measured
+    sustained BF16 rate over the products per term, scaled by the nominal
+    TF32/BF16 ratio for the TF32 forms (no TF32 rate is measured)."""
+    if precision == "tf32x3":
+        return (sustained * TF32_PER_BF16 / 3,
+                f"{src} BF16 sustained {sustained} TFLOP/s x nominal TF32/BF16 1.1/2.25 / 3 products".strip())
+    if precision == "tf32":
+        return (sustained * TF32_PER_BF16,
+                f"{src} BF16 sustained {sustained} TFLOP/s x nominal TF32/BF16 1.1/2.25, 1 product".strip())
+    return sustained / 3, f"{src} BF16 sustained {sustained} TFLOP/s / 3 products".strip()
+
+
+DTYPES = {"fp64": "f64", "mixed": "f32+bf16x3", "tf32x3": "f32+tf32x3", "tf32": "f32+tf32"}
+
+
+def format_legs(B, torch, p, args, stream, dev_in, ks, head, chi64):
+    """The contraction forms of the FP32 path (split-BF16 x3, split-TF32 x3,
+    one TF32 product) on the FP64 leg's k-subset at the headline's k-chunk:
+    per-k contraction time (the profiled stage, k5_split + k5_gemm) and the
+    error against the FP64 GPU path on the same k-points."""
+    kc = max(1, B.bgw_get_option(head["ctx"].ctx, B.BGW_OPT_KCHUNK))
+    _, sustained, src = bf16_peaks()
+    fl = flop_model(p)["contraction"] / p.nk
+    out = {"k_subset": ks, "kchunk": kc}
+    for prec in ("mixed", "tf32x3", "tf32"):
+        ctx, chi, per_k, st = subset_leg(B, torch, p, args, stream, dev_in, ks, prec, kchunk=kc)
+        ctx.close()
+        ct = st.get("contraction", 0.0) + st.get("operand_split", 0.0)
+        pk, lab = contraction_peak(prec, sustained, src)
+        out[DTYPES[prec]] = {"ms_per_k": per_k, "contraction_ms_per_k": ct,
+                             "gemm_ms_per_k": st.get("contraction", 0.0),
+                             "gemm_tflops": fl / max(1e-9, st.get("contraction", 0.0) * 1e-3) / 1e12,
+                             "gemm_peak": pk, "peak_source": lab,
+                             "vs_fp64_on_subset": error_stats(chi, chi64)}
+    return out
+
+
 def head_roofline(p, res, precision, args, steps):
     """Roofline of the dominant stage of the headline (matrix elements or
     contraction, whichever takes longer): achieved = algorithmic FLOPs of the
@@ -896,9 +939,9 @@ def head_roofline(p, res, precision, args, steps):
                  "achieved": ach, "peak": sustained / 15, "unit": "TFLOP/s", "frac": ach / (sustained / 15),
                  "peak_source": f"{src} BF16 sustained {sustained} TFLOP/s / 15 digit products"}
         else:
-            r = {"bound": "tensor", "kernel": "k5_gemm", "achieved": ach, "peak": sustained / 3,
-                 "unit": "TFLOP/s", "frac": ach / (sustained / 3),
-                 "peak_source": f"{src} BF16 sustained {sustained} TFLOP/s / 3 products"}
+            pk, lab = contraction_peak(precision, sustained, src)
+            r = {"bound": "tensor", "kernel": "k5_gemm", "achieved": ach, "peak": pk,
+                 "unit": "TFLOP/s", "frac": ach / pk, "peak_source": lab}
     else:
         ach = fl["mtxel"] / (mt * 1e-3) / 1e12
         pk = args.fp64_peak if precision == "fp64" else FP32_PEAK_TFLOPS
@@ -964,7 +1007,7 @@ def run_ours(args, world, rank, local):
     fl = flop_model(p)
     steps = args.steps
     nq = len(p.qs)
-    other_prec = "fp64" if args.precision == "mixed" else "mixed"
+    other_prec = "mixed" if args.precision == "fp64" else "fp64"
 
     head = measure(B, torch, p, args.precision, args, dist, stream, dev_in, local, True)
     ms = head["ms"]
@@ -978,11 +1021,11 @@ def run_ours(args, world, rank, local):
     # the whole mixed step (FP64 headline)
     other, octx = None, None
     if not args.no_other and nq == 1:
-        if args.precision == "mixed":
+        if args.precision != "fp64":
             n = min(args.fp64_ks, p.nk)
             umk = umklapp_ks(p)
             ks = sorted(set(range(n)) | set(umk[:n]))
-            octx, chi64, per_k, st64 = fp64_leg(B, torch, p, args, stream, dev_in, ks)
+            octx, chi64, per_k, st64 = subset_leg(B, torch, p, args, stream, dev_in, ks)
             chimx = chi0_on(B, head["ctx"], [(q, geps, nc)], p.freq, ks)
             ms64 = per_k * p.nk
             other = {"precision": "fp64 (FP64 grids, FFTs, M and contraction)",
@@ -996,6 +1039,8 @@ def run_ours(args, world, rank, local):
                      "speedup_mixed_vs_fp64": ms64 / ms,
                      "mixed_vs_fp64_on_subset": error_stats(chimx, chi64),
                      "error_reference": "the FP64 GPU path on the same k-subset"}
+            if not args.no_formats:
+                other["contraction_formats"] = format_legs(B, torch, p, args, stream, dev_in, ks, head, chi64)
         else:
             mix = measure(B, torch, p, "mixed", args, dist, stream, dev_in, local, False)
             ref = head["outs"][0].cpu().numpy()
@@ -1033,7 +1078,7 @@ def run_ours(args, world, rank, local):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "ms_per_step_eager": head["ms_eager"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.precision == "fp64" else "f32+bf16x3",
+                "dtype": DTYPES[args.precision],
                 "data": "synthetic",
                 "config": {"workload": desc, "precision": args.precision,
                            "timing": "one captured CUDA graph per step, replayed; stages from an "

@@ -80,10 +80,19 @@ typedef enum {
     BGW_FP64 = 0,          /* FP64 grids, FFTs and M; the contraction to FP64
                               accuracy on tensor cores (exact BF16 digit
                               slices) or, by option, on the FP64 pipe */
-    BGW_MIXED_BF16X3 = 1   /* FP32 grids/FFTs, complex64 M, contraction as
+    BGW_MIXED_BF16X3 = 1,  /* FP32 grids/FFTs, complex64 M, contraction as
                               split-BF16 (3 products) on tensor cores with FP32
                               accumulation per k, FP64 weights and FP64
                               reduction across k */
+    BGW_MIXED_TF32X3 = 2,  /* as BGW_MIXED_BF16X3 with split-TF32 operands
+                              (hi + lo to ~2^-22; 3 products, tcgen05
+                              kind::tf32 at half the BF16 rate): the same
+                              FP32 accumulation, twice the operand bytes */
+    BGW_MIXED_TF32 = 3     /* as BGW_MIXED_BF16X3 with ONE TF32 product
+                              (operands rounded to 11 significant bits):
+                              ~4e-5 relative error in chi0 (3e-4 in its
+                              off-diagonal part), above the 2e-5 bar of the
+                              mixed forms; for estimates only */
 } bgw_precision;
 
 /* One momentum transfer with its dielectric G-sphere (the G, G' of chi0). */
@@ -104,7 +113,7 @@ BGW_API const char *bgw_version(void);
  *   kcrys   : host, [nk][3] crystal coordinates
  *   nv      : occupied bands per k (bands 0..nv-1 of each upload)
  *   nc_max  : empty bands held per k (bands nv..nv+nc_max-1)
- *   prec    : BGW_FP64 or BGW_MIXED_BF16X3
+ *   prec    : BGW_FP64, BGW_MIXED_BF16X3, BGW_MIXED_TF32X3 or BGW_MIXED_TF32
  *   stream  : cudaStream_t to queue all work on (NULL = default stream)
  * The real-space grids, nk * (nv+nc_max) * 2 * N1*N2*N3 complex values
  * (complex128 for FP64, complex64 for mixed; fewer with BGW_OPT_GRID_SLOTS),

@@ -22,8 +22,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 BGW_OK, BGW_E_ARG, BGW_E_STATE, BGW_E_CUDA, BGW_E_NOMEM, BGW_E_GRID, BGW_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 BGW_W_ALIAS = 1
-BGW_FP64, BGW_MIXED_BF16X3 = 0, 1
-PRECISIONS = {"fp64": BGW_FP64, "mixed": BGW_MIXED_BF16X3}
+BGW_FP64, BGW_MIXED_BF16X3, BGW_MIXED_TF32X3, BGW_MIXED_TF32 = 0, 1, 2, 3
+PRECISIONS = {"fp64": BGW_FP64, "mixed": BGW_MIXED_BF16X3, "tf32x3": BGW_MIXED_TF32X3, "tf32": BGW_MIXED_TF32}
 
 EXPORTED = ["bgw_version", "bgw_create", "bgw_wfn_upload", "bgw_mtxel_spinor", "bgw_chi0_reset",
             "bgw_chi0_accumulate", "bgw_chi0_finalize", "bgw_profile", "bgw_profile_read",

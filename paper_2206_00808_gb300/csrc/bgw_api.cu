@@ -608,7 +608,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Bytes of split operands the mixed contraction keeps for q-point s.
 size_t mixed_q_bytes(const bgw_ctx_s *c, const QState &s, int nfreq, int kchunk) {
-    return align256(bgw::mixed_workspace_bytes((long)kchunk * c->nv * s.nc, s.ng, nfreq));
+    return align256(bgw::mixed_workspace_bytes((long)kchunk * c->nv * s.nc, s.ng, nfreq, (int)c->prec));
 }
 
 // Workspace of the FP64 contraction of P pairs (either kernel).
@@ -839,7 +839,8 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
                     void *ws = static_cast<char *>(c->mixed_ws.p) + off;
                     off += mixed_q_bytes(c, s, nfreq, kchunk);
                     const int rec = c->stage_begin_on(5, gs);
-                    e = bgw::mixed_split(M, PT, s.ng, static_cast<const double *>(c->W.p), nfreq, ws, gs);
+                    e = bgw::mixed_split(M, PT, s.ng, static_cast<const double *>(c->W.p), nfreq, ws, (int)c->prec,
+                                         gs);
                     c->stage_end(rec, 1);
                     if (e == cudaSuccess && ovl) e = cudaEventRecord(c->ov_free[turn], gs);
                     if (e != cudaSuccess) return join(), e;
@@ -852,7 +853,7 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
             }
             if (c->prec != BGW_FP64) {
                 const int rec = c->stage_begin_on(3, gs);
-                e = bgw::mixed_gemm(group.data(), (int)group.size(), nfreq, c->sm_count, gs,
+                e = bgw::mixed_gemm(group.data(), (int)group.size(), nfreq, (int)c->prec, c->sm_count, gs,
                                     static_cast<int *>(c->errflag.p), c->test_drop_load);
                 c->stage_end(rec, 1);
                 if (e != cudaSuccess) return join(), e;
@@ -944,6 +945,9 @@ struct CkptHeader {
     int32_t box1, box2, nv, nc_max;
 };
 static_assert(sizeof(CkptHeader) == 56, "checkpoint header layout");
+static_assert((int)BGW_MIXED_BF16X3 == bgw::kMixedBF16x3 && (int)BGW_MIXED_TF32X3 == bgw::kMixedTF32x3 &&
+                  (int)BGW_MIXED_TF32 == bgw::kMixedTF32,
+              "mixed operand formats follow bgw_precision");
 
 struct Fnv {
     uint64_t h = 1469598103934665603ull;
@@ -1014,7 +1018,7 @@ bgw_status bgw_create(bgw_ctx *out, const int fft[3], int nk, const double *kcry
         g_create_error = "bgw_create: nk, nv and nc_max must be >= 1";
         return BGW_E_ARG;
     }
-    if (prec != BGW_FP64 && prec != BGW_MIXED_BF16X3) {
+    if (prec != BGW_FP64 && prec != BGW_MIXED_BF16X3 && prec != BGW_MIXED_TF32X3 && prec != BGW_MIXED_TF32) {
         g_create_error = "bgw_create: unknown precision";
         return BGW_E_ARG;
     }
@@ -1530,7 +1534,8 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
     if (vst != BGW_OK) return vst;
     if (k_end == k_begin) return c->fail(BGW_E_ARG, "autotune: empty k range");
     // cache key: everything the timing depends on
-    std::string key = std::string(c->prec == BGW_FP64 ? "fp64" : "mixed") + " box " +
+    static const char *const prec_name[] = {"fp64", "mixed", "tf32x3", "tf32"};
+    std::string key = std::string(prec_name[c->prec]) + " box " +
                       std::to_string(c->box[0]) + "x" + std::to_string(c->box[1]) + "x" +
                       std::to_string(c->box[2]) + " nv " + std::to_string(c->nv) + " nfreq " +
                       std::to_string(nfreq) + " span " + std::to_string(k_end - k_begin);
@@ -1634,7 +1639,7 @@ bgw_status bgw_autotune(bgw_ctx c, int nq, const bgw_q *qs, int nfreq, const dou
             for (auto &s : tq) {
                 mb = std::max(mb, (size_t)kc * c->nv * s.nc * s.ng * c->csize);
                 if (c->prec != BGW_FP64)
-                    ws = std::max(ws, bgw::mixed_workspace_bytes((long)kc * c->nv * s.nc, s.ng, nfreq));
+                    ws = std::max(ws, bgw::mixed_workspace_bytes((long)kc * c->nv * s.nc, s.ng, nfreq, (int)c->prec));
                 else
                     ws = std::max(ws, f64_ws_bytes(c, (long)kc * c->nv * s.nc, s.ng, nfreq));
             }

@@ -10,7 +10,10 @@
 // B_j = w_j X.  Each operand is split into BF16 hi + lo (x ~ hi + lo to
 // ~2^-17 relative) and D = A_hi B_hi + A_hi B_lo + A_lo B_hi runs on tcgen05
 // kind::f16 with FP32 accumulation in tensor memory.  Each 64-pair K block
-// loads the four tiles once and issues all three products.  The accumulator
+// loads the four tiles once and issues all three products.  Two TF32 forms
+// use the same kernels on kind::tf32: three products of TF32 hi + lo
+// (x ~ hi + lo to ~2^-22; 32-pair K blocks, half the BF16 MMA rate), or the
+// single product hi.hi (~2^-11 per operand).  The accumulator
 // truncates on every add, so the large hi.hi products go to three TMEM
 // accumulators (one per third of K) and the two small cross products to a
 // fourth: no accumulator takes more than a third of the large adds, and the
@@ -19,14 +22,16 @@
 // accumulator (the FP64 reduction across k blocks).
 //
 // Kernels:
-//   k5_split   M -> X planes [1 + nfreq][hi, lo], each stored as tiles
-//              [R/128][Kp/64][128 rows][64 pairs] BF16 (K-major inside a tile,
+//   k5_split   M -> X planes [1 + nfreq][hi, lo] (hi only for one product),
+//              each stored as tiles [R/128][Kp/Kb][128 rows][Kb pairs] of
+//              128-byte rows (Kb = 64 BF16 or 32 TF32; K-major inside a tile,
 //              zero padded to R = 128-multiple rows, Kp = 64-multiple pairs):
 //              one 16 KB TMA box is one contiguous piece of memory, so the
 //              split writes and the GEMM loads whole DRAM pages
 //   k5_gemm    one CTA per (lower 128x128 tile of D, frequency): TMA loads
-//              (128B swizzle) into a 3-stage ring of 64 KB, one thread issues
-//              tcgen05.mma, all four warps drain TMEM and update chi in FP64.
+//              (128B swizzle) into a ring of 192 KB (3 stages of four tiles,
+//              or 6 of two for one product), one thread issues tcgen05.mma,
+//              four warps drain TMEM and update chi in FP64.
 // Every mbarrier wait has an iteration limit; on expiry the kernel records
 // an error code in *err, waits (bounded) for its own copies in flight,
 // frees its tensor memory and returns.
@@ -48,17 +53,33 @@ using namespace tc;
 
 constexpr int kTileM = 128;           // rows of D per CTA (A rows)
 constexpr int kTileN = 128;           // columns of D per CTA (B rows)
-constexpr int kBlockK = 64;           // BF16 elements per 128-byte swizzled row
-constexpr int kStages = 3;
-constexpr int kTileBytes = kTileM * kBlockK * 2;                 // 16 KB per operand tile
-constexpr int kStageBytes = 4 * kTileBytes;                      // A_hi, A_lo, B_hi, B_lo
+constexpr int kRowBytes = 128;        // one swizzled operand row (K-major)
+constexpr int kTileBytes = kTileM * kRowBytes;                   // 16 KB per operand tile
+constexpr int kPadK = 64;             // pair padding of the planes (both formats)
 constexpr int kAccCols = 4 * kTileN;                             // 3 hi.hi + 1 cross accumulator
 constexpr int kMaxGroup = 48;                                    // q-points per grouped launch
 constexpr int kErrFull = 1, kErrEmpty = 2, kErrAccum = 3, kErrDrain = 4;
 
+// Operand format F (the kMixed* values): element size, pairs per 128-byte
+// row, hi/lo planes per operand, ring depth and the MMA instruction
+// descriptor (D = F32, A = B = BF16 or TF32, both K-major, M = N = 128).
+template <int F>
+struct Fmt {
+    static constexpr bool tf32 = F != kMixedBF16x3;
+    static constexpr bool three = F != kMixedTF32;
+    static constexpr int esize = tf32 ? 4 : 2;
+    static constexpr int blockK = kRowBytes / esize;
+    static constexpr int halves = three ? 2 : 1;
+    static constexpr int stageBytes = 2 * halves * kTileBytes;
+    static constexpr int stages = three ? 3 : 6;
+    static constexpr uint32_t ab = tf32 ? 2u : 1u;
+    static constexpr uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                                      ((uint32_t)(kTileM >> 4) << 24);
+};
+
 // ------------------------------------------------------------ split kernel --
-// plane 0: A = X; plane 1 + j: B_j = w_j X.  Output [plane][hi|lo] of tiles
-// [R/128][Kp/64][128][64].
+// operand 0: A = X; operand 1 + j: B_j = w_j X.  Output [operand][hi|lo] of
+// tiles [R/128][Kp/Kb][128][Kb].
 // One CTA per (32 complex G = 64 real rows) x (64 pairs) block writes every
 // plane of that block: M is read once, the weights are converted to FP32
 // once per pair, and each thread stores 16 consecutive pairs of one row
@@ -76,9 +97,18 @@ __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) {
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
+// Nearest TF32 value (10 stored mantissa bits), ties away from zero: add half
+// a unit of the 13 dropped bits to the magnitude, then clear them (a carry
+// into the exponent is the correct rounding up).
+__device__ __forceinline__ float tf32_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+template <int F>
 __global__ void __launch_bounds__(256)
 k5_split(const float2 *__restrict__ M, int P, int ng, const double *__restrict__ w, int nfreq, int R,
-         int Kp, __nv_bfloat16 *__restrict__ X) {
+         int Kp, uint8_t *__restrict__ X) {
+    using T = Fmt<F>;
     extern __shared__ float split_sm[];
     float *re = split_sm;                                // [kSplitP][kSplitRow]
     float *im = re + kSplitP * kSplitRow + 16;           // offset by 16 banks from re
@@ -109,34 +139,48 @@ k5_split(const float2 *__restrict__ M, int P, int ng, const double *__restrict__
     float x[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) x[i] = src[(pq + i) * kSplitRow];
-    const long planeElems = (long)R * Kp;
-    const long kblocks = Kp / kSplitP;                   // 64-pair blocks per row tile
-    __nv_bfloat16 *base = X + (((long)(row / 128) * kblocks + p0 / kSplitP) * 128 + row % 128) * kSplitP + pq;
-    for (int plane = 0; plane <= nfreq; ++plane) {
-        const float *wp = wt + (plane - 1) * kSplitP + pq;
-        uint32_t h[8], l[8];
+    const long planeBytes = (long)R * Kp * T::esize;
+    const long kblocks = Kp / T::blockK;                 // K blocks per row tile
+    const int pc = p0 + pq;                              // this thread's first pair
+    uint8_t *base = X + ((((long)(row / 128) * kblocks + pc / T::blockK) * 128 + row % 128) * T::blockK +
+                         pc % T::blockK) * T::esize;
+    constexpr int kWords = 16 * T::esize / 4;            // 16 pairs in 32-bit words
+    for (int op = 0; op <= nfreq; ++op) {
+        const float *wp = wt + (op - 1) * kSplitP + pq;
+        uint32_t h[kWords], l[kWords];
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
             float a = x[i], b = x[i + 1];
-            if (plane > 0) {
+            if (op > 0) {
                 a *= wp[i];
                 b *= wp[i + 1];
             }
-            const __nv_bfloat162 hh = __floats2bfloat162_rn(a, b);
-            const float2 hf = __bfloat1622float2(hh);
-            h[i / 2] = bf2_bits(hh);
-            l[i / 2] = bf2_bits(__floats2bfloat162_rn(a - hf.x, b - hf.y));
+            if constexpr (T::tf32) {
+                const float ha = tf32_round(a), hb = tf32_round(b);
+                h[i] = __float_as_uint(ha);
+                h[i + 1] = __float_as_uint(hb);
+                l[i] = __float_as_uint(tf32_round(a - ha));
+                l[i + 1] = __float_as_uint(tf32_round(b - hb));
+            } else {
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(a, b);
+                const float2 hf = __bfloat1622float2(hh);
+                h[i / 2] = bf2_bits(hh);
+                l[i / 2] = bf2_bits(__floats2bfloat162_rn(a - hf.x, b - hf.y));
+            }
         }
-        uint4 *ho = reinterpret_cast<uint4 *>(base + (long)plane * 2 * planeElems);
-        uint4 *lo = reinterpret_cast<uint4 *>(base + ((long)plane * 2 + 1) * planeElems);
-        ho[0] = make_uint4(h[0], h[1], h[2], h[3]);
-        ho[1] = make_uint4(h[4], h[5], h[6], h[7]);
-        lo[0] = make_uint4(l[0], l[1], l[2], l[3]);
-        lo[1] = make_uint4(l[4], l[5], l[6], l[7]);
+        uint4 *ho = reinterpret_cast<uint4 *>(base + (long)op * T::halves * planeBytes);
+#pragma unroll
+        for (int v = 0; v < kWords / 4; ++v) ho[v] = make_uint4(h[4 * v], h[4 * v + 1], h[4 * v + 2], h[4 * v + 3]);
+        if constexpr (T::three) {
+            uint4 *lo = reinterpret_cast<uint4 *>(base + ((long)op * 2 + 1) * planeBytes);
+#pragma unroll
+            for (int v = 0; v < kWords / 4; ++v)
+                lo[v] = make_uint4(l[4 * v], l[4 * v + 1], l[4 * v + 2], l[4 * v + 3]);
+        }
     }
 }
 
-// One 128 x 64 tile (k-block kb, row tile rt, plane) of the tiled operand
+// One 128-row tile (k-block kb, row tile rt, plane) of the tiled operand
 // layout: coordinates {0, 0, kb, rt, plane} of the 5-D map.
 __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap *map, uint32_t bar, int kb,
                                               int rt, int plane) {
@@ -160,19 +204,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
-// M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
-        : "memory");
+// D (+)= A B^T for one 32-byte K step: kind::f16 (BF16) or kind::tf32.
+template <int F>
+__device__ __forceinline__ void mma_step(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    if constexpr (Fmt<F>::tf32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(Fmt<F>::idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(Fmt<F>::idesc), "r"(accumulate)
+            : "memory");
+    }
 }
 
 __device__ __forceinline__ void lower_tile(int t, int &bi, int &bj) {
@@ -203,7 +252,7 @@ constexpr int kGemmWarps = 6;
 struct GroupParams {
     CUtensorMap map[kMaxGroup];   // operand planes of each q-point
     double2 *acc[kMaxGroup];      // FP64 accumulator [nfreq][ng][ng]
-    int kp[kMaxGroup];            // padded pair count (multiple of kBlockK)
+    int kp[kMaxGroup];            // padded pair count (multiple of kPadK)
     int ng[kMaxGroup];
     int first[kMaxGroup + 1];     // first work item of each q-point
     int nq, nfreq;
@@ -214,7 +263,7 @@ struct Item {
     int q, ti, tj, j, nkb;
 };
 
-__device__ __forceinline__ Item decode(const GroupParams &gp, int item) {
+__device__ __forceinline__ Item decode(const GroupParams &gp, int item, int blockK) {
     Item it;
     int q = 0;
     while (q + 1 < gp.nq && gp.first[q + 1] <= item) ++q;
@@ -227,12 +276,15 @@ __device__ __forceinline__ Item decode(const GroupParams &gp, int item) {
     lower_tile(local % ntiles, it.ti, it.tj);
     it.q = q;
     it.j = local / ntiles;
-    it.nkb = gp.kp[q] / kBlockK;
+    it.nkb = gp.kp[q] / blockK;
     return it;
 }
 
+template <int F>
 __global__ void __launch_bounds__(kGemmWarps * 32, 1)
 k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
+    using T = Fmt<F>;
+    constexpr int kStages = T::stages, kStageBytes = T::stageBytes;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages];
     __shared__ __align__(8) uint64_t empty_bar[kStages];
@@ -279,12 +331,13 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
     if (warp == 4) {
         if (lane == 0) {
             // TMA producer; planes: 0 A_hi, 1 A_lo, 2 + 2j B_j hi, 3 + 2j B_j lo
+            // (one product: 0 A, 1 + j B_j)
             long pit = 0, issued_from = 0, dropped = -1;
             for (int item = blockIdx.x; item < total; item += gridDim.x) {
-                const Item w = decode(gp, item);
+                const Item w = decode(gp, item, T::blockK);
                 const CUtensorMap *map = &gp.map[w.q];
                 asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-                const int bhi = 2 + 2 * w.j, blo = 3 + 2 * w.j;
+                const int bhi = T::halves * (1 + w.j), blo = bhi + 1;
                 for (int it = 0; it < w.nkb; ++it, ++pit) {
                     const int s = (int)(pit % kStages);
                     if (!mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((pit / kStages) & 1) ^ 1))) {
@@ -300,10 +353,15 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
                     const uint32_t st0 = ring + s * kStageBytes;
                     const uint32_t fb = smem_u32(&full_bar[s]);
                     mbar_expect_tx(fb, kStageBytes);
-                    tma_load_tile(st0, map, fb, it, w.ti, 0);
-                    tma_load_tile(st0 + kTileBytes, map, fb, it, w.ti, 1);
-                    tma_load_tile(st0 + 2 * kTileBytes, map, fb, it, w.tj, bhi);
-                    tma_load_tile(st0 + 3 * kTileBytes, map, fb, it, w.tj, blo);
+                    if constexpr (T::three) {
+                        tma_load_tile(st0, map, fb, it, w.ti, 0);
+                        tma_load_tile(st0 + kTileBytes, map, fb, it, w.ti, 1);
+                        tma_load_tile(st0 + 2 * kTileBytes, map, fb, it, w.tj, bhi);
+                        tma_load_tile(st0 + 3 * kTileBytes, map, fb, it, w.tj, blo);
+                    } else {
+                        tma_load_tile(st0, map, fb, it, w.ti, 0);
+                        tma_load_tile(st0 + kTileBytes, map, fb, it, w.tj, bhi);
+                    }
                 }
                 if (*(volatile int *)&abort_flag) break;
             }
@@ -326,7 +384,7 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
             int nitem = 0;
             bool stop = false;
             for (int item = blockIdx.x; item < total && !stop; item += gridDim.x, ++nitem) {
-                const Item w = decode(gp, item);
+                const Item w = decode(gp, item, T::blockK);
                 if (nitem > 0 && !mbar_wait(smem_u32(&tmem_free), (uint32_t)((nitem - 1) & 1))) {
                     atomicExch(err, kErrAccum);
                     atomicExch(&abort_flag, 1);
@@ -358,16 +416,25 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t st0 = ring + s * kStageBytes;
-                    const uint64_t ahi = smem_desc(st0), alo = smem_desc(st0 + kTileBytes);
-                    const uint64_t bhd = smem_desc(st0 + 2 * kTileBytes), bld = smem_desc(st0 + 3 * kTileBytes);
                     const uint32_t acc_hh = tmem + (uint32_t)(slot * kTileN);
+                    if constexpr (T::three) {
+                        const uint64_t ahi = smem_desc(st0), alo = smem_desc(st0 + kTileBytes);
+                        const uint64_t bhd = smem_desc(st0 + 2 * kTileBytes), bld = smem_desc(st0 + 3 * kTileBytes);
 #pragma unroll
-                    for (int k = 0; k < kBlockK / 16; ++k) {
-                        // advance 16 BF16 = 32 bytes along K inside the swizzled row
-                        const uint64_t o = (uint64_t)(2 * k);
-                        mma_bf16(acc_hh, ahi + o, bhd + o, (first_in_sub && k == 0) ? 0u : 1u);
-                        mma_bf16(acc_x, ahi + o, bld + o, (it == 0 && k == 0) ? 0u : 1u);
-                        mma_bf16(acc_x, alo + o, bhd + o, 1u);
+                        for (int k = 0; k < kRowBytes / 32; ++k) {
+                            // advance 32 bytes along K inside the swizzled row (16 BF16 or 8 TF32)
+                            const uint64_t o = (uint64_t)(2 * k);
+                            mma_step<F>(acc_hh, ahi + o, bhd + o, (first_in_sub && k == 0) ? 0u : 1u);
+                            mma_step<F>(acc_x, ahi + o, bld + o, (it == 0 && k == 0) ? 0u : 1u);
+                            mma_step<F>(acc_x, alo + o, bhd + o, 1u);
+                        }
+                    } else {
+                        const uint64_t ad = smem_desc(st0), bd = smem_desc(st0 + kTileBytes);
+#pragma unroll
+                        for (int k = 0; k < kRowBytes / 32; ++k) {
+                            const uint64_t o = (uint64_t)(2 * k);
+                            mma_step<F>(acc_hh, ad + o, bd + o, (first_in_sub && k == 0) ? 0u : 1u);
+                        }
                     }
                     mma_commit(smem_u32(&empty_bar[s]));
                     if ((it % kSub) == kSub - 1 || it == w.nkb - 1) {
@@ -386,7 +453,7 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
         long gsub = 0;
         int nitem = 0;
         for (int item = blockIdx.x; item < total; item += gridDim.x, ++nitem) {
-            const Item w = decode(gp, item);
+            const Item w = decode(gp, item, T::blockK);
             const int nsub = (w.nkb + kSub - 1) / kSub;
             float racc[kTileN];
 #pragma unroll
@@ -422,12 +489,14 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if constexpr (T::three) {
 #pragma unroll
-            for (int c0 = 0; c0 < kTileN; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(lane_base + (uint32_t)(kSlots * kTileN + c0), v);   // cross terms
+                for (int c0 = 0; c0 < kTileN; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(lane_base + (uint32_t)(kSlots * kTileN + c0), v);   // cross terms
 #pragma unroll
-                for (int i = 0; i < 32; ++i) racc[c0 + i] += __uint_as_float(v[i]);
+                    for (int i = 0; i < 32; ++i) racc[c0 + i] += __uint_as_float(v[i]);
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&tmem_free));   // the MMAs of the next item may start
@@ -482,36 +551,67 @@ long round_up(long x, long m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-size_t mixed_workspace_bytes(long P, int ng, int nfreq) {
+static bool known_format(int fmt) { return fmt == kMixedBF16x3 || fmt == kMixedTF32x3 || fmt == kMixedTF32; }
+
+static int elem_size(int fmt) { return fmt == kMixedBF16x3 ? 2 : 4; }
+
+static int halves(int fmt) { return fmt == kMixedTF32 ? 1 : 2; }
+
+size_t mixed_workspace_bytes(long P, int ng, int nfreq, int fmt) {
     const long R = round_up(2L * ng, kTileM);
-    const long Kp = round_up(P, kBlockK);
-    return (size_t)(1 + nfreq) * 2 * R * Kp * sizeof(__nv_bfloat16) + 256;
+    const long Kp = round_up(P, kPadK);
+    return (size_t)(1 + nfreq) * halves(fmt) * R * Kp * elem_size(fmt) + 256;
 }
 
-cudaError_t mixed_split(const void *M, int P, int ng, const double *w, int nfreq, void *ws,
-                        cudaStream_t st) {
-    if (P == 0) return cudaSuccess;
+namespace {
+
+template <int F>
+cudaError_t split_launch(const void *M, int P, int ng, const double *w, int nfreq, void *ws, cudaStream_t st) {
     const long R = round_up(2L * ng, kTileM);
-    const long Kp = round_up(P, kBlockK);
+    const long Kp = round_up(P, kPadK);
     // R is a multiple of 128 (64 real rows per block) and Kp of 64
     dim3 sgrid((unsigned)(Kp / kSplitP), (unsigned)(R / (2 * kSplitG)));
     const size_t smem = sizeof(float) * split_smem_floats(nfreq);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k5_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k5_split<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k5_split<<<sgrid, 256, smem, st>>>(static_cast<const float2 *>(M), P, ng, w, nfreq, (int)R, (int)Kp,
-                                       static_cast<__nv_bfloat16 *>(ws));
+    k5_split<F><<<sgrid, 256, smem, st>>>(static_cast<const float2 *>(M), P, ng, w, nfreq, (int)R, (int)Kp,
+                                          static_cast<uint8_t *>(ws));
     return cudaGetLastError();
+}
+
+template <int F>
+cudaError_t gemm_launch(const GroupParams &gp, int items, int sm_count, cudaStream_t st, int *err) {
+    const int smem = Fmt<F>::stages * Fmt<F>::stageBytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k5_gemm<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = items < sm_count ? items : sm_count;
+    k5_gemm<F><<<grid, kGemmWarps * 32, smem, st>>>(gp, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t mixed_split(const void *M, int P, int ng, const double *w, int nfreq, void *ws, int fmt,
+                        cudaStream_t st) {
+    if (!known_format(fmt)) return cudaErrorInvalidValue;
+    if (P == 0) return cudaSuccess;
+    switch (fmt) {
+        case kMixedTF32x3: return split_launch<kMixedTF32x3>(M, P, ng, w, nfreq, ws, st);
+        case kMixedTF32: return split_launch<kMixedTF32>(M, P, ng, w, nfreq, ws, st);
+        default: return split_launch<kMixedBF16x3>(M, P, ng, w, nfreq, ws, st);
+    }
 }
 
 int mixed_max_group() { return kMaxGroup; }
 
-cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaStream_t st, int *err,
+cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int fmt, int sm_count, cudaStream_t st, int *err,
                        int drop_first_load) {
-    if (nq < 1 || nq > kMaxGroup) return cudaErrorInvalidValue;
+    if (nq < 1 || nq > kMaxGroup || !known_format(fmt)) return cudaErrorInvalidValue;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
+    const int es = elem_size(fmt), blockK = kRowBytes / es;
     GroupParams gp;
     memset(&gp, 0, sizeof gp);
     gp.nq = nq;
@@ -521,34 +621,34 @@ cudaError_t mixed_gemm(const MixedQ *qs, int nq, int nfreq, int sm_count, cudaSt
     for (int i = 0; i < nq; ++i) {
         gp.first[i] = items;
         const long R = round_up(2L * qs[i].ng, kTileM);
-        const long Kp = round_up(qs[i].P, kBlockK);
+        const long Kp = round_up(qs[i].P, kPadK);
         const int nt = (int)(R / kTileM);
         if (qs[i].P > 0) items += nt * (nt + 1) / 2 * nfreq;
         gp.kp[i] = (int)Kp;
         gp.ng[i] = qs[i].ng;
         gp.acc[i] = static_cast<double2 *>(qs[i].acc);
-        // tiled planes [plane][R/128][Kp/64][128][64]: a box is one whole tile
-        const int planes = 2 * (1 + nfreq);
-        const cuuint64_t tile = (cuuint64_t)kTileM * kBlockK * 2;
-        const cuuint64_t dims[5] = {(cuuint64_t)kBlockK, (cuuint64_t)kTileM, (cuuint64_t)(Kp / kBlockK),
-                                    (cuuint64_t)(R / kTileM), (cuuint64_t)planes};
-        const cuuint64_t strides[4] = {(cuuint64_t)kBlockK * 2, tile, tile * (cuuint64_t)(Kp / kBlockK),
-                                       tile * (cuuint64_t)(Kp / kBlockK) * (cuuint64_t)(R / kTileM)};
-        const cuuint32_t box[5] = {kBlockK, kTileM, 1, 1, 1};
+        // tiled planes [plane][R/128][Kp/Kb][128][Kb]: a box is one whole tile
+        const int planes = halves(fmt) * (1 + nfreq);
+        const cuuint64_t tile = (cuuint64_t)kTileBytes;
+        const cuuint64_t nkb = (cuuint64_t)(Kp / blockK);
+        const cuuint64_t dims[5] = {(cuuint64_t)blockK, (cuuint64_t)kTileM, nkb, (cuuint64_t)(R / kTileM),
+                                    (cuuint64_t)planes};
+        const cuuint64_t strides[4] = {(cuuint64_t)kRowBytes, tile, tile * nkb, tile * nkb * (cuuint64_t)(R / kTileM)};
+        const cuuint32_t box[5] = {(cuuint32_t)blockK, kTileM, 1, 1, 1};
         const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-        CUresult cr = g_encode(&gp.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, qs[i].ws, dims, strides,
-                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult cr = g_encode(&gp.map[i], es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                               5, qs[i].ws, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
     gp.first[nq] = items;
     if (items == 0) return cudaSuccess;
-    const int smem = kStages * kStageBytes + 1024;
-    e = cudaFuncSetAttribute(k5_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    const int grid = items < sm_count ? items : sm_count;
-    k5_gemm<<<grid, kGemmWarps * 32, smem, st>>>(gp, err);
-    return cudaGetLastError();
+    switch (fmt) {
+        case kMixedTF32x3: return gemm_launch<kMixedTF32x3>(gp, items, sm_count, st, err);
+        case kMixedTF32: return gemm_launch<kMixedTF32>(gp, items, sm_count, st, err);
+        default: return gemm_launch<kMixedBF16x3>(gp, items, sm_count, st, err);
+    }
 }
 
 }  // namespace bgw

@@ -34,6 +34,18 @@ def test_header_declares_the_boundary():
         assert n in names
 
 
+def test_precision_enum_matches_binding(lib):
+    """The four precisions of the boundary and their values, as the header
+    declares them and the binding passes them."""
+    import os
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "bgw_chi.h")).read()
+    body = text[text.index("typedef enum {\n    BGW_FP64"):]
+    body = body[:body.index("} bgw_precision;")]
+    vals = {n: int(v) for n, v in re.findall(r"\b(BGW_\w+)\s*=\s*(\d+)", body)}
+    assert vals == {"BGW_FP64": 0, "BGW_MIXED_BF16X3": 1, "BGW_MIXED_TF32X3": 2, "BGW_MIXED_TF32": 3}
+    assert lib.PRECISIONS == {"fp64": 0, "mixed": 1, "tf32x3": 2, "tf32": 3}
+
+
 def test_library_exports_every_declared_symbol(lib):
     import ctypes
     so = ctypes.CDLL(lib.LIB_PATH)

@@ -1,7 +1,11 @@
 """GPU parity of the mixed-precision path (FP32 grids and matrix elements,
 split-BF16 tensor-core contraction with FP64 weights and FP64 reduction over
 k) against the CPU FP64 oracle.  Bars: M within 5e-6 of max|M| elementwise;
-chi0 within 2e-5 relative Frobenius, overall and per frequency."""
+chi0 within 2e-5 relative Frobenius, overall and per frequency.  The TF32
+forms of the contraction: three products (BGW_MIXED_TF32X3) to the same 2e-5;
+one product (BGW_MIXED_TF32) to 1e-3, twice the unit roundoff 2^-11 of an
+operand rounded to 11 significant bits (each term x_r (w x_r') carries two
+such roundings; cancellation between terms is not counted)."""
 import numpy as np
 import pytest
 
@@ -12,14 +16,15 @@ pytestmark = pytest.mark.gpu
 
 TOL_M_FP32 = 5e-6
 TOL_CHI_MIXED = 2e-5
+TOL_CHI = {"mixed": TOL_CHI_MIXED, "tf32x3": TOL_CHI_MIXED, "tf32": 2 * 2.0 ** -11}
 
 
 def rel_fro(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
 
 
-def run(gpu_lib, p, chunks=None):
-    ctx = gpu_lib.Chi0Context(p, "mixed")
+def run(gpu_lib, p, chunks=None, prec="mixed"):
+    ctx = gpu_lib.Chi0Context(p, prec)
     ctx.upload()
     st = [ctx.accumulate(k0, k1) for k0, k1 in (chunks or [(0, p.nk)])]
     out = ctx.finalize()
@@ -68,6 +73,31 @@ def test_chi0_mixed_several_row_tiles(gpu_lib):
     ref = oracle.chi0(p)
     got, _ = run(gpu_lib, p)
     assert rel_fro(got, ref) <= TOL_CHI_MIXED
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("shape", [
+    {},                                   # si18_qx defaults
+    {"ng": 59, "nc": 13, "nfreq": 3},     # one partial row tile, a partial pair block
+    {"ng": 200, "nfreq": 2},              # 4 row tiles, 10 lower tiles
+])
+def test_chi0_tf32_contraction_matches_oracle(gpu_lib, prec, shape):
+    p = syn.make_problem("si18_qx", **shape)
+    ref = oracle.chi0(p)
+    got, _ = run(gpu_lib, p, prec=prec)
+    err = rel_fro(got, ref)
+    assert err <= TOL_CHI[prec]
+    for j in range(len(p.freq)):
+        assert rel_fro(got[j], ref[j]) <= TOL_CHI[prec]
+    if prec == "tf32":
+        assert err > 1e-7          # the single product is visibly coarser than the split forms
+
+
+def test_chi0_tf32x3_k_chunking_is_bitwise_identical(gpu_lib):
+    p = syn.make_problem("si18_qx")
+    one, _ = run(gpu_lib, p, prec="tf32x3")
+    chunked, _ = run(gpu_lib, p, chunks=[(0, 3), (3, 8)], prec="tf32x3")
+    assert np.array_equal(one, chunked)
 
 
 def test_chi0_mixed_k_chunking_is_bitwise_identical(gpu_lib):
