@@ -523,10 +523,13 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
                         const float d11 = even ? other[cc + 1] : racc[c0 + cc + 1];   // D[2g+1][2g'+1]
                         const int gp2 = (b_row + c0 + cc) >> 1;
                         if ((q < 8) == even && gp2 < ng) {
+                            // the 2x2 fold in FP32 (one more rounding of 2^-24),
+                            // then two conversions and two FP64 adds: half the
+                            // work of the slow FP64 pipe of four of each
                             double2 *o = acc + ((long)w.j * ng + g) * ng + gp2;
                             double2 t = *o;
-                            t.x += (double)d00 + (double)d11;
-                            t.y += (double)d01 - (double)d10;
+                            t.x += (double)(d00 + d11);
+                            t.y += (double)(d01 - d10);
                             *o = t;
                         }
                     }

@@ -122,12 +122,13 @@ def test_chi0_mixed_si24_k_subset(gpu_lib):
 
 @pytest.mark.parametrize("zy", [1, 2])
 @pytest.mark.parametrize("over", [{}, dict(box=(24, 24, 24), nv=9, nc=30, ng=113, nfreq=2),
-                                  dict(box=(32, 32, 32), nv=5, nc=13, ng=181, nfreq=2)])
+                                  dict(box=(32, 32, 32), nv=5, nc=13, ng=181, nfreq=2),
+                                  dict(box=(20, 20, 20), nv=6, nc=7, ng=89, nfreq=1),
+                                  dict(box=(16, 16, 16), nv=3, nc=9, ng=59, nfreq=1)])
 def test_both_zy_kernels_match_oracle(gpu_lib, zy, over):
     """The FP32 pair density + z + y passes as the plane kernel (pair tiles)
     and as the streamed kernel (resident valence planes, conduction planes in
-    double-buffered groups of four; ragged last groups here) against the
-    oracle."""
+    double-buffered groups; ragged last groups here) against the oracle."""
     p = syn.make_problem("si18_qx", **over)
     ref = oracle.chi0(p)
     ctx = gpu_lib.Chi0Context(p, "mixed")
@@ -137,3 +138,4 @@ def test_both_zy_kernels_match_oracle(gpu_lib, zy, over):
     got = ctx.finalize()
     ctx.close()
     assert rel_fro(got, ref) <= TOL_CHI_MIXED
+
