@@ -270,7 +270,7 @@ def flop_model(p):
     parts = [flop_model_q(p, iq) for iq in range(len(p.qs))]
     out = {k: sum(x[k] for x in parts) for k in parts[0]}
     out["wfn_to_grid"] = parts[0]["wfn_to_grid"]   # grids are built once per step
-    out["total"] = out["wfn_to_grid"] + out["mtxel"] + out["contraction"]
+    out["total"] = out["wfn_to_grid"] + out["mtxel"] + out["mtxel_x"] + out["contraction"]
     return out
 
 
@@ -278,12 +278,15 @@ def flop_model_q(p, iq=0):
     """Algorithmic FLOPs of one q-point: pruned radix FFTs (5 L log2 L per
     line of length L), the pair density (8 flops per point and spin
     component) and the Hermitian contraction (8 flops per complex MAC over
-    N_G(N_G+1)/2 entries per pair and frequency)."""
+    N_G(N_G+1)/2 entries per pair and frequency).  The matrix elements are
+    split as profiled: "mtxel" the pair density with the z and y passes,
+    "mtxel_x" the x pass (its sphere gather moves data only)."""
     q, geps, nc = p.qs[iq]
     n = np.array(p.box, float)
     L = float(np.log2(n[0]))
     w = geps.max(0) - geps.min(0) + 1
-    per_pair_fft = 5 * n[0] * L * (n[0] * n[1] + n[0] * w[1] + w[1] * w[2])
+    per_pair_zy = 5 * n[0] * L * (n[0] * n[1] + n[0] * w[1])
+    per_pair_x = 5 * n[0] * L * w[1] * w[2]
     per_pair_rho = 8 * 2 * np.prod(n)
     pairs = p.nk * p.nv * nc
     band_fft = 0.0
@@ -292,23 +295,27 @@ def flop_model_q(p, iq=0):
         band_fft += 2 * p.nbands * 5 * n[0] * L * (ws[1] * ws[2] + n[0] * ws[2] + n[0] * n[1])
     ng = len(geps)
     herk = 8.0 * pairs * len(p.freq) * ng * (ng + 1) / 2
-    return {"wfn_to_grid": band_fft, "mtxel": pairs * (per_pair_fft + per_pair_rho),
-            "contraction": herk, "total": band_fft + pairs * (per_pair_fft + per_pair_rho) + herk}
+    zy = pairs * (per_pair_zy + per_pair_rho)
+    x = pairs * per_pair_x
+    return {"wfn_to_grid": band_fft, "mtxel": zy, "mtxel_x": x, "contraction": herk,
+            "total": band_fft + zy + x + herk}
 
 
 def byte_model(p, csize):
-    """Least DRAM bytes of the two FFT stages in one step (every q-point):
-    the sphere -> grid transform reads each band's coefficients (complex128)
-    and writes its grid once; the matrix elements read the grids of the
-    valence bands at k and the conduction bands at k+q once and write M once
-    (csize bytes per complex value of the path's precision)."""
+    """Least DRAM bytes of the FFT stages in one step (every q-point): the
+    sphere -> grid transform reads each band's coefficients (complex128) and
+    writes its grid once; the matrix elements read the grids of the valence
+    bands at k and the conduction bands at k+q once (z and y passes) and
+    write M once (x pass); csize bytes per complex value of the path's
+    precision."""
     vol = float(np.prod(p.box))
     coeff = sum(p.nbands * 2 * len(g) * 16.0 for g in p.gvec)
     grids = p.nk * p.nbands * 2 * vol * csize
-    mtxel = 0.0
+    mtxel, mx = 0.0, 0.0
     for q, geps, nc in p.qs:
-        mtxel += p.nk * (p.nv + nc) * 2 * vol * csize + p.nk * p.nv * nc * len(geps) * csize
-    return {"wfn_to_grid": coeff + grids, "mtxel": mtxel}
+        mtxel += p.nk * (p.nv + nc) * 2 * vol * csize
+        mx += p.nk * p.nv * nc * len(geps) * csize
+    return {"wfn_to_grid": coeff + grids, "mtxel": mtxel, "mtxel_x": mx}
 
 
 # ---------------------------------------------------------------- oracle --
@@ -637,10 +644,11 @@ def measure(B, torch, p, precision, args, dist, stream, dev_in, local, with_cloc
     burst, sustained, _ = bf16_peaks()
     f64 = (args.fp64_peak, args.fp64_peak_label)
     f64c = f64 if args.fp64_dfma else (sustained / 15, "BF16 sustained / 15 digit products")
-    peaks = ({"wfn_to_grid": f64, "mtxel": f64, "contraction": f64c}
+    peaks = ({"wfn_to_grid": f64, "mtxel": f64, "mtxel_x": f64, "contraction": f64c}
              if precision == "fp64" else
              {"wfn_to_grid": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
               "mtxel": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
+              "mtxel_x": (FP32_PEAK_TFLOPS, "FP32 ALU (derived)"),
               "contraction": contraction_peak(precision, sustained, "")})
     bm = byte_model(p, 16 if precision == "fp64" else 8)
     hbm = measured_hbm_gbs()
@@ -916,9 +924,10 @@ def format_legs(B, torch, p, args, stream, dev_in, ks, head, chi64):
 
 
 def head_roofline(p, res, precision, args, steps):
-    """Roofline of the dominant stage of the headline (matrix elements or
-    contraction, whichever takes longer): achieved = algorithmic FLOPs of the
-    profiled steps over that stage's summed device time."""
+    """Roofline of the dominant kernel of the headline: the contraction
+    GEMM or the pair density + z + y kernel of the matrix elements (their x
+    pass is profiled apart), whichever takes longer; achieved = algorithmic
+    FLOPs of the profiled steps over that kernel's summed device time."""
     fl = flop_model(p)
     burst, sustained, src = bf16_peaks()
     st = res["stages"]
@@ -945,7 +954,10 @@ def head_roofline(p, res, precision, args, steps):
     else:
         ach = fl["mtxel"] / (mt * 1e-3) / 1e12
         pk = args.fp64_peak if precision == "fp64" else FP32_PEAK_TFLOPS
-        r = {"bound": "alu", "kernel": "matrix elements (pair density + pruned FFT + gather)",
+        kern = ("k2_zpass + k2_ypass (FP64)" if precision == "fp64" else
+                {1: "k2_zy_plane", 2: "k2_zy_stream"}.get((res.get("tuning") or {}).get("mtxel_zy"),
+                                                            "k2_zy_stream / k2_zy_plane"))
+        r = {"bound": "alu", "kernel": kern + " (pair density + pruned z and y FFT passes)",
              "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
              "peak_source": (args.fp64_peak_label if precision == "fp64" else
                              "FP32 FFMA from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz")}

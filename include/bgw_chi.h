@@ -448,8 +448,10 @@ BGW_API bgw_status bgw_autotune(bgw_ctx ctx, int nq, const bgw_q *qs, int nfreq,
 
 /*
  * Stage timing with CUDA events recorded on the context stream around each
- * launch group.  Stages: 0 sphere->grid (bgw_wfn_upload), 1 matrix elements,
- * 2 pair weights, 3 contraction, 4 finalize, 5 operand split (mixed path).
+ * launch group.  Stages: 0 sphere->grid (bgw_wfn_upload), 1 matrix elements:
+ * pair density with the z and y passes, 2 pair weights, 3 contraction,
+ * 4 finalize, 5 operand split (mixed path), 6 matrix elements: x pass with
+ * the dielectric-sphere gather.
  *   bgw_profile(ctx, 1) clears the totals and starts recording; 0 stops.
  *   bgw_profile_read(ctx, ms, calls, kernels, n) fills the first n stages:
  *   device milliseconds, launch groups and kernels launched since the last

@@ -37,7 +37,7 @@ BGW_OPT_KCHUNK, BGW_OPT_PAIR_TILE_V, BGW_OPT_PAIR_TILE_C, BGW_OPT_GRID_SLOTS = 1
 BGW_OPT_TEST_DROP_LOAD, BGW_OPT_TEST_FAIL_ALLOC, BGW_OPT_K1_PATH, BGW_OPT_MTXEL_LANES = 5, 6, 7, 8
 BGW_OPT_DEFER_K1, BGW_OPT_COPY_AHEAD, BGW_OPT_OVERLAP, BGW_OPT_FP64_CONTRACTION = 9, 10, 11, 12
 BGW_OPT_MTXEL_ZY = 13
-STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split"]
+STAGES = ["wfn_to_grid", "mtxel", "weights", "contraction", "finalize", "operand_split", "mtxel_x"]
 
 
 class bgw_q(ctypes.Structure):

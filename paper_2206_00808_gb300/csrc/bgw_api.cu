@@ -204,7 +204,7 @@ struct bgw_ctx_s {
     // q-set was installed; replays of a captured graph are not counted)
     std::vector<int> kcount;
     // stage timing (bgw_profile)
-    static constexpr int kStages = 6;
+    static constexpr int kStages = 7;
     bool prof = false;
     struct Rec { int stage; long kernels; cudaEvent_t a, b; cudaStream_t s; };
     std::vector<Rec> recs;
@@ -235,6 +235,13 @@ struct bgw_ctx_s {
         if (idx < 0) return;
         recs[idx].kernels = kernels;
         cudaEventRecord(recs[idx].b, recs[idx].s);
+    }
+    // Drop the last record opened if it is still the last one (nothing launched in it).
+    void stage_cancel(int idx) {
+        if (idx < 0 || idx != (int)recs.size() - 1) return;
+        pool.push_back(recs.back().a);
+        pool.push_back(recs.back().b);
+        recs.pop_back();
     }
     // Fold finished records into the totals (blocks on the stream).
     cudaError_t drain() {
@@ -550,6 +557,23 @@ cudaError_t ensure_mtxel_scratch(bgw_ctx_s *c, const QState &s, long P) {
     return e;
 }
 
+// Profiling of the matrix-element kernels in two stages: 1 the pair density
+// with the z and y passes, 6 the x pass with the sphere gather.  The hook
+// closes the open record and opens one of the other stage at each x-pass mark.
+struct XProf {
+    bgw_ctx_s *c;
+    int rec;
+    bgw::XPassHook hook;
+    explicit XProf(bgw_ctx_s *ctx) : c(ctx), rec(ctx->stage_begin(1)), hook{&XProf::mark, this} {}
+    const bgw::XPassHook *get() const { return rec >= 0 ? &hook : nullptr; }
+    void finish() { c->stage_cancel(rec); }
+    static void mark(void *p, int begin, int kernels) {
+        auto *x = static_cast<XProf *>(p);
+        x->c->stage_end(x->rec, kernels);
+        x->rec = x->c->stage_begin(begin ? 6 : 1);
+    }
+};
+
 cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const int G0[3], int v0,
                          int nv, int c0, int nc, void *M, long ldm, int tv = 0, int tc = 0) {
     const bgw::Axes ax = mtxel_axes(c, s, G0);
@@ -561,12 +585,13 @@ cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const in
     const void *Uv = c->slot_ptr(sv, v0);
     const void *Uc = c->slot_ptr(sc, c->nv + c0);
     const int *gmap = static_cast<const int *>(s.gmap_dev.p);
-    const int rec = c->stage_begin(1);
+    XProf xp(c);
     cudaError_t e = (c->prec == BGW_FP64)
-        ? bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, 0, 0, c->mtxel_lanes)
+        ? bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, 0, 0, c->mtxel_lanes, 0,
+                         xp.get())
         : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, tv, tc, c->mtxel_lanes,
-                         c->mtxel_zy);
-    c->stage_end(rec, 3);
+                         c->mtxel_zy, xp.get());
+    xp.finish();
     return e;
 }
 
@@ -605,6 +630,7 @@ void compute_kmap(const bgw_ctx_s *c, QState &s) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 
 // Bytes of split operands the mixed contraction keeps for q-point s.
 size_t mixed_q_bytes(const bgw_ctx_s *c, const QState &s, int nfreq, int kchunk) {
@@ -908,13 +934,13 @@ bgw_status mtxel_into(bgw_ctx_s *c, const char *who, QState &s, int ik, int a0, 
     const int sb = ensure_grid(c, kp, ge);
     if (ge != cudaSuccess) return c->cuda_fail(ge, "grid");
     const int *gmap = static_cast<const int *>(c->gmap_tmp.p);
-    const int rec = c->stage_begin(1);
+    XProf xp(c);
     e = (c->prec == BGW_FP64)
             ? bgw::mtxel_f64(c->slot_ptr(sa, a0), c->slot_ptr(sb, b0), na, nb2, ax, gmap, s.ng, c->A.p, c->Bs.p, M,
-                             s.ng, c->st, 0, 0, c->mtxel_lanes)
+                             s.ng, c->st, 0, 0, c->mtxel_lanes, 0, xp.get())
             : bgw::mtxel_f32(c->slot_ptr(sa, a0), c->slot_ptr(sb, b0), na, nb2, ax, gmap, s.ng, c->A.p, c->Bs.p, M,
-                             s.ng, c->st, 0, 0, c->mtxel_lanes, c->mtxel_zy);
-    c->stage_end(rec, 3);
+                             s.ng, c->st, 0, 0, c->mtxel_lanes, c->mtxel_zy, xp.get());
+    xp.finish();
     if (e != cudaSuccess) return c->cuda_fail(e, "matrix-element kernels");
     return BGW_OK;
 }
@@ -1758,7 +1784,7 @@ bgw_status bgw_profile_read(bgw_ctx c, double *ms, long *calls, long *kernels, i
     DeviceGuard dg(c->device);
     c->err.clear();
     if (c->capturing) return c->fail(BGW_E_STATE, "profile_read: not allowed during graph capture");
-    if (n < 0 || n > bgw_ctx_s::kStages) return c->fail(BGW_E_ARG, "profile_read: n outside 0..6");
+    if (n < 0 || n > bgw_ctx_s::kStages) return c->fail(BGW_E_ARG, "profile_read: n outside 0..7");
     cudaError_t e = c->drain();
     if (e != cudaSuccess) return c->cuda_fail(e, "profile_read: stream");
     for (int i = 0; i < n; ++i) {

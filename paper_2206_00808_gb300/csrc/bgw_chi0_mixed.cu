@@ -238,16 +238,22 @@ __device__ __forceinline__ void lower_tile(int t, int &bi, int &bj) {
 // share A tiles in L2) are dealt round-robin to one CTA per SM.
 // Warp roles: warps 0-3 drain tensor memory (warp w owns TMEM lanes
 // 32w..32w+31 = tile rows), warp 4 allocates TMEM and issues the TMA loads,
-// warp 5 issues the MMAs.  The hi.hi products of each run of kSub K blocks go
-// to one of three TMEM slots in turn; when a run completes, warps 0-3 add
-// that slot into FP32 registers (round to nearest) and hand it back, so no
-// TMEM accumulator takes more than 4*kSub truncating adds of the large
-// products whatever K is.  The two cross products go to a fourth slot, read
-// once per item; the next item's MMAs start once it has been read.  Barrier
-// phases run on across items.
+// warp 5 issues the MMAs, warps 6-7 add finished tiles to the FP64
+// accumulator.  The hi.hi products of each run of kSub K blocks go to one of
+// three TMEM slots in turn; when a run completes, warps 0-3 add that slot
+// into FP32 registers (round to nearest) and hand it back, so no TMEM
+// accumulator takes more than 4*kSub truncating adds of the large products
+// whatever K is.  The two cross products go to a fourth slot, read once per
+// item; the next item's MMAs start once it has been read.  Warps 0-3 then
+// fold the 2x2 real blocks into a complex FP32 tile in shared memory and go
+// back to draining slots, while warps 6-7 add that tile into chi in FP64 (the
+// slow FP64 pipe stays off the path that frees the slots).  Barrier phases
+// run on across items.
 constexpr int kSub = 8;
 constexpr int kSlots = 3;
-constexpr int kGemmWarps = 6;
+constexpr int kGemmWarps = 8;
+constexpr int kFoldRow = kTileN / 2 + 1;                          // padded row of the complex tile
+constexpr int kFoldBytes = kTileM / 2 * kFoldRow * 8;             // 64 x 65 complex FP32
 
 struct GroupParams {
     CUtensorMap map[kMaxGroup];   // operand planes of each q-point
@@ -292,15 +298,18 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
     __shared__ __align__(8) uint64_t slot_free[kSlots];
     __shared__ __align__(8) uint64_t accum_bar;
     __shared__ __align__(8) uint64_t tmem_free;
+    __shared__ __align__(8) uint64_t fold_full;   // warps 0-3 wrote the complex tile
+    __shared__ __align__(8) uint64_t fold_free;   // warps 6-7 added it to chi
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int total = gp.first[gp.nq];
 
-    // 1024-byte aligned stage ring
+    // 1024-byte aligned stage ring, then the complex FP32 tile [64][kFoldRow]
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t ring = (raw + 1023u) & ~1023u;
+    float2 *ftile = reinterpret_cast<float2 *>(smem_raw + (ring - raw) + kStages * kStageBytes);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -313,6 +322,8 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
         }
         mbar_init(smem_u32(&accum_bar), 1);
         mbar_init(smem_u32(&tmem_free), 128);
+        mbar_init(smem_u32(&fold_full), 128);
+        mbar_init(smem_u32(&fold_free), 64);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -446,9 +457,40 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
             }
         }
         __syncwarp();
+    } else if (warp >= 6) {
+        // warps 6-7: add each finished complex tile to chi in FP64 (a warp
+        // takes 32 consecutive columns of a row: whole 512-byte segments)
+        const int tid = threadIdx.x - 6 * 32;
+        int nitem = 0;
+        for (int item = blockIdx.x; item < total; item += gridDim.x, ++nitem) {
+            const Item w = decode(gp, item, T::blockK);
+            bool ok = mbar_wait(smem_u32(&fold_full), (uint32_t)(nitem & 1));
+            if (!ok && lane == 0) atomicExch(err, kErrAccum);
+            ok = __all_sync(0xffffffffu, ok && !*(volatile int *)&abort_flag);
+            if (!ok) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            const int ng = gp.ng[w.q];
+            double2 *acc = gp.acc[w.q] + (long)w.j * ng * ng;
+            const int g0 = w.ti * (kTileM / 2), h0 = w.tj * (kTileN / 2);
+            for (int i = tid; i < (kTileM / 2) * (kTileN / 2); i += 64) {
+                const int gl = i / (kTileN / 2), hl = i % (kTileN / 2);
+                const int g = g0 + gl, h = h0 + hl;
+                if (g < ng && h < ng) {
+                    const float2 v = ftile[gl * kFoldRow + hl];
+                    double2 *o = acc + (long)g * ng + h;
+                    double2 t = *o;
+                    t.x += (double)v.x;
+                    t.y += (double)v.y;
+                    *o = t;
+                }
+            }
+            mbar_arrive(smem_u32(&fold_free));
+        }
     } else {
         // warps 0-3: promote finished hi.hi slots into FP32 registers, then
-        // fold the tile into complex chi and add it in FP64
+        // fold the 2x2 real blocks into the complex FP32 tile
         const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
         long gsub = 0;
         int nitem = 0;
@@ -500,41 +542,37 @@ k5_gemm(const __grid_constant__ GroupParams gp, int *__restrict__ err) {
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&tmem_free));   // the MMAs of the next item may start
-            const int ng = gp.ng[w.q];
-            double2 *acc = gp.acc[w.q];
-            const int a_row = w.ti * kTileM, b_row = w.tj * kTileN;
+            // the previous item's tile must have been added to chi
+            if (nitem > 0) {
+                bool fr = mbar_wait(smem_u32(&fold_free), (uint32_t)((nitem - 1) & 1));
+                if (!fr && lane == 0) atomicExch(err, kErrAccum);
+                fr = __all_sync(0xffffffffu, fr && !*(volatile int *)&abort_flag);
+                if (!fr) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+            }
             const int r = 32 * warp + lane;            // tile row
-            const int g = (a_row + r) >> 1;            // complex row
             const bool even = (r & 1) == 0;
+            float2 *frow = ftile + (r >> 1) * kFoldRow;
 #pragma unroll
             for (int c0 = 0; c0 < kTileN; c0 += 32) {
                 float other[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) other[i] = __shfl_xor_sync(0xffffffffu, racc[c0 + i], 1);
                 // rows 2g (re-row) and 2g+1 (im-row) now sit in both lanes of the pair;
-                // the even lane writes column pairs 0..7 of this chunk, the odd lane 8..15.
-                if (g < ng) {
+                // the even lane writes column pairs 0..7 of this chunk, the odd lane 8..15
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int cc = 2 * q;
-                        const float d00 = even ? racc[c0 + cc] : other[cc];           // D[2g][2g']
-                        const float d01 = even ? racc[c0 + cc + 1] : other[cc + 1];   // D[2g][2g'+1]
-                        const float d10 = even ? other[cc] : racc[c0 + cc];           // D[2g+1][2g']
-                        const float d11 = even ? other[cc + 1] : racc[c0 + cc + 1];   // D[2g+1][2g'+1]
-                        const int gp2 = (b_row + c0 + cc) >> 1;
-                        if ((q < 8) == even && gp2 < ng) {
-                            // the 2x2 fold in FP32 (one more rounding of 2^-24),
-                            // then two conversions and two FP64 adds: half the
-                            // work of the slow FP64 pipe of four of each
-                            double2 *o = acc + ((long)w.j * ng + g) * ng + gp2;
-                            double2 t = *o;
-                            t.x += (double)(d00 + d11);
-                            t.y += (double)(d01 - d10);
-                            *o = t;
-                        }
-                    }
+                for (int q = 0; q < 16; ++q) {
+                    const int cc = 2 * q;
+                    const float d00 = even ? racc[c0 + cc] : other[cc];           // D[2g][2g']
+                    const float d01 = even ? racc[c0 + cc + 1] : other[cc + 1];   // D[2g][2g'+1]
+                    const float d10 = even ? other[cc] : racc[c0 + cc];           // D[2g+1][2g']
+                    const float d11 = even ? other[cc + 1] : racc[c0 + cc + 1];   // D[2g+1][2g'+1]
+                    if ((q < 8) == even) frow[(c0 + cc) >> 1] = make_float2(d00 + d11, d01 - d10);
                 }
             }
+            mbar_arrive(smem_u32(&fold_full));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -586,7 +624,7 @@ cudaError_t split_launch(const void *M, int P, int ng, const double *w, int nfre
 
 template <int F>
 cudaError_t gemm_launch(const GroupParams &gp, int items, int sm_count, cudaStream_t st, int *err) {
-    const int smem = Fmt<F>::stages * Fmt<F>::stageBytes + 1024;
+    const int smem = Fmt<F>::stages * Fmt<F>::stageBytes + 1024 + kFoldBytes;
     cudaError_t e = cudaFuncSetAttribute(k5_gemm<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int grid = items < sm_count ? items : sm_count;

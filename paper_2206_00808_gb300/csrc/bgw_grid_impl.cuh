@@ -1360,9 +1360,21 @@ static bool use_stream(const Axes &a) {
     return a.w[2] <= kZW;
 }
 
+// Marks around one x-pass launch group for the profiling hook.
+struct XMark {
+    const XPassHook *h;
+    XMark(const XPassHook *hook, int zy_kernels) : h(hook) {
+        if (h) h->fn(h->ctx, 1, zy_kernels);
+    }
+    ~XMark() {
+        if (h) h->fn(h->ctx, 0, 1);
+    }
+};
+
 static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const Axes &a,
                                const int *gmap, int ng, C *Ap, C *Bp, C *Mp, long ldm,
-                               cudaStream_t st, int tv_req, int tc_req, int lanes, int zy) {
+                               cudaStream_t st, int tv_req, int tc_req, int lanes, int zy,
+                               const XPassHook *hook) {
     const long P = (long)nv * nc;
     if (oct_len(a) && (lanes == 8 || (lanes == 0 && use_coop(a) && use_oct(a)))) {
         // eight lanes per line: fused z+y, then the x pass
@@ -1379,6 +1391,7 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         });
         const long lines = (long)a.w[1] * a.w[2];
         const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
+        XMark xm(hook, 1);
         if (mtxel_scatter_mode(a, sizeof(C))) {
             const long groups = P * lines;
             BGW_FOR_EACH_OCT_LEN(a.n[0], (k2_xpass_scatter_oct<N><<<(unsigned)((groups + 31) / 32), kOctThreads,
@@ -1431,6 +1444,7 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         });
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        XMark xm(hook, 1);
         return xpass(Bp, P, a, gmap, ng, Mp, ldm, st);
     }
     int TV = 0, TC = 0;
@@ -1452,6 +1466,7 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
                                           Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
         const long lines = (long)a.w[1] * a.w[2];
         const T scale = (T)(1.0 / ((double)a.n[0] * a.n[1] * a.n[2]));
+        XMark xm(hook, 2);
         BGW_FOR_EACH_COOP_LEN(a.n[0], (k2_xpass_scatter_c4<N><<<quads_for(P * lines), kLineThreads, 0, st>>>(
                                           Bp, P, a.w[0], a.w[1], a.w[2], a.s[0], gmap + ng, scale, Mp, ldm)));
         return cudaGetLastError();
@@ -1481,12 +1496,13 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         BGW_FOR_EACH_LEN(a.n[1], (k2_ypass<N><<<blocks_for(npx * a.w[2]), kLineThreads, 0, st>>>(
                                      Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
     }
+    XMark xm(hook, TV > 0 ? 1 : 2);
     return xpass(Bp, P, a, gmap, ng, Mp, ldm, st);
 }
 
 static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                          const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                         cudaStream_t st, int tv_req, int tc_req, int lanes, int zy) {
+                         cudaStream_t st, int tv_req, int tc_req, int lanes, int zy, const XPassHook *hook) {
     if ((long)nv * nc == 0) return cudaSuccess;
     const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
     C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
@@ -1495,7 +1511,7 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
     for (int vb0 = 0; vb0 < nv; vb0 += VB) {
         const int nvb = nv - vb0 < VB ? nv - vb0 : VB;
         cudaError_t e = mtxel_batch(uv + (long)vb0 * 2 * vol, uc, nvb, nc, a, gmap, ng, Ap, Bp,
-                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req, lanes, zy);
+                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req, lanes, zy, hook);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -65,12 +65,21 @@ cudaError_t wfn_to_grid_batch_f32(const K1Job *jobs, int n, int B, cudaStream_t 
 // zy (FP32): 0 automatic (the streamed z + y kernel where it applies, unless a
 // pair tile tv x tc is given), 1 the plane kernel with the pair tile tv x tc,
 // 2 streamed where it applies.
+// hook (profiling, may be NULL): fn(ctx, 1, n) just before each x-pass launch
+// group (n = kernels launched since the previous mark) and fn(ctx, 0, n)
+// right after it.
+struct XPassHook {
+    void (*fn)(void *ctx, int begin, int kernels);
+    void *ctx;
+};
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0);
+                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0,
+                      const XPassHook *hook = nullptr);
 cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0);
+                      cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0,
+                      const XPassHook *hook = nullptr);
 // The last forward pass gathers the kept w0*w1*w2 cube through shared memory
 // when it is small; a larger cube is written straight to M through an
 // inverse map (cube cell -> G index or -1) stored in the map buffer right

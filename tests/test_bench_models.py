@@ -15,7 +15,8 @@ def test_byte_model_counts_each_grid_and_coefficient_once():
         coeff = sum(p.nbands * 2 * len(g) * 16 for g in p.gvec)
         assert bm["wfn_to_grid"] == coeff + p.nk * p.nbands * 2 * vol * csize
         _, geps, nc = p.qs[0]
-        assert bm["mtxel"] == p.nk * (p.nv + nc) * 2 * vol * csize + p.nk * p.nv * nc * len(geps) * csize
+        assert bm["mtxel"] == p.nk * (p.nv + nc) * 2 * vol * csize          # grids read by the z + y kernel
+        assert bm["mtxel_x"] == p.nk * p.nv * nc * len(geps) * csize        # M written by the x pass
 
 
 def test_flop_model_scales_with_pairs_and_frequencies():
@@ -24,7 +25,14 @@ def test_flop_model_scales_with_pairs_and_frequencies():
     a, b = bench.flop_model(p), bench.flop_model(q)
     assert np.isclose(b["contraction"], 3 * a["contraction"])
     assert np.isclose(b["mtxel"], a["mtxel"]) and np.isclose(b["wfn_to_grid"], a["wfn_to_grid"])
-    assert np.isclose(a["total"], a["wfn_to_grid"] + a["mtxel"] + a["contraction"])
+    assert np.isclose(a["total"], a["wfn_to_grid"] + a["mtxel"] + a["mtxel_x"] + a["contraction"])
+    # x lines: w_y w_z per pair against N^2 + N w_y lines of the z + y kernel
+    n = p.box[0]
+    w = p.qs[0][1].max(0) - p.qs[0][1].min(0) + 1
+    fft = 5 * n * np.log2(n)
+    pairs = p.nk * p.nv * p.qs[0][2]
+    assert np.isclose(a["mtxel_x"], pairs * fft * w[1] * w[2])
+    assert np.isclose(a["mtxel"], pairs * (fft * (n * n + n * w[1]) + 16 * n ** 3))
     ng = len(p.qs[0][1])
     assert np.isclose(a["contraction"], 8.0 * p.nk * p.nv * p.qs[0][2] * ng * (ng + 1) / 2)
 

@@ -80,3 +80,24 @@ def test_autotune_keeps_results_and_uses_cache(gpu_lib, case, tmp_path):
         ctx2.close()
     lines = open(cache).read().strip().splitlines()
     assert len(lines) == 2 and all("|" in l for l in lines)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_profile_splits_the_matrix_element_stages(gpu_lib, prec):
+    """bgw_profile times the pair density + z + y kernels (stage 1) apart from
+    the x pass with the sphere gather (stage 6): both non-empty, one x-pass
+    kernel per launch group and at least one group per k-point."""
+    p = syn.make_problem("si18_qx")
+    ctx = gpu_lib.Chi0Context(p, prec)
+    ctx.upload()
+    ctx.accumulate()
+    ctx.reset()
+    gpu_lib.bgw_profile(ctx.ctx, True)
+    ctx.accumulate()
+    prof = gpu_lib.bgw_profile_read(ctx.ctx)
+    gpu_lib.bgw_profile(ctx.ctx, False)
+    ctx.close()
+    zy, x = prof["mtxel"], prof["mtxel_x"]
+    assert zy[0] > 0 and x[0] > 0
+    assert x[2] == x[1] >= p.nk
+    assert zy[2] >= zy[1] >= p.nk
