@@ -156,8 +156,11 @@ k2_zpass(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, lon
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P * plane) return;
     const long xy = t % plane;
-    const long p = t / plane;
-    const long v = p / nc, c = p % nc;
+    // pairs run conduction-major, so each conduction grid is read by all the
+    // batch's valence bands while it is in L2; A keeps the pair order v * nc + c
+    const long po = t / plane, nvb = P / nc;
+    const long c = po / nvb, v = po % nvb;
+    const long p = v * nc + c;
     const long vol = plane * N;
     const C *v0 = Uv + (2 * v) * vol + xy * N;
     const C *c0 = Uc + (2 * c) * vol + xy * N;
@@ -170,7 +173,7 @@ k2_zpass(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, lon
 #pragma unroll
     for (int f = 0; f < N; ++f) {
         const int j = rot<N>(f, ns);
-        if (j < w2) A[t * w2 + j] = a[f];
+        if (j < w2) A[(p * plane + xy) * w2 + j] = a[f];
     }
 }
 
@@ -287,8 +290,9 @@ k2_zpass_c4(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, 
     const bool valid = line < P * plane;
     if (!valid) line = 0;
     const long xy = line % plane;
-    const long p = line / plane;
-    const long v = p / nc, c = p % nc;
+    const long po = line / plane, nvb = P / nc;       // conduction-major, as k2_zpass
+    const long c = po / nvb, v = po % nvb;
+    const long p = v * nc + c;
     const long vol = plane * N;
     const C *v0 = Uv + (2 * v) * vol + xy * N;
     const C *c0 = Uc + (2 * c) * vol + xy * N;
@@ -306,7 +310,7 @@ k2_zpass_c4(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, 
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             const int jj = rot<N>(t * Q + j + M * k1, ns);
-            if (jj < w2) A[line * w2 + jj] = out[k1][j];
+            if (jj < w2) A[(p * plane + xy) * w2 + jj] = out[k1][j];
         }
 }
 
