@@ -923,6 +923,21 @@ def format_legs(B, torch, p, args, stream, dev_in, ks, head, chi64):
     return out
 
 
+def zy_kernel_name(p, precision, zy):
+    """The kernel of the pair density + z + y stage for this box and choice
+    (the library's rule: FP64 separate passes; eight lanes per line on cubic
+    48^3/64^3; else the streamed kernel on even boxes up to 32 unless the
+    plane kernel was chosen)."""
+    n = p.box[1]
+    if precision == "fp64":
+        return "k2_zpass + k2_ypass (FP64)"
+    if p.box[0] == p.box[1] == p.box[2] and n in (48, 64):
+        return "k2_zy_oct"
+    if zy != 1 and n % 2 == 0 and n <= 32 and n not in (22, 26, 28):
+        return "k2_zy_stream"
+    return "k2_zy_plane"
+
+
 def head_roofline(p, res, precision, args, steps):
     """Roofline of the dominant kernel of the headline: the contraction
     GEMM or the pair density + z + y kernel of the matrix elements (their x
@@ -954,9 +969,7 @@ def head_roofline(p, res, precision, args, steps):
     else:
         ach = fl["mtxel"] / (mt * 1e-3) / 1e12
         pk = args.fp64_peak if precision == "fp64" else FP32_PEAK_TFLOPS
-        kern = ("k2_zpass + k2_ypass (FP64)" if precision == "fp64" else
-                {1: "k2_zy_plane", 2: "k2_zy_stream"}.get((res.get("tuning") or {}).get("mtxel_zy"),
-                                                            "k2_zy_stream / k2_zy_plane"))
+        kern = zy_kernel_name(p, precision, (res.get("tuning") or {}).get("mtxel_zy", args.mtxel_zy))
         r = {"bound": "alu", "kernel": kern + " (pair density + pruned z and y FFT passes)",
              "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
              "peak_source": (args.fp64_peak_label if precision == "fp64" else

@@ -66,3 +66,12 @@ def test_oracle_sample_sizes():
     p = syn.make_problem("gasb32", coeff_on=None)
     assert 1 <= bench.sample_nc(p) < p.nc
     assert bench.sample_nc(syn.make_problem("si18_qx")) == 24
+
+
+def test_zy_kernel_names_follow_the_library_rule():
+    g = syn.make_problem("gasb32", coeff_on=None)
+    assert bench.zy_kernel_name(g, "mixed", 0) == "k2_zy_stream"
+    assert bench.zy_kernel_name(g, "mixed", 1) == "k2_zy_plane"
+    assert bench.zy_kernel_name(g, "fp64", 2).startswith("k2_zpass")
+    b = syn.make_bi2se3_problem(kgrid=(1, 1, 1), nv=2, nc=2, nfreq=1, device=None)
+    assert bench.zy_kernel_name(b, "mixed", 2) == "k2_zy_oct"
