@@ -882,7 +882,31 @@ __host__ __device__ constexpr size_t stream_smem() {
     return sizeof(cpx<float>) * ((size_t)(SV + 2 * SC) * 2 * N * plane_row<N>() + (size_t)2 * SV * SC * N * kZW);
 }
 
-template <int N>
+// Kept outputs of a forward line whose cube starts at s: f = (s + j) mod N,
+// j < w.  WIN: every such f lies within kWin of 0, so only those 2 kWin + 1
+// registers are stored and the compiler drops the butterflies that feed no
+// kept output.
+constexpr int kWin = 8;
+
+template <int N, bool WIN>
+__device__ __forceinline__ void store_kept(const C (&a)[N], C *o, int stride, int ns, int w) {
+    if constexpr (WIN) {
+#pragma unroll
+        for (int i = 0; i < 2 * kWin + 1; ++i) {
+            const int f = i <= kWin ? i : N - (2 * kWin + 1) + i;
+            const int j = rot<N>(f, ns);
+            if (j < w) o[j * stride] = a[f];
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < N; ++f) {
+            const int j = rot<N>(f, ns);
+            if (j < w) o[j * stride] = a[f];
+        }
+    }
+}
+
+template <int N, bool WIN>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int CC, int w1, int w2, int s1,
              int s2, C *__restrict__ Bs) {
@@ -902,10 +926,12 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
     const int tv = min(kStreamV, nv - v0), cend = min(nc, cbeg + CC);
     const long vol = (long)n0 * NN;
     const int ns1 = N - s1, ns2 = N - s2;
-    // copies of band planes (both spin components of x-plane x) into rows of RS
-    auto copy_planes = [&](C *dst, const C *src, long band0, int nb) {
+    // copies of band planes (both spin components of x-plane x) into rows of
+    // RS by threads [t0, t0 + nt): all threads for the prologue, the z-line
+    // threads in the phases (the y lines are the longer role)
+    auto copy_planes = [&](C *dst, const C *src, long band0, int nb, int t0, int nt) {
         const int total = nb * 2 * CH;
-        for (int i = threadIdx.x; i < total; i += kStreamThreads) {
+        for (int i = threadIdx.x - t0; i < total; i += nt) {
             const int ba = i / CH, ch = i % CH;           // ba = band * 2 + alpha
             const int yz = 2 * ch;
             const C *g = src + ((band0 + (ba >> 1)) * 2 + (ba & 1)) * vol + (long)x * NN + yz;
@@ -914,15 +940,15 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
         }
     };
     const int ng = (cend - cbeg + kStreamC - 1) / kStreamC;
-    copy_planes(V, Uv, v0, tv);
-    if (ng > 0) copy_planes(Cb0, Uc, cbeg, min(kStreamC, cend - cbeg));
+    copy_planes(V, Uv, v0, tv, 0, kStreamThreads);
+    if (ng > 0) copy_planes(Cb0, Uc, cbeg, min(kStreamC, cend - cbeg), 0, kStreamThreads);
     __pipeline_commit();
     __pipeline_wait_prior(0);
     __syncthreads();
     for (int k = 0; k <= ng; ++k) {
-        if (k + 1 < ng) {
+        if (k + 1 < ng && threadIdx.x < kZThreads) {
             const int c1 = cbeg + (k + 1) * kStreamC;
-            copy_planes(Cb0 + ((k + 1) & 1) * (kStreamC * 2 * PS), Uc, c1, min(kStreamC, cend - c1));
+            copy_planes(Cb0 + ((k + 1) & 1) * (kStreamC * 2 * PS), Uc, c1, min(kStreamC, cend - c1), 0, kZThreads);
         }
         __pipeline_commit();
         if (threadIdx.x < kZThreads) {
@@ -944,12 +970,7 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
                     a[2 * z + 1] = rho2(C{va.z, va.w}, C{ca.z, ca.w}, C{vb.z, vb.w}, C{cb.z, cb.w});
                 }
                 fft_line<T, -1, N>(a);
-                C *zo = Z0 + (k & 1) * ZS + ((long)pr * N + y) * w2;
-#pragma unroll
-                for (int f = 0; f < N; ++f) {
-                    const int j = rot<N>(f, ns2);
-                    if (j < w2) zo[j] = a[f];
-                }
+                store_kept<N, WIN>(a, Z0 + (k & 1) * ZS + ((long)pr * N + y) * w2, 1, ns2, w2);
             }
         } else if (k >= 1) {
             // y lines of group k - 1; keep w1 outputs -> Bs[p][x][jy][jz]
@@ -965,12 +986,7 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
                 for (int yy = 0; yy < N; ++yy) b[yy] = zi[yy * w2];
                 fft_line<T, -1, N>(b);
                 const long p = (long)(v0 + v) * nc + (c0 + c);
-                C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
-#pragma unroll
-                for (int f = 0; f < N; ++f) {
-                    const int j = rot<N>(f, ns1);
-                    if (j < w1) bo[j * w2] = b[f];
-                }
+                store_kept<N, WIN>(b, Bs + ((p * n0 + x) * w1) * w2 + jz, w2, ns1, w1);
             }
         }
         __pipeline_wait_prior(0);        // group k + 1 has landed
@@ -1358,6 +1374,16 @@ static cudaError_t xpass(const C *Bp, long P, const Axes &a, const int *gmap, in
         default: return cudaErrorInvalidValue;                                         \
     }
 
+// Whether every kept output of the z and y lines lies within kWin of 0.
+static bool kept_in_window(const Axes &a) {
+    for (int ax = 1; ax <= 2; ++ax)
+        for (int j = 0; j < a.w[ax]; ++j) {
+            const int f = (a.s[ax] + j) % a.n[ax];
+            if (f > kWin && f < a.n[ax] - kWin) return false;
+        }
+    return true;
+}
+
 static bool use_stream(const Axes &a) {
     const int n = a.n[1];
     if (!use_plane_kernels(a) || n % 2 != 0 || n > 32 || n == 28 || n == 26 || n == 22) return false;
@@ -1440,11 +1466,15 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         if (CC < kStreamC) CC = kStreamC;
         dim3 grid((unsigned)a.n[0], (unsigned)nvg, (unsigned)((nc + CC - 1) / CC));
         cudaError_t e = cudaSuccess;
+        const bool win = kept_in_window(a);
         BGW_FOR_EACH_STREAM_LEN(a.n[1], {
             const size_t ss = stream_smem<N>();
-            e = cudaFuncSetAttribute(k2_zy_stream<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+            auto kern = k2_zy_stream<N, false>;
+            if constexpr (N > 2 * kWin + 1)
+                if (win) kern = k2_zy_stream<N, true>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
             if (e != cudaSuccess) return e;
-            k2_zy_stream<N><<<grid, kStreamThreads, ss, st>>>(uv, uc, nv, nc, CC, a.w[1], a.w[2], a.s[1], a.s[2], Bp);
+            kern<<<grid, kStreamThreads, ss, st>>>(uv, uc, nv, nc, CC, a.w[1], a.w[2], a.s[1], a.s[2], Bp);
         });
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
