@@ -76,6 +76,31 @@ __device__ __forceinline__ int rot(int f, int ns) {
     return j >= N ? j - N : j;
 }
 
+// Kept outputs of a forward line whose cube starts at s: f = (s + j) mod N,
+// j < w.  WIN: every such f lies within kWin of 0, so only those 2 kWin + 1
+// registers are stored and the compiler drops the butterflies that feed no
+// kept output.
+constexpr int kWin = 8;
+
+template <int N, bool WIN>
+__device__ __forceinline__ void store_kept(const C (&a)[N], C *o, int stride, int ns, int w) {
+    if constexpr (WIN) {
+#pragma unroll
+        for (int i = 0; i < 2 * kWin + 1; ++i) {
+            const int f = i <= kWin ? i : N - (2 * kWin + 1) + i;
+            const int j = rot<N>(f, ns);
+            if (j < w) o[j * stride] = a[f];
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < N; ++f) {
+            const int j = rot<N>(f, ns);
+            if (j < w) o[j * stride] = a[f];
+        }
+    }
+}
+
+
 // ------------------------------------------------------ sphere -> grid --
 // Pass x: one thread per (band component b, y', z') line of the cube.
 template <int N>
@@ -149,7 +174,7 @@ k1_zpass(const C *__restrict__ R, long nbxy, int w2, int s2, C *__restrict__ U) 
 // ------------------------------------------------ pair density -> M --
 // Pass z: one thread per (pair p, x, y): rho(z) = sum_alpha conj(u_v) u_c,
 // forward transform along z, keep outputs s2 .. s2+w2-1.
-template <int N>
+template <int N, bool WIN>
 __global__ void __launch_bounds__(kLineThreads)
 k2_zpass(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, long plane, int w2,
          int s2, C *__restrict__ A) {
@@ -169,16 +194,11 @@ k2_zpass(const C *__restrict__ Uv, const C *__restrict__ Uc, int nc, long P, lon
     for (int z = 0; z < N; ++z)
         a[z] = rho2(v0[z], c0[z], v0[vol + z], c0[vol + z]);
     fft_line<T, -1, N>(a);
-    const int ns = N - s2;
-#pragma unroll
-    for (int f = 0; f < N; ++f) {
-        const int j = rot<N>(f, ns);
-        if (j < w2) A[(p * plane + xy) * w2 + j] = a[f];
-    }
+    store_kept<N, WIN>(a, A + (p * plane + xy) * w2, 1, N - s2, w2);
 }
 
 // Pass y: one thread per (p, x, j2); keep outputs s1 .. s1+w1-1.
-template <int N>
+template <int N, bool WIN>
 __global__ void __launch_bounds__(kLineThreads)
 k2_ypass(const C *__restrict__ A, long npx, int w1, int w2, int s1, C *__restrict__ Bs) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,12 +209,7 @@ k2_ypass(const C *__restrict__ A, long npx, int w1, int w2, int s1, C *__restric
 #pragma unroll
     for (int y = 0; y < N; ++y) a[y] = A[(px * N + y) * w2 + jz];
     fft_line<T, -1, N>(a);
-    const int ns = N - s1;
-#pragma unroll
-    for (int f = 0; f < N; ++f) {
-        const int j = rot<N>(f, ns);
-        if (j < w1) Bs[(px * w1 + j) * w2 + jz] = a[f];
-    }
+    store_kept<N, WIN>(a, Bs + px * w1 * w2 + jz, w2, N - s1, w1);
 }
 
 // Pass x + gather: one block per PP pairs (so that the w1*w2 x lines of
@@ -202,7 +217,7 @@ k2_ypass(const C *__restrict__ A, long npx, int w1, int w2, int s1, C *__restric
 // memory, then M[p][g] = cube[gmap[g]] / N^3.
 constexpr int kGatherThreads = 256;
 
-template <int N>
+template <int N, bool WIN>
 __global__ void __launch_bounds__(kGatherThreads)
 k2_xpass_gather(const C *__restrict__ Bs, long P, int PP, int w0, int w1, int w2, int s0,
                 const int *__restrict__ gmap, int ng, T scale, C *__restrict__ M, long ldm) {
@@ -219,12 +234,7 @@ k2_xpass_gather(const C *__restrict__ Bs, long P, int PP, int w0, int w1, int w2
 #pragma unroll
         for (int x = 0; x < N; ++x) a[x] = bi[x * lines];
         fft_line<T, -1, N>(a);
-        C *co = cube + pp * csz + ll;
-#pragma unroll
-        for (int f = 0; f < N; ++f) {
-            const int j = rot<N>(f, ns);
-            if (j < w0) co[j * lines] = a[f];
-        }
+        store_kept<N, WIN>(a, cube + pp * csz + ll, lines, ns, w0);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < np * ng; i += kGatherThreads) {
@@ -882,30 +892,6 @@ __host__ __device__ constexpr size_t stream_smem() {
     return sizeof(cpx<float>) * ((size_t)(SV + 2 * SC) * 2 * N * plane_row<N>() + (size_t)2 * SV * SC * N * kZW);
 }
 
-// Kept outputs of a forward line whose cube starts at s: f = (s + j) mod N,
-// j < w.  WIN: every such f lies within kWin of 0, so only those 2 kWin + 1
-// registers are stored and the compiler drops the butterflies that feed no
-// kept output.
-constexpr int kWin = 8;
-
-template <int N, bool WIN>
-__device__ __forceinline__ void store_kept(const C (&a)[N], C *o, int stride, int ns, int w) {
-    if constexpr (WIN) {
-#pragma unroll
-        for (int i = 0; i < 2 * kWin + 1; ++i) {
-            const int f = i <= kWin ? i : N - (2 * kWin + 1) + i;
-            const int j = rot<N>(f, ns);
-            if (j < w) o[j * stride] = a[f];
-        }
-    } else {
-#pragma unroll
-        for (int f = 0; f < N; ++f) {
-            const int j = rot<N>(f, ns);
-            if (j < w) o[j * stride] = a[f];
-        }
-    }
-}
-
 template <int N, bool WIN>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int CC, int w1, int w2, int s1,
@@ -1337,6 +1323,15 @@ static int plane_tile_list(int nv, int nc, const Axes &a, int *TV, int *TC, int 
 
 // The x pass of the one-lane-per-line paths: gather through shared memory
 // when the kept cube is small, else scatter through the inverse map.
+// Whether every kept output along axis ax lies within kWin of 0.
+static bool kept_in_window(const Axes &a, int ax) {
+    for (int j = 0; j < a.w[ax]; ++j) {
+        const int f = (a.s[ax] + j) % a.n[ax];
+        if (f > kWin && f < a.n[ax] - kWin) return false;
+    }
+    return true;
+}
+
 static cudaError_t xpass(const C *Bp, long P, const Axes &a, const int *gmap, int ng, C *Mp, long ldm,
                          cudaStream_t st) {
     const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
@@ -1350,12 +1345,14 @@ static cudaError_t xpass(const C *Bp, long P, const Axes &a, const int *gmap, in
     }
     BGW_FOR_EACH_LEN(a.n[0], {
         const int PP = gather_pairs(a, P);
+        auto kern = k2_xpass_gather<N, false>;
+        if constexpr (N > 2 * kWin + 1)
+            if (kept_in_window(a, 0)) kern = k2_xpass_gather<N, true>;
         if (smem * PP > 48 * 1024) {
-            e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(smem * PP));
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem * PP));
             if (e != cudaSuccess) return e;
         }
-        k2_xpass_gather<N><<<(unsigned)((P + PP - 1) / PP), kGatherThreads, smem * PP, st>>>(
+        kern<<<(unsigned)((P + PP - 1) / PP), kGatherThreads, smem * PP, st>>>(
             Bp, P, PP, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
     });
     return cudaGetLastError();
@@ -1374,15 +1371,6 @@ static cudaError_t xpass(const C *Bp, long P, const Axes &a, const int *gmap, in
         default: return cudaErrorInvalidValue;                                         \
     }
 
-// Whether every kept output of the z and y lines lies within kWin of 0.
-static bool kept_in_window(const Axes &a) {
-    for (int ax = 1; ax <= 2; ++ax)
-        for (int j = 0; j < a.w[ax]; ++j) {
-            const int f = (a.s[ax] + j) % a.n[ax];
-            if (f > kWin && f < a.n[ax] - kWin) return false;
-        }
-    return true;
-}
 
 static bool use_stream(const Axes &a) {
     const int n = a.n[1];
@@ -1432,12 +1420,14 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         const size_t smem = sizeof(C) * (size_t)a.w[0] * a.w[1] * a.w[2];
         BGW_FOR_EACH_LEN(a.n[0], {
             const int PP = gather_pairs(a, P);
+            auto kern = k2_xpass_gather<N, false>;
+            if constexpr (N > 2 * kWin + 1)
+                if (kept_in_window(a, 0)) kern = k2_xpass_gather<N, true>;
             if (smem * PP > 48 * 1024) {
-                e = cudaFuncSetAttribute(k2_xpass_gather<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(smem * PP));
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem * PP));
                 if (e != cudaSuccess) return e;
             }
-            k2_xpass_gather<N><<<(unsigned)((P + PP - 1) / PP), kGatherThreads, smem * PP, st>>>(
+            kern<<<(unsigned)((P + PP - 1) / PP), kGatherThreads, smem * PP, st>>>(
                 Bp, P, PP, a.w[0], a.w[1], a.w[2], a.s[0], gmap, ng, scale, Mp, ldm);
         });
         return cudaGetLastError();
@@ -1466,7 +1456,7 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         if (CC < kStreamC) CC = kStreamC;
         dim3 grid((unsigned)a.n[0], (unsigned)nvg, (unsigned)((nc + CC - 1) / CC));
         cudaError_t e = cudaSuccess;
-        const bool win = kept_in_window(a);
+        const bool win = kept_in_window(a, 1) && kept_in_window(a, 2);
         BGW_FOR_EACH_STREAM_LEN(a.n[1], {
             const size_t ss = stream_smem<N>();
             auto kern = k2_zy_stream<N, false>;
@@ -1524,11 +1514,20 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         });
     } else {
         const long plane = (long)a.n[0] * a.n[1];
-        BGW_FOR_EACH_LEN(a.n[2], (k2_zpass<N><<<blocks_for(P * plane), kLineThreads, 0, st>>>(
-                                     uv, uc, nc, P, plane, a.w[2], a.s[2], Ap)));
+        const bool wz = kept_in_window(a, 2), wy = kept_in_window(a, 1);
+        BGW_FOR_EACH_LEN(a.n[2], {
+            auto kern = k2_zpass<N, false>;
+            if constexpr (N > 2 * kWin + 1)
+                if (wz) kern = k2_zpass<N, true>;
+            kern<<<blocks_for(P * plane), kLineThreads, 0, st>>>(uv, uc, nc, P, plane, a.w[2], a.s[2], Ap);
+        });
         const long npx = P * a.n[0];
-        BGW_FOR_EACH_LEN(a.n[1], (k2_ypass<N><<<blocks_for(npx * a.w[2]), kLineThreads, 0, st>>>(
-                                     Ap, npx, a.w[1], a.w[2], a.s[1], Bp)));
+        BGW_FOR_EACH_LEN(a.n[1], {
+            auto kern = k2_ypass<N, false>;
+            if constexpr (N > 2 * kWin + 1)
+                if (wy) kern = k2_ypass<N, true>;
+            kern<<<blocks_for(npx * a.w[2]), kLineThreads, 0, st>>>(Ap, npx, a.w[1], a.w[2], a.s[1], Bp);
+        });
     }
     XMark xm(hook, TV > 0 ? 1 : 2);
     return xpass(Bp, P, a, gmap, ng, Mp, ldm, st);
