@@ -759,7 +759,7 @@ __host__ __device__ constexpr int plane_row() { return N % 2 == 0 ? N + 2 : N + 
 
 // Pair density + z pass + y pass for one x-plane and a tile of tv x tc pairs.
 // Shared: planes[(tv+tc)][2][N][N+1], then Z[tv*tc][N][w2].
-template <int N, int MINB, int THREADS>
+template <int N, int MINB, int THREADS, bool WIN = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int TV, int TC,
             int w1, int w2, int s1, int s2, C *__restrict__ Bs) {
@@ -837,12 +837,7 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
             for (int z = 0; z < N; ++z) a[z] = rho2(pv[z], pc[z], pv[PS + z], pc[PS + z]);
         }
         fft_line<T, -1, N>(a);
-        C *zo = Z + ((long)pr * N + y) * w2;
-#pragma unroll
-        for (int f = 0; f < N; ++f) {
-            const int j = rot<N>(f, ns2);
-            if (j < w2) zo[j] = a[f];
-        }
+        store_kept<N, WIN>(a, Z + ((long)pr * N + y) * w2, 1, ns2, w2);
     }
     __syncthreads();
     // 3. y lines over the kept z outputs; keep w1 outputs -> Bs[p][x][jy][jz]
@@ -855,12 +850,7 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
         for (int y = 0; y < N; ++y) a[y] = zi[y * w2];
         fft_line<T, -1, N>(a);
         const long p = (long)(v0 + v) * nc + (c0 + c);
-        C *bo = Bs + ((p * n0 + x) * w1) * w2 + jz;
-#pragma unroll
-        for (int f = 0; f < N; ++f) {
-            const int j = rot<N>(f, ns1);
-            if (j < w1) bo[j * w2] = a[f];
-        }
+        store_kept<N, WIN>(a, Bs + ((p * n0 + x) * w1) * w2 + jz, w2, ns1, w1);
     }
 }
 
@@ -1500,11 +1490,20 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         cudaError_t e = cudaSuccess;
         const bool three = plane_three_per_sm(a, psmem);
         const bool large = psmem > kPlaneSmemMax;
+        const bool win = kept_in_window(a, 1) && kept_in_window(a, 2);
         BGW_FOR_EACH_LEN(a.n[1], {
             auto kern = k2_zy_plane<N, 2, kPlaneThreads>;
             if constexpr (N <= 30)
                 if (three) kern = k2_zy_plane<N, 3, kPlaneThreads>;
             if (large) kern = k2_zy_plane<N, 1, kPlaneThreadsLarge>;
+            if constexpr (N > 2 * kWin + 1 && sizeof(T) == 4) {   // the plane kernels run in FP32 only
+                if (win) {
+                    kern = k2_zy_plane<N, 2, kPlaneThreads, true>;
+                    if constexpr (N <= 30)
+                        if (three) kern = k2_zy_plane<N, 3, kPlaneThreads, true>;
+                    if (large) kern = k2_zy_plane<N, 1, kPlaneThreadsLarge, true>;
+                }
+            }
             if (psmem > 48 * 1024) {
                 e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
                 if (e != cudaSuccess) return e;
