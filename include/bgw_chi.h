@@ -417,11 +417,14 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        BGW_E_NOMEM; 0 switches it off.  The environment
  *                        variable BGW_FAULT=oom@n, read by bgw_create, does the
  *                        same.
- *   BGW_OPT_TEST_DROP_LOAD  for failure-handling tests only: the next mixed
+ *   BGW_OPT_TEST_DROP_LOAD  for failure-handling tests only: 1, the next mixed
  *                        contractions lose one operand load on purpose, so the
  *                        kernel's bounded waits (about 2 s) expire, it frees its
  *                        resources and records an error that a host finalize
- *                        reports as BGW_E_TIMEOUT.  No fault, trap or hang.
+ *                        reports as BGW_E_TIMEOUT; 2, the same for the streamed
+ *                        z + y kernel of FP32 32^3 boxes (whose planes arrive by
+ *                        TMA): its first CTA skips one plane copy.  No fault,
+ *                        trap or hang.
  */
 enum { BGW_OPT_KCHUNK = 1, BGW_OPT_PAIR_TILE_V = 2, BGW_OPT_PAIR_TILE_C = 3, BGW_OPT_GRID_SLOTS = 4,
        BGW_OPT_TEST_DROP_LOAD = 5, BGW_OPT_TEST_FAIL_ALLOC = 6, BGW_OPT_K1_PATH = 7,

@@ -590,7 +590,7 @@ cudaError_t launch_mtxel(bgw_ctx_s *c, const QState &s, int ik, int kp, const in
         ? bgw::mtxel_f64(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, 0, 0, c->mtxel_lanes, 0,
                          xp.get())
         : bgw::mtxel_f32(Uv, Uc, nv, nc, ax, gmap, s.ng, c->A.p, c->Bs.p, M, ldm, c->st, tv, tc, c->mtxel_lanes,
-                         c->mtxel_zy, xp.get());
+                         c->mtxel_zy, xp.get(), static_cast<int *>(c->errflag.p), c->test_drop_load == 2);
     xp.finish();
     return e;
 }
@@ -880,7 +880,7 @@ cudaError_t run_range(bgw_ctx_s *c, std::vector<QState> &qs, int nfreq, const do
             if (c->prec != BGW_FP64) {
                 const int rec = c->stage_begin_on(3, gs);
                 e = bgw::mixed_gemm(group.data(), (int)group.size(), nfreq, (int)c->prec, c->sm_count, gs,
-                                    static_cast<int *>(c->errflag.p), c->test_drop_load);
+                                    static_cast<int *>(c->errflag.p), c->test_drop_load == 1);
                 c->stage_end(rec, 1);
                 if (e != cudaSuccess) return join(), e;
             }
@@ -939,7 +939,8 @@ bgw_status mtxel_into(bgw_ctx_s *c, const char *who, QState &s, int ik, int a0, 
             ? bgw::mtxel_f64(c->slot_ptr(sa, a0), c->slot_ptr(sb, b0), na, nb2, ax, gmap, s.ng, c->A.p, c->Bs.p, M,
                              s.ng, c->st, 0, 0, c->mtxel_lanes, 0, xp.get())
             : bgw::mtxel_f32(c->slot_ptr(sa, a0), c->slot_ptr(sb, b0), na, nb2, ax, gmap, s.ng, c->A.p, c->Bs.p, M,
-                             s.ng, c->st, 0, 0, c->mtxel_lanes, c->mtxel_zy, xp.get());
+                             s.ng, c->st, 0, 0, c->mtxel_lanes, c->mtxel_zy, xp.get(),
+                             static_cast<int *>(c->errflag.p));
     xp.finish();
     if (e != cudaSuccess) return c->cuda_fail(e, "matrix-element kernels");
     return BGW_OK;
@@ -1482,7 +1483,8 @@ bgw_status bgw_set_option(bgw_ctx c, int option, long value) {
             (option == BGW_OPT_PAIR_TILE_V ? c->tile_v : c->tile_c) = (int)value;
             return BGW_OK;
         case BGW_OPT_TEST_DROP_LOAD:
-            c->test_drop_load = value != 0;
+            if (value < 0 || value > 2) return c->fail(BGW_E_ARG, "set_option: test drop load must be 0, 1 or 2");
+            c->test_drop_load = (int)value;
             return BGW_OK;
         case BGW_OPT_K1_PATH:
             if (value < 0 || value > 4) return c->fail(BGW_E_ARG, "set_option: K1 path must be 0..4");

@@ -15,8 +15,9 @@ cudaError_t wfn_to_grid_batch_f32(const K1Job *jobs, int n, int B, cudaStream_t 
 }
 cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv, int tc, int lanes, int zy, const XPassHook *hook) {
-    return f32::mtxel(Uv, Uc, nv, nc, a, gmap, ng, A, Bs, M, ldm, st, tv, tc, lanes, zy, hook);
+                      cudaStream_t st, int tv, int tc, int lanes, int zy, const XPassHook *hook, int *err,
+                      int drop) {
+    return f32::mtxel(Uv, Uc, nv, nc, a, gmap, ng, A, Bs, M, ldm, st, tv, tc, lanes, zy, hook, err, drop);
 }
 int plane_tile_candidates(int nv, int nc, const Axes &a, int *tv, int *tc, int max) {
     return f32::plane_tile_list(nv, nc, a, tv, tc, max);

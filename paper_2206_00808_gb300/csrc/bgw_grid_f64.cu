@@ -14,8 +14,9 @@ cudaError_t wfn_to_grid_batch_f64(const K1Job *jobs, int n, int B, cudaStream_t 
 }
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                      cudaStream_t st, int tv, int tc, int lanes, int zy, const XPassHook *hook) {
-    return f64::mtxel(Uv, Uc, nv, nc, a, gmap, ng, A, Bs, M, ldm, st, tv, tc, lanes, zy, hook);
+                      cudaStream_t st, int tv, int tc, int lanes, int zy, const XPassHook *hook, int *err,
+                      int drop) {
+    return f64::mtxel(Uv, Uc, nv, nc, a, gmap, ng, A, Bs, M, ldm, st, tv, tc, lanes, zy, hook, err, drop);
 }
 cudaError_t bounds_take_grid_f64(unsigned *word) { return bgw_bounds_take(word); }
 }  // namespace bgw

@@ -23,10 +23,12 @@
 #include <cuda_pipeline.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "bgw_bounds.cuh"
 #include "bgw_fft.cuh"
 #include "bgw_internal.h"
+#include "bgw_tc_common.cuh"
 
 namespace bgw {
 
@@ -876,25 +878,38 @@ struct StreamTile {
     static constexpr int C = N >= 24 ? 2 : (N >= 18 ? 3 : 4);
 };
 
-template <int N>
+// TMA staging (N = 32): a plane component is two boxes of N rows x kTmaHalf
+// values (128 bytes) in the 128-byte swizzle, 16-byte chunk c of row r at
+// chunk c ^ (r & 7); 1024-byte aligned, so one more KB is requested.
+constexpr int kTmaHalf = 16;
+constexpr int kErrCopy = 5;   // a plane copy of the streamed kernel did not land in time
+
+template <int N, bool TMA>
 __host__ __device__ constexpr size_t stream_smem() {
     constexpr int SV = StreamTile<N>::V, SC = StreamTile<N>::C;
-    return sizeof(cpx<float>) * ((size_t)(SV + 2 * SC) * 2 * N * plane_row<N>() + (size_t)2 * SV * SC * N * kZW);
+    return sizeof(cpx<float>) * ((size_t)(SV + 2 * SC) * 2 * N * (TMA ? N : plane_row<N>()) +
+                                 (size_t)2 * SV * SC * N * kZW) +
+           (TMA ? 1024 : 0);
 }
 
-template <int N, bool WIN>
+template <int N, bool WIN, bool TMA>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int CC, int w1, int w2, int s1,
-             int s2, C *__restrict__ Bs) {
+             int s2, C *__restrict__ Bs, const __grid_constant__ CUtensorMap map_v,
+             const __grid_constant__ CUtensorMap map_c, int *__restrict__ err, int drop_first_copy) {
     constexpr int kStreamV = StreamTile<N>::V, kStreamC = StreamTile<N>::C;
     static_assert(N % 2 == 0 && kStreamV * kStreamC * N <= kZThreads, "one z line per z thread");
+    static_assert(!TMA || (N == 2 * kTmaHalf && sizeof(T) == 4), "TMA staging: N = 32, FP32");
     extern __shared__ unsigned char smem_raw[];
-    constexpr int RS = plane_row<N>();
+    __shared__ __align__(8) uint64_t bar_v, bar_c[2];
+    constexpr int RS = TMA ? N : plane_row<N>();   // row of a staged plane (dense and swizzled with TMA)
     constexpr int PS = N * RS;                   // one spin component of a plane
     constexpr int NN = N * N;
     constexpr int CH = NN / 2;                   // 16-byte chunks per plane component
     constexpr int ZS = kStreamV * kStreamC * N * kZW;
-    C *V = reinterpret_cast<C *>(smem_raw);
+    unsigned char *sbase = smem_raw;
+    if constexpr (TMA) sbase += (1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u;
+    C *V = reinterpret_cast<C *>(sbase);
     C *Cb0 = V + kStreamV * 2 * PS;
     C *Z0 = Cb0 + 2 * kStreamC * 2 * PS;
     const int x = blockIdx.x, n0 = gridDim.x;
@@ -915,18 +930,55 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
             __pipeline_memcpy_async(d, g, 16);
         }
     };
+    // TMA: nb band planes (both spin components, two boxes each) issued by one
+    // thread onto one mbarrier; every thread waits (bounded) for them
+    auto tma_planes = [&](C *dst, const CUtensorMap *map, int band0, int nb, uint64_t *bar) {
+        if (threadIdx.x != 0) return;
+        const uint32_t b = tc::smem_u32(bar);
+        tc::fence_proxy_async_smem();            // the buffer's last readers passed a barrier
+        tc::mbar_expect_tx(b, (uint32_t)(nb * 2 * NN * sizeof(C)));
+        for (int ba = 0; ba < 2 * nb; ++ba)
+            for (int h = 0; h < 2; ++h)
+                tc::tma_load_4d(tc::smem_u32(dst + ba * PS + h * (N * kTmaHalf)), map, b, h * 2 * kTmaHalf, 0, x,
+                                2 * band0 + ba);
+    };
+    auto wait_planes = [&](uint64_t *bar, uint32_t parity) {
+        if (!tc::mbar_wait(tc::smem_u32(bar), parity) && err) atomicExch(err, kErrCopy);
+    };
     const int ng = (cend - cbeg + kStreamC - 1) / kStreamC;
-    copy_planes(V, Uv, v0, tv, 0, kStreamThreads);
-    if (ng > 0) copy_planes(Cb0, Uc, cbeg, min(kStreamC, cend - cbeg), 0, kStreamThreads);
-    __pipeline_commit();
-    __pipeline_wait_prior(0);
+    if constexpr (TMA) {
+        if (threadIdx.x == 0) {
+            tc::mbar_init(tc::smem_u32(&bar_v), 1);
+            tc::mbar_init(tc::smem_u32(&bar_c[0]), 1);
+            tc::mbar_init(tc::smem_u32(&bar_c[1]), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        // test hook: the first CTA never issues its valence planes, so its
+        // bounded wait expires and records kErrCopy
+        if (!(drop_first_copy && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0))
+            tma_planes(V, &map_v, v0, tv, &bar_v);
+        if (ng > 0) tma_planes(Cb0, &map_c, cbeg, min(kStreamC, cend - cbeg), &bar_c[0]);
+        wait_planes(&bar_v, 0);
+        if (ng > 0) wait_planes(&bar_c[0], 0);
+    } else {
+        copy_planes(V, Uv, v0, tv, 0, kStreamThreads);
+        if (ng > 0) copy_planes(Cb0, Uc, cbeg, min(kStreamC, cend - cbeg), 0, kStreamThreads);
+        __pipeline_commit();
+        __pipeline_wait_prior(0);
+    }
     __syncthreads();
     for (int k = 0; k <= ng; ++k) {
-        if (k + 1 < ng && threadIdx.x < kZThreads) {
+        if (k + 1 < ng) {
             const int c1 = cbeg + (k + 1) * kStreamC;
-            copy_planes(Cb0 + ((k + 1) & 1) * (kStreamC * 2 * PS), Uc, c1, min(kStreamC, cend - c1), 0, kZThreads);
+            if constexpr (TMA)
+                tma_planes(Cb0 + ((k + 1) & 1) * (kStreamC * 2 * PS), &map_c, c1, min(kStreamC, cend - c1),
+                           &bar_c[(k + 1) & 1]);
+            else if (threadIdx.x < kZThreads)
+                copy_planes(Cb0 + ((k + 1) & 1) * (kStreamC * 2 * PS), Uc, c1, min(kStreamC, cend - c1), 0,
+                            kZThreads);
         }
-        __pipeline_commit();
+        if constexpr (!TMA) __pipeline_commit();
         if (threadIdx.x < kZThreads) {
             // z line (pair, y) of group k, pair = v * tc + c
             const int tc = k < ng ? min(kStreamC, cend - (cbeg + k * kStreamC)) : 0;
@@ -941,7 +993,11 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
                 C a[N];
 #pragma unroll
                 for (int z = 0; z < N / 2; ++z) {
-                    const float4 va = v4[z], vb = v4[P4 + z], ca = c4[z], cb = c4[P4 + z];
+                    // float4 index of values 2z, 2z+1 of row y (swizzled boxes with TMA)
+                    int q = z;
+                    if constexpr (TMA)
+                        q = (z / 8) * (N * kTmaHalf / 2) - y * (RS / 2) + y * (kTmaHalf / 2) + ((z % 8) ^ (y & 7));
+                    const float4 va = v4[q], vb = v4[P4 + q], ca = c4[q], cb = c4[P4 + q];
                     a[2 * z] = rho2(C{va.x, va.y}, C{ca.x, ca.y}, C{vb.x, vb.y}, C{cb.x, cb.y});
                     a[2 * z + 1] = rho2(C{va.z, va.w}, C{ca.z, ca.w}, C{vb.z, vb.w}, C{cb.z, cb.w});
                 }
@@ -965,7 +1021,11 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
                 store_kept<N, WIN>(b, Bs + ((p * n0 + x) * w1) * w2 + jz, w2, ns1, w1);
             }
         }
-        __pipeline_wait_prior(0);        // group k + 1 has landed
+        if constexpr (TMA) {
+            if (k + 1 < ng) wait_planes(&bar_c[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1));
+        } else {
+            __pipeline_wait_prior(0);    // group k + 1 has landed
+        }
         __syncthreads();                 // Z[k & 1] written, Z[(k - 1) & 1] and Cb[k & 1] read
     }
 }
@@ -1379,10 +1439,35 @@ struct XMark {
     }
 };
 
+// Tensor maps of the valence (nvb bands from uv) and conduction (nc bands
+// from uc) grids for the TMA form of the streamed kernel: 4-D, innermost the
+// 2 N floats of a z row, then y, x and band component; one box is half a row
+// (kTmaHalf values, 128 bytes) by all N rows, 128-byte swizzle.
+static cudaError_t stream_maps(const C *uv, int nvb, const C *uc, int nc, const Axes &a, CUtensorMap *mv,
+                               CUtensorMap *mc) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    cudaError_t e = tc::tensor_map_encoder(&enc);
+    if (e != cudaSuccess) return e;
+    auto one = [&](const C *base, int nb, CUtensorMap *m) -> cudaError_t {
+        const cuuint64_t row = (cuuint64_t)a.n[2] * sizeof(C);
+        const cuuint64_t dims[4] = {(cuuint64_t)2 * a.n[2], (cuuint64_t)a.n[1], (cuuint64_t)a.n[0], (cuuint64_t)2 * nb};
+        const cuuint64_t strides[3] = {row, row * a.n[1], row * a.n[1] * a.n[0]};
+        const cuuint32_t box[4] = {2 * kTmaHalf, (cuuint32_t)a.n[1], 1, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<C *>(base), dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    };
+    e = one(uv, nvb, mv);
+    if (e == cudaSuccess) e = one(uc, nc, mc);
+    return e;
+}
+
 static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const Axes &a,
                                const int *gmap, int ng, C *Ap, C *Bp, C *Mp, long ldm,
                                cudaStream_t st, int tv_req, int tc_req, int lanes, int zy,
-                               const XPassHook *hook) {
+                               const XPassHook *hook, int *err, int drop) {
     const long P = (long)nv * nc;
     if (oct_len(a) && (lanes == 8 || (lanes == 0 && use_coop(a) && use_oct(a)))) {
         // eight lanes per line: fused z+y, then the x pass
@@ -1447,14 +1532,23 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
         dim3 grid((unsigned)a.n[0], (unsigned)nvg, (unsigned)((nc + CC - 1) / CC));
         cudaError_t e = cudaSuccess;
         const bool win = kept_in_window(a, 1) && kept_in_window(a, 2);
+        CUtensorMap mv, mc;
+        memset(&mv, 0, sizeof mv);
+        memset(&mc, 0, sizeof mc);
         BGW_FOR_EACH_STREAM_LEN(a.n[1], {
-            const size_t ss = stream_smem<N>();
-            auto kern = k2_zy_stream<N, false>;
+            constexpr bool kTma = N == 2 * kTmaHalf && sizeof(T) == 4;   // 32^3 boxes: planes by TMA
+            if constexpr (kTma) {
+                e = stream_maps(uv, nv, uc, nc, a, &mv, &mc);
+                if (e != cudaSuccess) return e;
+            }
+            const size_t ss = stream_smem<N, kTma>();
+            auto kern = k2_zy_stream<N, false, kTma>;
             if constexpr (N > 2 * kWin + 1)
-                if (win) kern = k2_zy_stream<N, true>;
+                if (win) kern = k2_zy_stream<N, true, kTma>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
             if (e != cudaSuccess) return e;
-            kern<<<grid, kStreamThreads, ss, st>>>(uv, uc, nv, nc, CC, a.w[1], a.w[2], a.s[1], a.s[2], Bp);
+            kern<<<grid, kStreamThreads, ss, st>>>(uv, uc, nv, nc, CC, a.w[1], a.w[2], a.s[1], a.s[2], Bp, mv, mc,
+                                                   err, drop);
         });
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1534,7 +1628,8 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
 
 static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                          const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
-                         cudaStream_t st, int tv_req, int tc_req, int lanes, int zy, const XPassHook *hook) {
+                         cudaStream_t st, int tv_req, int tc_req, int lanes, int zy, const XPassHook *hook,
+                         int *err, int drop) {
     if ((long)nv * nc == 0) return cudaSuccess;
     const C *uv = static_cast<const C *>(Uv), *uc = static_cast<const C *>(Uc);
     C *Ap = static_cast<C *>(A), *Bp = static_cast<C *>(Bs), *Mp = static_cast<C *>(M);
@@ -1543,7 +1638,7 @@ static cudaError_t mtxel(const void *Uv, const void *Uc, int nv, int nc, const A
     for (int vb0 = 0; vb0 < nv; vb0 += VB) {
         const int nvb = nv - vb0 < VB ? nv - vb0 : VB;
         cudaError_t e = mtxel_batch(uv + (long)vb0 * 2 * vol, uc, nvb, nc, a, gmap, ng, Ap, Bp,
-                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req, lanes, zy, hook);
+                                    Mp + (long)vb0 * nc * ldm, ldm, st, tv_req, tc_req, lanes, zy, hook, err, drop);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

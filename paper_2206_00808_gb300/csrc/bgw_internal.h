@@ -67,7 +67,10 @@ cudaError_t wfn_to_grid_batch_f32(const K1Job *jobs, int n, int B, cudaStream_t 
 // 2 streamed where it applies.
 // hook (profiling, may be NULL): fn(ctx, 1, n) just before each x-pass launch
 // group (n = kernels launched since the previous mark) and fn(ctx, 0, n)
-// right after it.
+// right after it.  err (may be NULL): device int that a bounded wait of the
+// streamed FP32 kernel's TMA staging sets to 5 when it gives up.  drop
+// (tests only): the first CTA of that kernel skips one plane copy, so that
+// wait expires.
 struct XPassHook {
     void (*fn)(void *ctx, int begin, int kernels);
     void *ctx;
@@ -75,11 +78,11 @@ struct XPassHook {
 cudaError_t mtxel_f64(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
                       cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0,
-                      const XPassHook *hook = nullptr);
+                      const XPassHook *hook = nullptr, int *err = nullptr, int drop = 0);
 cudaError_t mtxel_f32(const void *Uv, const void *Uc, int nv, int nc, const Axes &a,
                       const int *gmap, int ng, void *A, void *Bs, void *M, long ldm,
                       cudaStream_t st, int tv = 0, int tc = 0, int lanes = 0, int zy = 0,
-                      const XPassHook *hook = nullptr);
+                      const XPassHook *hook = nullptr, int *err = nullptr, int drop = 0);
 // The last forward pass gathers the kept w0*w1*w2 cube through shared memory
 // when it is small; a larger cube is written straight to M through an
 // inverse map (cube cell -> G index or -1) stored in the map buffer right
