@@ -139,3 +139,27 @@ def test_both_zy_kernels_match_oracle(gpu_lib, zy, over):
     ctx.close()
     assert rel_fro(got, ref) <= TOL_CHI_MIXED
 
+
+
+@pytest.mark.parametrize("shift", [(0, 0, 0), (0, 0, 7), (0, 7, 0)])
+def test_streamed_zy_kernel_off_centre_sphere(gpu_lib, shift):
+    """M of the streamed z + y kernel on a 32^3 box (TMA staging) element by
+    element against the oracle for a G set shifted off centre: (0, 0, 0)
+    keeps every output within 8 of zero (the pruned store window), the other
+    two put kept z or y outputs outside it (the full store loop)."""
+    torch = pytest.importorskip("torch")
+    p = syn.make_problem("si18_qx", box=(32, 32, 32), nv=5, nc=9, ng=181, nfreq=1)
+    q, geps, _ = p.qs[0]
+    g = np.ascontiguousarray(geps + np.asarray(shift, dtype=geps.dtype))
+    nc = 9
+    ctx = gpu_lib.Chi0Context(p, "mixed")
+    gpu_lib.bgw_set_option(ctx.ctx, gpu_lib.BGW_OPT_MTXEL_ZY, 2)
+    ctx.upload()
+    for ik in (0, 4):
+        kp, G0 = oracle.umklapp(p.kcrys, ik, q)
+        M = torch.zeros((p.nv, nc, len(g)), dtype=torch.complex64, device="cuda")
+        gpu_lib.bgw_mtxel_spinor(ctx.ctx, q, g, ik, 0, p.nv, 0, nc, M)
+        ref = oracle.mtxel(p.box, p.gvec[ik], p.coeff[ik][:p.nv], p.gvec[kp],
+                           p.coeff[kp][p.nv:p.nv + nc], G0, g)
+        assert np.abs(M.cpu().numpy() - ref).max() <= TOL_M_FP32 * np.abs(ref).max()
+    ctx.close()
