@@ -114,14 +114,20 @@ inline bool wfn_uses_r(const Axes &a, size_t csize) {
 }
 
 // Valence bands per batch of the matrix-element kernels: their scratch
-// (A, where used, + Bs per pair) stays under 1 GiB.
+// (A, where used, + Bs per pair) stays under 1 GiB.  When the bands need more
+// than one batch, a batch is a whole number of the streamed FP32 kernel's
+// valence groups (5 bands at N = 24, else 4), so no batch but the last ends
+// in a short group (18 bands ran as 17 + 1: groups 4,4,4,4,1 and 1).
 inline int mtxel_v_batch(int nv, int nc, const Axes &a, size_t csize) {
     const size_t per_pair =
         csize * ((mtxel_uses_a(a) ? (size_t)a.n[0] * a.n[1] * a.w[2] : 0) + (size_t)a.n[0] * a.w[1] * a.w[2]);
     const size_t cap = (size_t)1 << 30;
     size_t vb = cap / (per_pair * (size_t)(nc > 0 ? nc : 1) + 1);
     if (vb < 1) vb = 1;
-    return (int)(vb < (size_t)nv ? vb : (size_t)nv);
+    if (vb >= (size_t)nv) return nv;
+    const size_t group = a.n[1] == 24 ? 5 : 4;
+    if (vb >= group) vb -= vb % group;
+    return (int)vb;
 }
 
 // Candidate pair tiles (tv, tc) of the plane-fused FP32 kernel for this shape,
