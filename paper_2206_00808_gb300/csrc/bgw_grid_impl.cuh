@@ -884,20 +884,22 @@ struct StreamTile {
 constexpr int kTmaHalf = 16;
 constexpr int kErrCopy = 5;   // a plane copy of the streamed kernel did not land in time
 
-template <int N, bool TMA>
-__host__ __device__ constexpr size_t stream_smem() {
-    constexpr int SV = StreamTile<N>::V, SC = StreamTile<N>::C;
+// Shared memory of the streamed kernel with SV x SC band groups: the valence
+// planes, two conduction buffers and two Z buffers (kept width w2 with TMA,
+// kZW otherwise).
+template <int N, int SV, int SC, bool TMA>
+__host__ __device__ constexpr size_t stream_smem(int w2) {
     return sizeof(cpx<float>) * ((size_t)(SV + 2 * SC) * 2 * N * (TMA ? N : plane_row<N>()) +
-                                 (size_t)2 * SV * SC * N * kZW) +
+                                 (size_t)2 * SV * SC * N * (TMA ? w2 : kZW)) +
            (TMA ? 1024 : 0);
 }
 
-template <int N, bool WIN, bool TMA>
+template <int N, int SV, int SC, bool WIN, bool TMA>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, int CC, int w1, int w2, int s1,
              int s2, C *__restrict__ Bs, const __grid_constant__ CUtensorMap map_v,
              const __grid_constant__ CUtensorMap map_c, int *__restrict__ err, int drop_first_copy) {
-    constexpr int kStreamV = StreamTile<N>::V, kStreamC = StreamTile<N>::C;
+    constexpr int kStreamV = SV, kStreamC = SC;
     static_assert(N % 2 == 0 && kStreamV * kStreamC * N <= kZThreads, "one z line per z thread");
     static_assert(!TMA || (N == 2 * kTmaHalf && sizeof(T) == 4), "TMA staging: N = 32, FP32");
     extern __shared__ unsigned char smem_raw[];
@@ -906,7 +908,7 @@ k2_zy_stream(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc,
     constexpr int PS = N * RS;                   // one spin component of a plane
     constexpr int NN = N * N;
     constexpr int CH = NN / 2;                   // 16-byte chunks per plane component
-    constexpr int ZS = kStreamV * kStreamC * N * kZW;
+    const int ZS = kStreamV * kStreamC * N * (TMA ? w2 : kZW);   // as the host sized them
     unsigned char *sbase = smem_raw;
     if constexpr (TMA) sbase += (1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u;
     C *V = reinterpret_cast<C *>(sbase);
@@ -1510,12 +1512,6 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
     if ((zy == 2 || (zy == 0 && tv_req <= 0)) && use_stream(a)) {
         // streamed pair density + z + y: conduction ranges sized for about four
         // waves of one CTA per SM
-        int kStreamV = 4, kStreamC = 2;
-        BGW_FOR_EACH_STREAM_LEN(a.n[1], {
-            kStreamV = StreamTile<N>::V;
-            kStreamC = StreamTile<N>::C;
-        });
-        const int nvg = (nv + kStreamV - 1) / kStreamV;
         static int sms = 0;
         if (sms == 0) {
             int dev = 0;
@@ -1523,33 +1519,50 @@ static cudaError_t mtxel_batch(const C *uv, const C *uc, int nv, int nc, const A
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
                 sms = 148;
         }
-        const long want = 4L * sms;
-        const long per = (long)a.n[0] * nvg;
-        const int chunks = (int)((want + per - 1) / per);
-        int CC = (nc + chunks - 1) / chunks;
-        CC = (CC + kStreamC - 1) / kStreamC * kStreamC;
-        if (CC < kStreamC) CC = kStreamC;
-        dim3 grid((unsigned)a.n[0], (unsigned)nvg, (unsigned)((nc + CC - 1) / CC));
         cudaError_t e = cudaSuccess;
         const bool win = kept_in_window(a, 1) && kept_in_window(a, 2);
         CUtensorMap mv, mc;
         memset(&mv, 0, sizeof mv);
         memset(&mc, 0, sizeof mc);
+        auto launch = [&](auto kern, int SV, int SC, size_t ss) -> cudaError_t {
+            const int nvg = (nv + SV - 1) / SV;
+            const long want = 4L * sms;
+            const long per = (long)a.n[0] * nvg;
+            const int chunks = (int)((want + per - 1) / per);
+            int CC = (nc + chunks - 1) / chunks;
+            CC = (CC + SC - 1) / SC * SC;
+            if (CC < SC) CC = SC;
+            dim3 grid((unsigned)a.n[0], (unsigned)nvg, (unsigned)((nc + CC - 1) / CC));
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+            if (r != cudaSuccess) return r;
+            kern<<<grid, kStreamThreads, ss, st>>>(uv, uc, nv, nc, CC, a.w[1], a.w[2], a.s[1], a.s[2], Bp, mv, mc,
+                                                   err, drop);
+            return cudaSuccess;
+        };
         BGW_FOR_EACH_STREAM_LEN(a.n[1], {
             constexpr bool kTma = N == 2 * kTmaHalf && sizeof(T) == 4;   // 32^3 boxes: planes by TMA
+            constexpr int V0 = StreamTile<N>::V, C0 = StreamTile<N>::C;
             if constexpr (kTma) {
                 e = stream_maps(uv, nv, uc, nc, a, &mv, &mc);
                 if (e != cudaSuccess) return e;
+                // 2 x 4 band groups where they need fewer phases than 4 x 2 (a
+                // valence count that is not a multiple of 4) and fit
+                const long ph0 = (long)((nv + V0 - 1) / V0) * ((nc + C0 - 1) / C0);
+                const long ph1 = (long)((nv + 1) / 2) * ((nc + 3) / 4);
+                const size_t ss1 = stream_smem<N, 2, 4, true>(a.w[2]);
+                if (ph1 < ph0 && ss1 + 256 <= (size_t)227 * 1024) {
+                    e = win ? launch(k2_zy_stream<N, 2, 4, true, true>, 2, 4, ss1)
+                            : launch(k2_zy_stream<N, 2, 4, false, true>, 2, 4, ss1);
+                    break;
+                }
             }
-            const size_t ss = stream_smem<N, kTma>();
-            auto kern = k2_zy_stream<N, false, kTma>;
+            const size_t ss = stream_smem<N, V0, C0, kTma>(a.w[2]);
+            auto kern = k2_zy_stream<N, V0, C0, false, kTma>;
             if constexpr (N > 2 * kWin + 1)
-                if (win) kern = k2_zy_stream<N, true, kTma>;
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-            if (e != cudaSuccess) return e;
-            kern<<<grid, kStreamThreads, ss, st>>>(uv, uc, nv, nc, CC, a.w[1], a.w[2], a.s[1], a.s[2], Bp, mv, mc,
-                                                   err, drop);
+                if (win) kern = k2_zy_stream<N, V0, C0, true, kTma>;
+            e = launch(kern, V0, C0, ss);
         });
+        if (e != cudaSuccess) return e;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         XMark xm(hook, 1);
