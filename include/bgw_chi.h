@@ -353,10 +353,11 @@ BGW_API bgw_status bgw_graph_launch(bgw_ctx ctx);
  *                        1 the plane kernel with the
  *                        pair tile of BGW_OPT_PAIR_TILE_V/C (or the autotuner's),
  *                        2 the streamed kernel where it applies: a CTA keeps
- *                        four valence x-planes in shared memory and streams the
- *                        conduction x-planes in groups of four, copying the next
- *                        group while the current one is transformed.  Same
- *                        results up to rounding.
+ *                        a group of valence x-planes (4, or 2 where that needs
+ *                        fewer passes; 5 at N = 24) in shared memory and streams
+ *                        the conduction x-planes in groups (2, or 4), copying
+ *                        the next group (by TMA on 32^3 boxes) while the current
+ *                        one is transformed.  Same results up to rounding.
  *   BGW_OPT_DEFER_K1     0 (default): bgw_wfn_upload builds the k-point's
  *                        real-space grid before it returns (on the stream).
  *                        1: the build is deferred to the next call that reads
