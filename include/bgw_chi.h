@@ -177,7 +177,11 @@ BGW_API bgw_status bgw_chi0_accumulate(bgw_ctx ctx, int nq, const bgw_q *qs, int
  * 1/N_k and Hermitian by construction.
  *   on_device : 1 = chi0 is a device pointer (asynchronous);
  *               0 = chi0 is a host pointer (blocks until written).
- * The accumulators are kept (call bgw_chi0_reset to start over).
+ * The accumulators are kept (call bgw_chi0_reset to start over).  A host
+ * finalize also reads the context's device error word: BGW_E_TIMEOUT if a
+ * bounded device-side wait gave up since the last such read (the result is
+ * invalid; the context stays usable), BGW_E_ARG if the FP64 tensor-core
+ * contraction met a positive pair weight.
  */
 BGW_API bgw_status bgw_chi0_finalize(bgw_ctx ctx, int iq, void *chi0, int on_device);
 
@@ -201,7 +205,8 @@ BGW_API bgw_status bgw_chi0_finalize(bgw_ctx ctx, int iq, void *chi0, int on_dev
  *   frequencies), the k counts, then each q-point's FP64 accumulators as
  *   complex128 [N_w][N_G][N_G] (lower block triangle meaningful).  Waits for
  *   the context stream.  BGW_E_TIMEOUT if a device-side wait of the mixed
- *   contraction gave up (the sum is invalid); BGW_E_STATE during graph
+ *   or FP64 tensor-core contraction or of the TMA-staged FP32 matrix-element
+ *   kernel gave up (the sum is invalid); BGW_E_STATE during graph
  *   capture or without a running sum; BGW_E_ARG if buf is too small.
  * bgw_chi0_resume: starts a running sum from a checkpoint: the q-set and
  *   frequencies (as for accumulate) must be those the checkpoint was taken
