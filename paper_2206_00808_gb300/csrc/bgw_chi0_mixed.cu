@@ -14,11 +14,12 @@
 // use the same kernels on kind::tf32: three products of TF32 hi + lo
 // (x ~ hi + lo to ~2^-22; 32-pair K blocks, half the BF16 MMA rate), or the
 // single product hi.hi (~2^-11 per operand).  The accumulator
-// truncates on every add, so the large hi.hi products go to three TMEM
-// accumulators (one per third of K) and the two small cross products to a
-// fourth: no accumulator takes more than a third of the large adds, and the
-// small terms are not rounded against the large sum.  The epilogue adds the
-// four, folds the 2x2 blocks into complex chi and adds them to the FP64
+// truncates on every add, so the large hi.hi products rotate over three TMEM
+// accumulators that are drained into FP32 registers (round to nearest) every
+// kSub K blocks, and the two small cross products go to a fourth: no
+// accumulator takes more than 4 kSub large adds, and the small terms are not
+// rounded against the large sum.  At each work item's end the sums are
+// folded from 2x2 real blocks into complex chi and added to the FP64
 // accumulator (the FP64 reduction across k blocks).
 //
 // Kernels:
@@ -28,13 +29,16 @@
 //              zero padded to R = 128-multiple rows, Kp = 64-multiple pairs):
 //              one 16 KB TMA box is one contiguous piece of memory, so the
 //              split writes and the GEMM loads whole DRAM pages
-//   k5_gemm    one CTA per (lower 128x128 tile of D, frequency): TMA loads
-//              (128B swizzle) into a ring of 192 KB (3 stages of four tiles,
-//              or 6 of two for one product), one thread issues tcgen05.mma,
-//              four warps drain TMEM and update chi in FP64.
-// Every mbarrier wait has an iteration limit; on expiry the kernel records
-// an error code in *err, waits (bounded) for its own copies in flight,
-// frees its tensor memory and returns.
+//   k5_gemm    persistent, one CTA per SM walking the work items (lower
+//              128x128 tile of D, frequency) of every q-point of a group: TMA
+//              loads (128B swizzle) into a ring of 192 KB (3 stages of four
+//              tiles, or 6 of two for one product), one thread issues
+//              tcgen05.mma, four warps drain TMEM and fold each finished tile
+//              into a complex FP32 tile in shared memory, two warps add that
+//              tile to chi in FP64.
+// Every mbarrier wait gives up after about 2 s (with an iteration backstop);
+// on expiry the kernel records an error code in *err, waits (bounded) for its
+// own copies in flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
