@@ -859,19 +859,23 @@ k2_zy_plane(const C *__restrict__ Uv, const C *__restrict__ Uc, int nv, int nc, 
 // Streamed form of the pair density + z + y passes (FP32, even N <= 32): one
 // CTA per (x-plane, group of up to SV valence bands, range of conduction
 // bands).  The valence x-planes stay in shared memory for the whole item; the
-// conduction x-planes come in groups of SC bands through two buffers filled
-// by cp.async.  Each phase k, after which the CTA synchronises once:
+// conduction x-planes come in groups of SC bands through two buffers, filled
+// by TMA on 32^3 boxes (one thread, an mbarrier per buffer) and by cp.async
+// from the z-line threads otherwise.  Each phase k, after which the CTA
+// synchronises once:
 //   threads 0..kZThreads-1  z lines of group k (pair density, FFT, kept outputs
 //                           into Z[k & 1]),
 //   the other threads       y lines of group k - 1 (from Z[(k - 1) & 1] to Bs),
 //   copies                  of group k + 1 into the buffer group k - 1 used,
 // so copies, z lines and y lines of consecutive groups run together.
-// Shared: V[SV][2][N][RS], Cb[2][SC][2][N][RS], Z[2][SV*SC][N][kZW].
+// Shared: V[SV][2][N][RS], Cb[2][SC][2][N][RS], Z[2][SV*SC][N][W] with RS the
+// padded row N + 2 (dense and swizzled with TMA) and W = kZW (w2 with TMA).
 constexpr int kZThreads = 256, kYThreads = 128, kStreamThreads = kZThreads + kYThreads;
 constexpr int kZW = 17;   // largest kept z width the Z buffers hold
 
-// Valence and conduction group sizes per box length: as many z lines
-// (SV * SC * N) as z threads, or nearly.
+// Default valence and conduction group sizes per box length: as many z
+// lines (SV * SC * N) as z threads, or nearly (32^3 TMA launches may take
+// 2 x 4 instead, see mtxel_batch).
 template <int N>
 struct StreamTile {
     static constexpr int V = N == 24 ? 5 : 4;
