@@ -75,3 +75,26 @@ def test_zy_kernel_names_follow_the_library_rule():
     assert bench.zy_kernel_name(g, "fp64", 2).startswith("k2_zpass")
     b = syn.make_bi2se3_problem(kgrid=(1, 1, 1), nv=2, nc=2, nfreq=1, device=None)
     assert bench.zy_kernel_name(b, "mixed", 2) == "k2_zy_oct"
+
+
+def test_captured_traffic_lookup_and_operand_bytes():
+    """roofline.traffic comes only from a capture of the same launch shape
+    with an unchanged kernel source; the operand bytes of one GaSb-like
+    contraction launch (k-chunk 2) are 34 planes x 1664 rows x 14,400 pairs x
+    2 B."""
+    nbytes, why = bench.captured_traffic("k5_gemm", "gasb32", "mixed", 4)
+    assert nbytes is None and "no ncu capture" in why
+    nbytes, why = bench.captured_traffic("k5_gemm", "si24", "mixed", 2)
+    assert nbytes is None
+    p = syn.make_problem("gasb32", coeff_on=None)
+    assert bench.gemm_operand_bytes(p, 2) == 34 * 1664 * 14400 * 2
+    saved = dict(bench.CAPTURED_TRAFFIC)
+    try:
+        key = ("k5_gemm", "gasb32", "mixed", 2)
+        path, _, b = bench.CAPTURED_TRAFFIC[key]
+        bench.CAPTURED_TRAFFIC[key] = (path, "0" * 16, b)          # a source edited since the capture
+        nbytes, why = bench.captured_traffic(*key)
+        assert nbytes is None and "changed since the capture" in why
+    finally:
+        bench.CAPTURED_TRAFFIC.clear()
+        bench.CAPTURED_TRAFFIC.update(saved)
